@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Throughput of the implicit LISL HJB solver: grid-point·steps/s at 2049 x 2049, 65 controls.
+
+Workload (the mixed-precision configuration): uncertain-correlation HJB on [-2, 2]^2,
+2049 x 2049 nodes, 65 controls rho in [-0.95, 0.95], (s1, s2) ~ U[0.15, 0.4]^2 from seed 0,
+dt = 1/128.  A bench step is one implicit time step of the whole hot path: source tables,
+Howard policy iteration (FP64 policy decision with an FP32 screen), Galerkin hierarchy
+rebuilds, and FP64 iterative refinement around an FP32 BiCGSTAB with an FP32 multigrid
+V-cycle.  The W warm-up steps are the first W steps of the 128-step horizon; the K timed
+steps continue the march (K = 125 covers the rest of the horizon).  The working set
+(about 1 GB of vectors, tables and coarse levels) is far larger than L2, so no flush is
+needed between steps.
+
+Output: one JSON line (rank 0).  `value` is the device-timed rate of all ranks together;
+`e2e` repeats the measurement through the public API with the state in pinned host memory
+(H2D before and D2H after every step); `fp64` times the FP64 path on the same steps and
+`mixed_vs_fp64_rel_err` compares the two.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SL-HJB grid-point·steps/s at 2049², 65 controls: mixed vs FP64 GPU at 1e-8 rel"
+UNIT = "grid-point·steps/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=125)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=2049)
+    p.add_argument("--fp64-steps", type=int, default=8)
+    p.add_argument("--e2e-steps", type=int, default=16)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary (None if absent)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith(kernel + ":"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+# ------------------------------------------------------------------------------- CPU oracle
+
+def oracle_rate(n_sample: int, steps: int, t_start_steps: int = 0):
+    """Times the CPU oracle (as it stands) on the same PDE family at n_sample^2."""
+    import workloads as W
+    from oracle import lisl
+    full = W.mixed_2049(seed=0)
+    dt = 1.0 / 128
+    p = W.manufactured(n_sample, 65, -0.95, 0.95, full.s1, full.s2, T=dt * steps, n_steps=steps)
+    t0 = time.perf_counter()
+    lisl.solve(p)
+    wall = time.perf_counter() - t0
+    return n_sample * n_sample * steps / wall, wall
+
+
+def cpu_baseline_record():
+    rate, wall = oracle_rate(257, 1)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 implicit step of the same PDE family on a 257x257 grid (65 controls, "
+                      f"dt=1/128, direct sparse solve), {wall:.1f} s wall; NumPy/SciPy on one host "
+                      f"core ({os.cpu_count()} available)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    # bounded per-step sample: 129^2 steps of the oracle, W + K of them
+    n_sample = 129
+    import workloads as W
+    from oracle import lisl
+    full = W.mixed_2049(seed=0)
+    dt = 1.0 / 128
+    total = args.warmup + args.steps
+    p = W.manufactured(n_sample, 65, -0.95, 0.95, full.s1, full.s2, T=dt * total, n_steps=total)
+    U = p.g.copy()
+    pol = None
+    t_steps = []
+    for s in range(1, total + 1):
+        t0 = time.perf_counter()
+        r = lisl.howard_step(p, U, s * dt, dt, policy0=pol)
+        t_steps.append(time.perf_counter() - t0)
+        U, pol = r.X, r.policy
+    timed = sum(t_steps[args.warmup:])
+    value = n_sample * n_sample * args.steps / timed
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * timed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"oracle sample: {n_sample}x{n_sample} grid of the 2049x2049 "
+                                   f"65-control uncertain-correlation workload, dt=1/128"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step one implicit step at {n_sample}x{n_sample}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- GPU path
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1605_04821_gb300 as slp
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    else:
+        dist = None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    prob = W.mixed_2049(seed=0) if args.n == 2049 else W.scaled(args.n, 65, 128, seed=0,
+                                                                   rho_range=(-0.95, 0.95))
+    n = prob.n
+    dt = 1.0 / 128
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        return slp.solver_from_problem(prob, device=dev, precision=precision, argmin_screen=precision)
+
+    # ---- mixed path (the metric)
+    s = make(1)
+    g = torch.as_tensor(prob.g, dtype=torch.float64, device=dev)
+    u = g.clone()
+    for i in range(1, args.warmup + 1):
+        s.step(u, i * dt, dt)
+    torch.cuda.synchronize()
+    u_after_warm = u.clone()
+    compare_at = min(args.fp64_steps, args.steps)
+    u_cmp = None
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = slp.launch_count()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = {"pi_iters": 0, "krylov_iters": 0, "ir_iters": 0, "rebuilds": 0, "policy_changes": 0}
+    for i in range(1, args.steps + 1):
+        st = s.step(u, (args.warmup + i) * dt, dt)
+        for kk in stats:
+            stats[kk] += st[kk]
+        if i == compare_at:
+            u_cmp = u.clone()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = slp.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    barrier()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * n * args.steps / (ms / 1e3)
+
+    # ---- roofline: the fine-level FP32 operator (matrix-free SpMV), timed alone with events
+    m = n - 2
+    x = torch.zeros((n, n), dtype=torch.float32, device=dev)
+    x[1:-1, 1:-1] = torch.rand((m, m), device=dev)
+    y = torch.zeros_like(x)
+    for _ in range(3):
+        s.apply(0, x, y)
+    reps = 50
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    timing = "CUDA graph of 50 back-to-back launches, CUDA events around the replay"
+    try:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(reps):
+                s.apply(0, x, y)
+        graph.replay()
+        torch.cuda.synchronize()
+        r0.record(stream)
+        graph.replay()
+        r1.record(stream)
+        torch.cuda.synchronize()
+    except Exception:
+        timing = "50 stream-ordered launches, CUDA events around them"
+        r0.record(stream)
+        for _ in range(reps):
+            s.apply(0, x, y)
+        r1.record(stream)
+        torch.cuda.synchronize()
+    kern_ms = r0.elapsed_time(r1) / reps
+    bytes_per_launch = m * m * (1 + 4 + 4)   # policy byte, x_j, y_j (taps hit L1/L2)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_launch / (kern_ms / 1e3) / 1e9
+    roofline = {"kernel": "k_fine_op<float,OP_APPLY> (fine-level matrix-free operator, FP32)",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                "traffic": traffic_record("k_fine_op_f32_apply_2049"),
+                "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": kern_ms,
+                "timing": timing}
+    del s
+    torch.cuda.empty_cache()
+
+    # ---- e2e through the public API with host-resident state
+    se = make(1)
+    ue = u_after_warm.clone()
+    # replay the warm-up so that the handle's policy matches the timed run's starting point
+    ue.copy_(g)
+    for i in range(1, args.warmup + 1):
+        se.step(ue, i * dt, dt)
+    host = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    host.copy_(ue)
+    ke = min(args.e2e_steps, args.steps)
+    torch.cuda.synchronize()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for i in range(1, ke + 1):
+        ue.copy_(host, non_blocking=True)
+        se.step(ue, (args.warmup + i) * dt, dt)
+        host.copy_(ue, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = h0.elapsed_time(h1)
+    e2e = {"value": world * n * n * ke / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8, "steps": ke}
+    del se
+    torch.cuda.empty_cache()
+
+    # ---- FP64 path on the first steps of the same timed range
+    fp64 = None
+    err = None
+    if not args.no_fp64:
+        s64 = make(0)
+        u64 = g.clone()
+        for i in range(1, args.warmup + 1):
+            s64.step(u64, i * dt, dt)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for i in range(1, compare_at + 1):
+            s64.step(u64, (args.warmup + i) * dt, dt)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = f0.elapsed_time(f1)
+        fp64 = {"value": n * n * compare_at / (f_ms / 1e3), "unit": UNIT, "steps": compare_at,
+                "ms_per_step": f_ms / compare_at}
+        if u_cmp is not None:
+            err = float((u_cmp - u64).abs().max() / u64.abs().max())
+        del s64
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_record()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"uncertain-correlation HJB, {n}x{n} grid, 65 controls rho in "
+                                   f"[-0.95,0.95], s1={prob.s1:.4f} s2={prob.s2:.4f} (seed 0), "
+                                   f"dt=1/128, steps {args.warmup + 1}..{args.warmup + args.steps}",
+                       "precision": "mixed: FP32 V-cycle/inner BiCGSTAB, FP64 residual, argmin "
+                                    "decision and refinement",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "working set > L2 (no flush needed)",
+                       "levels": int(make_levels(n)), "pi_iters": stats["pi_iters"],
+                       "krylov_iters": stats["krylov_iters"], "ir_iters": stats["ir_iters"],
+                       "rebuilds": stats["rebuilds"]},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "fp64": fp64,
+            "mixed_vs_fp64_rel_err": err,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def make_levels(n):
+    L, nn = 1, n
+    while nn > 5 and (nn - 1) % 2 == 0:
+        nn = (nn + 1) // 2
+        L += 1
+    return L
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * sl_hjb.h - C ABI of a GB300 (sm_103a) solver for the implicit truncated LISL Scheme 2
+ * applied to two-dimensional Hamilton-Jacobi-Bellman equations
+ *
+ *     u_t - inf_{k} { tr(a^k D^2 u) + b^k . Du + c^k u + f^k(t, x) } = 0,  a^k = sigma^k sigma^k^T / 2,
+ *
+ * on a square grid with Dirichlet data psi and initial data g (Section 1, Eqs. 1.1-1.3).
+ *
+ * Each implicit Euler step (theta = 1 in Eq. FullScheme) solves the nonlinear system
+ * max_k (A^k X - F^k) = 0 (Eq. nonlinear_sys) by Howard policy iteration. Each iteration runs
+ * two phases:
+ *   - a per-node argmin over the discrete control set of the truncated wide-stencil operator
+ *     (Section 2.1, Proposition 2.2, Eq. Lhat);
+ *   - a BiCGSTAB solve at the fixed policy, right-preconditioned by a geometric multigrid
+ *     V-cycle with Galerkin coarse operators (Section 3.3).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: nx == ny = n nodes per dimension, boundary included, uniform spacing
+ *     h = (x_hi - x_lo) / (n - 1) = (y_hi - y_lo) / (n - 1).  Node (i1, i2) sits at
+ *     (x_lo + h i1, y_lo + h i2).
+ *   - Full-grid arrays are row-major [i2][i1] (x1 runs fastest), n*n entries.
+ *   - Policy arrays cover the (n-2)^2 interior nodes, row-major, one uint8_t control index
+ *     per node.
+ *   - Every pointer named *_dev is device memory; the caller owns it, and the library never
+ *     frees it.  The handle owns all workspace; sl_hjb_create allocates it and
+ *     sl_hjb_destroy frees it.
+ *   - Work is ordered on the given CUDA stream (a cudaStream_t passed as void*; NULL = legacy
+ *     default stream).  Calls that return iteration counts or statistics synchronise that
+ *     stream before returning.
+ *   - Errors: every call returns an sl_status.  The first failure is recorded in the handle;
+ *     sl_hjb_last_error returns a message.  No call traps or hangs the GPU: iteration loops
+ *     are capped and report SL_ENOCONV_* when the cap is reached.
+ */
+#ifndef SL_HJB_H
+#define SL_HJB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sl_hjb sl_hjb;
+
+typedef enum {
+  SL_OK = 0,
+  SL_EINVAL = 1,          /* invalid argument or unsupported configuration */
+  SL_ENOMEM = 2,          /* device allocation failed */
+  SL_ECUDA = 3,           /* a CUDA runtime call failed */
+  SL_ECFL = 4,            /* dt * c^k > 1 for some control (Proposition 2.4, theta = 1) */
+  SL_ENOCONV_PI = 5,      /* Howard iteration reached pi_max */
+  SL_ENOCONV_KRYLOV = 6,  /* BiCGSTAB / refinement reached its iteration cap */
+  SL_EBREAKDOWN = 7,      /* BiCGSTAB breakdown (rho or omega vanished) */
+  SL_ENAN = 8,            /* a NaN or Inf appeared in a residual or control value */
+  SL_ETIMEOUT = 9         /* reserved: a bounded device-side wait gave up */
+} sl_status;
+
+/* Grid of Eq. 1.1 (Section 2.4: "N_x x N_x equispaced nodes"). */
+typedef struct {
+  int nx, ny;                     /* nodes per dimension, boundary included; nx == ny >= 5 */
+  double x_lo, x_hi, y_lo, y_hi;  /* square cells: x_hi - x_lo == y_hi - y_lo */
+} sl_grid;
+
+/* Discrete control set {k = 0..K-1} with x-independent coefficients (Eq. def_L).
+ * Column p of sigma^k (a 2 x P matrix) is (sigma[(k*2+0)*P + p], sigma[(k*2+1)*P + p]).
+ * Scheme 2 (Section 1) uses the directions +-sqrt(h) sigma_p and h b. */
+typedef struct {
+  int K;                /* 1 .. 255 */
+  int P;                /* 1 .. 4 */
+  const double *sigma;  /* host, K*2*P */
+  const double *b;      /* host, K*2 drift, or NULL for b = 0 */
+  const double *c;      /* host, K discount, or NULL for c = 0 */
+} sl_controls;
+
+/* Time factors tau(t) of the separable source and boundary data. */
+enum { SL_TAU_ONE = 0, SL_TAU_EXP = 1 /* exp(rate t) */, SL_TAU_LINEAR = 2 /* t */ };
+
+/* Source f^k(t, x) = sum_m phi[k*nf + m] sum_q tau_q(t) G[((m*nq + q)*n + i2)*n + i1]
+ * and boundary data psi(t, x) = sum_q tau'_q(t) Psi[(q*n + i2)*n + i1] (boundary entries).
+ * G and Psi stay in the caller's device memory and must outlive the handle. */
+typedef struct {
+  int nf, nq;
+  const double *phi;       /* host, K*nf */
+  const double *G_dev;     /* device, nf*nq*n*n */
+  const int *tau_kind;     /* host, nq */
+  const double *tau_rate;  /* host, nq */
+  int npsi;                /* 0: psi = 0 */
+  const double *Psi_dev;   /* device, npsi*n*n, or NULL */
+  const int *psi_kind;     /* host, npsi */
+  const double *psi_rate;  /* host, npsi */
+} sl_source;
+
+typedef struct {
+  int precision;        /* 0: FP64 throughout.  1: mixed - FP32 V-cycle, FP32 preconditioner
+                           weights and FP32 inner BiCGSTAB inside FP64 iterative refinement;
+                           FP64 outer residual and FP64 policy decision. */
+  int levels;           /* multigrid levels including the finest; 0 = coarsen to 5 x 5 */
+  int nu1, nu2;         /* damped-Jacobi pre- / post-smoothing sweeps */
+  double omega;         /* Jacobi weight */
+  double krylov_tol;    /* stop when ||F - A X||_2 <= krylov_tol ||F||_2 and
+                           ||F - A X||_inf <= krylov_tol ||F||_inf (true FP64 residual).  With
+                           c = 0, A^alpha has row sums >= 1, so one step's error is at most
+                           krylov_tol ||F||_inf and n steps add at most n times that. */
+  int kry_max;          /* BiCGSTAB iterations per solve (FP64) or per refinement (mixed) */
+  double inner_tol;     /* mixed: relative tolerance of each inner FP32 solve */
+  int ir_max;           /* mixed: refinement sweeps per solve */
+  double pi_tol;        /* Howard stop: ||X^m - X^{m-1}||_inf <= pi_tol max(1, ||X^m||_inf) */
+  int pi_max;           /* Howard iterations per step */
+  double tie_rel;       /* argmin picks the lowest k with v_k <= v_min + tie_rel max(1, |v_min|) */
+  int argmin_screen;    /* 1: screen controls in FP32 with a rigorous rounding bound, then
+                           decide in FP64 among the survivors (identical result); 0: all FP64 */
+  double rebuild_frac;  /* rebuild the Galerkin hierarchy when more than rebuild_frac * N
+                           rows changed control since the last build (0: on any change) */
+} sl_opts;
+
+typedef struct {
+  int steps;                  /* implicit steps taken */
+  int pi_iters;               /* Howard iterations, summed over steps */
+  int krylov_iters;           /* BiCGSTAB iterations (inner ones in mixed mode) */
+  int ir_iters;               /* refinement sweeps (mixed mode) */
+  int rebuilds;               /* Galerkin hierarchy builds */
+  long long policy_changes;   /* rows whose control changed, summed over improvements */
+  long long explicit_rows;    /* coarse rows stored explicitly in the last build */
+  double res_final;           /* last relative residual ||F - A X||_2 / ||F||_2 */
+  double t_argmin_ms, t_hier_ms, t_solve_ms;  /* host-timed phases (sync points) */
+} sl_stats;
+
+/* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
+ * krylov_tol 1e-12, kry_max 200, inner_tol 1e-5, ir_max 30, pi_tol 1e-10, pi_max 100,
+ * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0. */
+void sl_opts_default(sl_opts *o);
+
+/* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every
+ * boundary-distance class in FP64 (Proposition 2.2: truncation factors mu, weights A, B;
+ * bilinear taps) and allocates the workspace.  Validates the grid (square, n = 2^j + 1 when
+ * levels > 1), K, P and the options.  Returns SL_EINVAL on bad input, SL_ENOMEM / SL_ECUDA on
+ * device failure.  *h is NULL on failure. */
+sl_status sl_hjb_create(sl_hjb **h, const sl_grid *grid, const sl_controls *ctrl,
+                        const sl_source *src, const sl_opts *opts, void *stream);
+
+/* One implicit step from t_n - dt to t_n (Eq. FullScheme, theta = 1) with Howard iteration.
+ * u_dev (n*n, FP64): in U^{n-1} (boundary ignored), out U^n with psi(t_n) on the boundary.
+ * The policy of the previous step is the starting policy; the first step starts from an
+ * improvement on U^{n-1}.  policy_out_dev ((n-2)^2 uint8) receives the final policy if not
+ * NULL.  stats (host, may be NULL) is overwritten with this step's counts.  Returns
+ * SL_ECFL if dt * c^k > 1, SL_ENOCONV_PI / SL_ENOCONV_KRYLOV / SL_EBREAKDOWN / SL_ENAN on
+ * failure of an iteration (u_dev then holds the last iterate). */
+sl_status sl_hjb_step(sl_hjb *h, double *u_dev, double t_n, double dt, uint8_t *policy_out_dev,
+                      sl_stats *stats, void *stream);
+
+/* n_steps uniform implicit steps from t0 to t0 + T; u_dev in: g, out: U(t0 + T).
+ * stats accumulates over the steps. */
+sl_status sl_hjb_solve(sl_hjb *h, double *u_dev, double t0, double T, int n_steps,
+                       uint8_t *policy_out_dev, sl_stats *stats, void *stream);
+
+const char *sl_hjb_last_error(const sl_hjb *h);
+void sl_hjb_destroy(sl_hjb *h);
+
+/* ---- Stage entry points: single phases of a step, for parity checks and diagnostics ---- */
+
+/* Policy improvement (row-wise linear search of Eq. nonlinear_sys) on x_ext_dev (n*n FP64,
+ * psi on the boundary) at time t: v_k(j) = (L^k X)_j + c^k X_j + f^k(t, x_j); the new policy
+ * becomes the handle's policy and is copied to policy_out_dev if not NULL.  *changes
+ * (host, may be NULL) receives the number of rows whose control changed. */
+sl_status sl_hjb_improve(sl_hjb *h, const double *x_ext_dev, double t, uint8_t *policy_out_dev,
+                         long long *changes, void *stream);
+
+/* Replaces the handle's policy ((n-2)^2 uint8, device). */
+sl_status sl_hjb_set_policy(sl_hjb *h, const uint8_t *policy_dev, void *stream);
+
+/* Builds the Galerkin hierarchy A_{l+1} = R A_l P (bilinear P, full-weighting R) for the
+ * current policy and step size dt, in the precision of opts.precision (FP64, or FP32
+ * copies in mixed mode). */
+sl_status sl_hjb_build_hierarchy(sl_hjb *h, double dt, void *stream);
+
+/* y = A_level x on level `level` (0 = finest) with the current policy / hierarchy.
+ * x_dev, y_dev: n_l*n_l full-grid vectors of that level, FP64 (precision 0) or FP32
+ * (precision 1); x has zero boundary entries, y's boundary entries are left untouched.
+ * Stream-ordered and asynchronous (no host synchronisation), so it can be captured in a
+ * CUDA graph. */
+sl_status sl_hjb_apply(sl_hjb *h, int level, int precision, const void *x_dev, void *y_dev,
+                       void *stream);
+
+/* One V(nu1, nu2) cycle from x = 0 for A_0 x = b (the preconditioner application).
+ * b_dev, x_dev: n*n full-grid vectors, FP64 (precision 0) or FP32 (precision 1). */
+sl_status sl_hjb_vcycle(sl_hjb *h, int precision, const void *b_dev, void *x_dev, void *stream);
+
+/* Solves A^alpha X = F^alpha of the step at time t with step dt for the current policy,
+ * starting from x_ext_dev (n*n FP64, overwritten with the solution and psi(t) on the
+ * boundary); u_prev_dev is U^{n-1}.  Uses BiCGSTAB (precision 0) or refinement (1). */
+sl_status sl_hjb_linear_solve(sl_hjb *h, const double *u_prev_dev, double *x_ext_dev, double t,
+                              double dt, sl_stats *stats, void *stream);
+
+/* Sizes of level `level` of the current hierarchy: nodes per dimension, stored explicit
+ * rows, and the number of non-zeros (class rows counted with their table's non-zeros). */
+sl_status sl_hjb_level_info(const sl_hjb *h, int level, int *n, long long *explicit_rows,
+                            long long *nnz);
+
+/* Number of levels in use. */
+int sl_hjb_num_levels(const sl_hjb *h);
+
+/* Number of CUDA kernel launches the library has issued since it was loaded, over all
+ * handles (host-side counter; used to report how many of the library's kernels ran in a
+ * timed region). */
+long long sl_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SL_HJB_H */

@@ -1,0 +1,274 @@
+"""GB300 (sm_103a) solver for HJB equations with the implicit truncated LISL Scheme 2.
+
+Python binding of the C ABI in include/sl_hjb.h (ctypes; argument marshalling only).  Every
+step of the solve runs in the library's CUDA kernels; PyTorch provides device memory and
+streams.  Importing this package does not need a GPU; loading the library does need the
+built libslhjb.so, and any call fails loudly when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libslhjb.so")
+
+SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ECFL = 0, 1, 2, 3, 4
+SL_ENOCONV_PI, SL_ENOCONV_KRYLOV, SL_EBREAKDOWN, SL_ENAN, SL_ETIMEOUT = 5, 6, 7, 8, 9
+STATUS_NAMES = {0: "SL_OK", 1: "SL_EINVAL", 2: "SL_ENOMEM", 3: "SL_ECUDA", 4: "SL_ECFL",
+                5: "SL_ENOCONV_PI", 6: "SL_ENOCONV_KRYLOV", 7: "SL_EBREAKDOWN", 8: "SL_ENAN",
+                9: "SL_ETIMEOUT"}
+
+EXPORTED = ["sl_opts_default", "sl_hjb_create", "sl_hjb_step", "sl_hjb_solve",
+            "sl_hjb_last_error", "sl_hjb_destroy", "sl_hjb_improve", "sl_hjb_set_policy",
+            "sl_hjb_build_hierarchy", "sl_hjb_apply", "sl_hjb_vcycle", "sl_hjb_linear_solve",
+            "sl_hjb_level_info", "sl_hjb_num_levels", "sl_launch_count"]
+
+
+class SlGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("x_lo", ctypes.c_double),
+                ("x_hi", ctypes.c_double), ("y_lo", ctypes.c_double), ("y_hi", ctypes.c_double)]
+
+
+class SlControls(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("P", ctypes.c_int), ("sigma", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("c", ctypes.c_void_p)]
+
+
+class SlSource(ctypes.Structure):
+    _fields_ = [("nf", ctypes.c_int), ("nq", ctypes.c_int), ("phi", ctypes.c_void_p),
+                ("G_dev", ctypes.c_void_p), ("tau_kind", ctypes.c_void_p),
+                ("tau_rate", ctypes.c_void_p), ("npsi", ctypes.c_int), ("Psi_dev", ctypes.c_void_p),
+                ("psi_kind", ctypes.c_void_p), ("psi_rate", ctypes.c_void_p)]
+
+
+class SlOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("levels", ctypes.c_int), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("krylov_tol", ctypes.c_double),
+                ("kry_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("ir_max", ctypes.c_int),
+                ("pi_tol", ctypes.c_double), ("pi_max", ctypes.c_int), ("tie_rel", ctypes.c_double),
+                ("argmin_screen", ctypes.c_int), ("rebuild_frac", ctypes.c_double)]
+
+
+class SlStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("pi_iters", ctypes.c_int), ("krylov_iters", ctypes.c_int),
+                ("ir_iters", ctypes.c_int), ("rebuilds", ctypes.c_int),
+                ("policy_changes", ctypes.c_longlong), ("explicit_rows", ctypes.c_longlong),
+                ("res_final", ctypes.c_double), ("t_argmin_ms", ctypes.c_double),
+                ("t_hier_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Loads libslhjb.so (build it with paper_1605_04821_gb300.build first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run `python -m paper_1605_04821_gb300.build` "
+                           "(the solver has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "sl_opts_default": (None, [ctypes.POINTER(SlOpts)]),
+        "sl_hjb_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(SlGrid), ctypes.POINTER(SlControls),
+                              ctypes.POINTER(SlSource), ctypes.POINTER(SlOpts), vp]),
+        "sl_hjb_step": (i, [vp, vp, d, d, vp, ctypes.POINTER(SlStats), vp]),
+        "sl_hjb_solve": (i, [vp, vp, d, d, i, vp, ctypes.POINTER(SlStats), vp]),
+        "sl_hjb_last_error": (ctypes.c_char_p, [vp]),
+        "sl_hjb_destroy": (None, [vp]),
+        "sl_hjb_improve": (i, [vp, vp, d, vp, ctypes.POINTER(ll), vp]),
+        "sl_hjb_set_policy": (i, [vp, vp, vp]),
+        "sl_hjb_build_hierarchy": (i, [vp, d, vp]),
+        "sl_hjb_apply": (i, [vp, i, i, vp, vp, vp]),
+        "sl_hjb_vcycle": (i, [vp, i, vp, vp, vp]),
+        "sl_hjb_linear_solve": (i, [vp, vp, vp, d, d, ctypes.POINTER(SlStats), vp]),
+        "sl_hjb_level_info": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ll), ctypes.POINTER(ll)]),
+        "sl_hjb_num_levels": (i, [vp]),
+        "sl_launch_count": (ll, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library since it was loaded."""
+    return int(load().sl_launch_count())
+
+
+def default_opts(**kw) -> SlOpts:
+    o = SlOpts()
+    load().sl_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Solver:
+    """Owns one library handle.  All tensors are CUDA tensors on the current device.
+
+    G: (nf, nq, n, n) float64 source tables; Psi: (npsi, n, n) float64 or None.  The handle
+    keeps references to G and Psi, which must stay alive and unchanged.
+    """
+
+    def __init__(self, n: int, lo: float, hi: float, sigma: np.ndarray, phi: np.ndarray, G,
+                 tau_kind, tau_rate, Psi=None, psi_kind=None, psi_rate=None, b=None, c=None,
+                 opts: Optional[SlOpts] = None, stream=None, **opt_kw):
+        import torch
+        lib = load()
+        self._lib = lib
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        K, _, P = sigma.shape
+        self.n, self.K, self.P = n, K, P
+        self._keep = []
+
+        def host(a, dtype):
+            arr = np.ascontiguousarray(a, dtype=dtype)
+            self._keep.append(arr)
+            return arr.ctypes.data_as(ctypes.c_void_p)
+
+        grid = SlGrid(n, n, lo, hi, lo, hi)
+        ctrl = SlControls(K, P, host(sigma, np.float64),
+                          host(b, np.float64) if b is not None else None,
+                          host(c, np.float64) if c is not None else None)
+        G = G.contiguous()
+        assert G.is_cuda and G.dtype == torch.float64 and G.shape[2:] == (n, n)
+        nf, nq = G.shape[0], G.shape[1]
+        self._G = G
+        npsi = 0
+        psi_ptr = None
+        if Psi is not None:
+            Psi = Psi.contiguous()
+            self._Psi = Psi
+            npsi = Psi.shape[0]
+            psi_ptr = _ptr(Psi)
+        src = SlSource(nf, nq, host(phi, np.float64), _ptr(G), host(tau_kind, np.int32),
+                       host(tau_rate, np.float64), npsi, psi_ptr,
+                       host(psi_kind, np.int32) if npsi else None,
+                       host(psi_rate, np.float64) if npsi else None)
+        self.opts = opts if opts is not None else default_opts(**opt_kw)
+        h = ctypes.c_void_p()
+        st = lib.sl_hjb_create(ctypes.byref(h), ctypes.byref(grid), ctypes.byref(ctrl),
+                               ctypes.byref(src), ctypes.byref(self.opts), _stream(stream))
+        if st != SL_OK:
+            raise SLError(st, "sl_hjb_create failed (see stderr)")
+        self.h = h
+        self.m = n - 2
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.sl_hjb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != SL_OK:
+            raise SLError(st, self._lib.sl_hjb_last_error(self.h).decode())
+
+    def step(self, u, t_n: float, dt: float, policy_out=None, stream=None) -> dict:
+        s = SlStats()
+        self._check(self._lib.sl_hjb_step(self.h, _ptr(u), t_n, dt,
+                                          _ptr(policy_out) if policy_out is not None else None,
+                                          ctypes.byref(s), _stream(stream)))
+        return s.as_dict()
+
+    def solve(self, u, t0: float, T: float, n_steps: int, policy_out=None, stream=None) -> dict:
+        s = SlStats()
+        self._check(self._lib.sl_hjb_solve(self.h, _ptr(u), t0, T, n_steps,
+                                           _ptr(policy_out) if policy_out is not None else None,
+                                           ctypes.byref(s), _stream(stream)))
+        return s.as_dict()
+
+    def improve(self, x_ext, t: float, policy_out=None, stream=None) -> int:
+        ch = ctypes.c_longlong(0)
+        self._check(self._lib.sl_hjb_improve(self.h, _ptr(x_ext), t,
+                                             _ptr(policy_out) if policy_out is not None else None,
+                                             ctypes.byref(ch), _stream(stream)))
+        return ch.value
+
+    def set_policy(self, policy, stream=None):
+        self._check(self._lib.sl_hjb_set_policy(self.h, _ptr(policy), _stream(stream)))
+
+    def build_hierarchy(self, dt: float, stream=None):
+        self._check(self._lib.sl_hjb_build_hierarchy(self.h, dt, _stream(stream)))
+
+    def apply(self, level: int, x, y, stream=None):
+        import torch
+        prec = 0 if x.dtype == torch.float64 else 1
+        self._check(self._lib.sl_hjb_apply(self.h, level, prec, _ptr(x), _ptr(y), _stream(stream)))
+
+    def vcycle(self, b, x, stream=None):
+        import torch
+        prec = 0 if b.dtype == torch.float64 else 1
+        self._check(self._lib.sl_hjb_vcycle(self.h, prec, _ptr(b), _ptr(x), _stream(stream)))
+
+    def linear_solve(self, u_prev, x_ext, t: float, dt: float, stream=None) -> dict:
+        s = SlStats()
+        self._check(self._lib.sl_hjb_linear_solve(self.h, _ptr(u_prev), _ptr(x_ext), t, dt,
+                                                  ctypes.byref(s), _stream(stream)))
+        return s.as_dict()
+
+    def num_levels(self) -> int:
+        return self._lib.sl_hjb_num_levels(self.h)
+
+    def level_info(self, level: int):
+        n = ctypes.c_int(0)
+        ex = ctypes.c_longlong(0)
+        nnz = ctypes.c_longlong(0)
+        self._check(self._lib.sl_hjb_level_info(self.h, level, ctypes.byref(n), ctypes.byref(ex),
+                                                ctypes.byref(nnz)))
+        return n.value, ex.value
+
+
+def solver_from_problem(prob, device=None, stream=None, **opt_kw) -> Solver:
+    """Marshals a `workloads.Problem` with a separable source into a Solver."""
+    import torch
+    if prob.G is None:
+        raise ValueError("the library needs the separable source form (phi, G, tau)")
+    dev = device or torch.device("cuda")
+    G = torch.as_tensor(prob.G, dtype=torch.float64, device=dev)
+    psi = prob.psi_fn(0.0)
+    Psi = None
+    kw = {}
+    if np.any(psi != 0.0):
+        Psi = torch.as_tensor(psi[None], dtype=torch.float64, device=dev)
+        kw = dict(Psi=Psi, psi_kind=np.array([0], dtype=np.int32), psi_rate=np.array([0.0]))
+    return Solver(prob.n, prob.lo, prob.hi, prob.sigma, prob.phi, G,
+                  np.asarray(prob.tau_kind, dtype=np.int32), np.asarray(prob.tau_rate, dtype=np.float64),
+                  b=prob.drift, c=prob.c, stream=stream, **kw, **opt_kw)

@@ -1,0 +1,903 @@
+// sl_api.cu - C ABI and host orchestration: Howard policy iteration around a
+// multigrid-preconditioned BiCGSTAB (FP64) or FP64 iterative refinement of an FP32
+// BiCGSTAB with an FP32 V-cycle (mixed).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sl_hjb.h"
+#include "sl_geometry.h"
+#include "sl_launch.h"
+
+using namespace sl;
+
+namespace {
+
+struct CoarseBuf {
+  int n = 0, m = 0, R = 0, win = 0, cap = 0, nexpl = 0, ctmax = 0;
+  int32_t *cls = nullptr, *erow = nullptr, *clin = nullptr, *coff = nullptr, *cnt = nullptr;
+  double *ewin64 = nullptr, *cw64 = nullptr, *cdiag64 = nullptr;
+  float *ewin32 = nullptr, *cw32 = nullptr, *cdiag32 = nullptr;
+  long long class_nnz_sum = 0;  // sum over class rows of their table's non-zeros
+  std::vector<int> cnt_host;
+};
+
+template <typename T> T *pick(double *a, float *b);
+template <> double *pick<double>(double *a, float *) { return a; }
+template <> float *pick<float>(double *, float *b) { return b; }
+
+struct VBuf {  // V-cycle vectors of one level
+  double *x64 = nullptr, *t64 = nullptr, *r64 = nullptr, *b64 = nullptr;
+  float *x32 = nullptr, *t32 = nullptr, *r32 = nullptr, *b32 = nullptr;
+};
+
+struct KBuf {  // BiCGSTAB vectors on the finest level
+  double *r64 = nullptr, *rh64 = nullptr, *p64 = nullptr, *v64 = nullptr, *s64 = nullptr,
+         *t64 = nullptr, *ph64 = nullptr, *sh64 = nullptr;
+  float *r32 = nullptr, *rh32 = nullptr, *p32 = nullptr, *v32 = nullptr, *s32 = nullptr,
+        *t32 = nullptr, *ph32 = nullptr, *sh32 = nullptr, *e32 = nullptr;
+};
+
+}  // namespace
+
+struct sl_hjb {
+  int n = 0, m = 0, K = 0, P = 0, nf = 0, nq = 0, npsi = 0;
+  double h = 0;
+  sl_opts o{};
+  std::vector<double> phi, phimax, tau_rate, psi_rate, cvec;
+  std::vector<int> tau_kind, psi_kind;
+  const double *G = nullptr, *Psi = nullptr;
+  FineTabHost ft;
+  FineTab tab{};
+  // device tables
+  int32_t *d_lin = nullptr, *d_slin = nullptr, *d_off = nullptr;
+  double *d_w64 = nullptr, *d_W64 = nullptr, *d_ws64 = nullptr, *d_c64 = nullptr, *d_Wmaxc = nullptr;
+  float *d_w32 = nullptr, *d_W32 = nullptr, *d_ws32 = nullptr, *d_c32 = nullptr;
+  uint8_t *d_nt = nullptr;
+  double *d_phi = nullptr, *d_phimax = nullptr, *d_tau = nullptr, *d_tpsi = nullptr;
+  float *d_phi32 = nullptr;
+  int halo = 0, SW = 0, SH = 0;
+  // step state (full-grid FP64 vectors)
+  double *X = nullptr, *Xb = nullptr, *Uprev = nullptr, *F = nullptr, *R = nullptr, *Xpi = nullptr,
+         *Fvec = nullptr;
+  float *F32 = nullptr;
+  uint8_t *policy = nullptr;
+  bool have_policy = false;
+  // hierarchy
+  int L = 1;
+  CoarseBuf cl[kMaxLevels];
+  VBuf vb[kMaxLevels];
+  KBuf kb;
+  double *cwork = nullptr, *Ainv64 = nullptr;
+  float *Ainv32 = nullptr;
+  bool hier_valid = false, class_valid = false;
+  double hier_dt = -1.0, class_dt = -1.0;
+  long long changes_since_build = 0;
+  // reductions
+  BicgScalars *S = nullptr, *S32 = nullptr, *hS = nullptr;
+  double *partials = nullptr, *d_maxd = nullptr, *h_maxd = nullptr;
+  unsigned *counter = nullptr;
+  unsigned long long *d_changes = nullptr, *h_changes = nullptr;
+  int *d_flags = nullptr, *h_flags = nullptr, *d_count = nullptr, *h_count = nullptr;
+  std::vector<void *> allocs;
+  std::string err;
+  sl_status sticky = SL_OK;
+};
+
+namespace {
+
+sl_status fail(sl_hjb *h, sl_status st, const std::string &msg) {
+  if (h) {
+    if (h->sticky == SL_OK) h->sticky = st;
+    h->err = msg;
+  }
+  return st;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(h, SL_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+
+template <typename T>
+sl_status dalloc(sl_hjb *h, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+  if (e != cudaSuccess) return fail(h, SL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->allocs.push_back(*p);
+  e = cudaMemset(*p, 0, count * sizeof(T));
+  if (e != cudaSuccess) return fail(h, SL_ECUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+  return SL_OK;
+}
+
+#define AL(ptr, count)                             \
+  do {                                             \
+    sl_status s_ = dalloc(h, &(ptr), (count));     \
+    if (s_ != SL_OK) return s_;                    \
+  } while (0)
+
+template <typename T>
+sl_status upload(sl_hjb *h, T **p, const std::vector<T> &v) {
+  AL(*p, v.size());
+  if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SL_OK;
+}
+
+#define UP(ptr, vec)                               \
+  do {                                             \
+    sl_status s_ = upload(h, &(ptr), (vec));       \
+    if (s_ != SL_OK) return s_;                    \
+  } while (0)
+
+double tau_eval(int kind, double rate, double t) {
+  if (kind == SL_TAU_ONE) return 1.0;
+  if (kind == SL_TAU_EXP) return std::exp(rate * t);
+  return t;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+size_t NN(const sl_hjb *h, int l) { return size_t(h->cl[l].n) * h->cl[l].n; }
+
+// ---------------------------------------------------------------------- per-step tables
+sl_status coef(sl_hjb *h, double t, double *Xext, cudaStream_t s) {
+  std::vector<double> tv(std::max(1, h->nq) + std::max(1, h->npsi), 0.0);
+  for (int q = 0; q < h->nq; ++q) tv[q] = tau_eval(h->tau_kind[q], h->tau_rate[q], t);
+  for (int q = 0; q < h->npsi; ++q) tv[h->nq + q] = tau_eval(h->psi_kind[q], h->psi_rate[q], t);
+  CK(cudaMemcpyAsync(h->d_tau, tv.data(), tv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  // the copy source is a host temporary: make sure it has been consumed
+  CK(cudaStreamSynchronize(s));
+  launch_coef(h->G, h->nf, h->nq, h->d_tau, h->Psi, h->npsi, h->d_tau + h->nq, h->n, h->F, h->F32,
+              Xext, h->Xb, s);
+  CK(cudaGetLastError());
+  return SL_OK;
+}
+
+// ---------------------------------------------------------------------- argmin
+sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_t s) {
+  ArgminArgs a{};
+  a.tab = h->tab;
+  a.slin = h->d_slin;
+  a.off = h->d_off;
+  a.X = Xext;
+  a.F = h->F;
+  a.F32 = h->F32;
+  a.phi = h->d_phi;
+  a.phi32 = h->d_phi32;
+  a.phimax = h->d_phimax;
+  a.nf = h->nf;
+  a.tie_rel = h->o.tie_rel;
+  a.cmax = 0.0;
+  for (double c : h->cvec) a.cmax = std::max(a.cmax, std::fabs(c));
+  a.Wmax_class = h->d_Wmaxc;
+  a.policy = h->policy;
+  a.changes = h->d_changes;
+  a.flags = h->d_flags;
+  a.halo = h->halo;
+  a.SW = h->SW;
+  a.SH = h->SH;
+  a.screen = h->o.argmin_screen;
+  CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+  CK(launch_argmin(a, s));
+  CK(cudaMemcpyAsync(h->h_changes, h->d_changes, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*h->h_flags & 1) return fail(h, SL_ENAN, "non-finite control value in the policy improvement");
+  if (changes) *changes = (long long)*h->h_changes;
+  h->have_policy = true;
+  return SL_OK;
+}
+
+// ---------------------------------------------------------------------- hierarchy
+template <typename T>
+CoarseLev<T> lev_view(sl_hjb *h, int l) {
+  CoarseBuf &c = h->cl[l];
+  CoarseLev<T> L{};
+  L.n = c.n;
+  L.m = c.m;
+  L.R = c.R;
+  L.win = c.win;
+  L.cls = c.cls;
+  L.clin = c.clin;
+  L.cw = pick<T>(c.cw64, c.cw32);
+  L.cnt = c.cnt;
+  L.cdiag = pick<T>(c.cdiag64, c.cdiag32);
+  L.ctmax = c.ctmax;
+  L.ewin = pick<T>(c.ewin64, c.ewin32);
+  L.erow = c.erow;
+  L.cap = c.cap;
+  return L;
+}
+
+// Translation-invariant class stencils S_k^l (host, FP64), rebuilt when dt changes.
+sl_status build_class_tables(sl_hjb *h, double dt) {
+  const bool interior_exists = (h->n - 1 >= 2 * h->ft.B);
+  std::vector<std::vector<double>> prev(h->K);
+  int Rprev = h->ft.R0;
+  if (interior_exists)
+    for (int k = 0; k < h->K; ++k) prev[k] = fine_interior_window(h->ft, k, dt);
+  for (int l = 1; l < h->L; ++l) {
+    CoarseBuf &c = h->cl[l];
+    std::vector<std::vector<double>> cur(h->K);
+    std::vector<int32_t> lin, off;
+    std::vector<double> w, diag(h->K, 1.0);
+    std::vector<int> cnt(h->K, 0);
+    int ctmax = 1;
+    std::vector<std::vector<std::pair<int, double>>> taps(h->K);
+    const int Wd = 2 * c.R + 1;
+    for (int k = 0; k < h->K; ++k) {
+      if (!interior_exists) break;
+      cur[k] = rap_class_window(prev[k], Rprev, c.R);
+      for (int e = 0; e < Wd * Wd; ++e) {
+        const double v = cur[k][e];
+        if (v == 0.0) continue;
+        taps[k].push_back({e, v});
+        if (e == c.R * Wd + c.R) diag[k] = v;
+      }
+      ctmax = std::max(ctmax, int(taps[k].size()));
+    }
+    lin.assign(size_t(h->K) * ctmax, 0);
+    off.assign(size_t(h->K) * ctmax, 0);
+    w.assign(size_t(h->K) * ctmax, 0.0);
+    for (int k = 0; k < h->K; ++k) {
+      cnt[k] = int(taps[k].size());
+      for (size_t t = 0; t < taps[k].size(); ++t) {
+        const int e = taps[k][t].first;
+        const int dy = e / Wd - c.R, dx = e % Wd - c.R;
+        lin[size_t(k) * ctmax + t] = dy * c.n + dx;
+        off[size_t(k) * ctmax + t] = (dy << 16) | (dx & 0xffff);
+        w[size_t(k) * ctmax + t] = taps[k][t].second;
+      }
+    }
+    if (c.ctmax < ctmax) {
+      // (re)allocate: sizes only grow
+      AL(c.clin, size_t(h->K) * ctmax);
+      AL(c.coff, size_t(h->K) * ctmax);
+      AL(c.cw64, size_t(h->K) * ctmax);
+      AL(c.cw32, size_t(h->K) * ctmax);
+    }
+    if (!c.cnt) {
+      AL(c.cnt, size_t(h->K));
+      AL(c.cdiag64, size_t(h->K));
+      AL(c.cdiag32, size_t(h->K));
+    }
+    c.ctmax = ctmax;
+    std::vector<float> w32(w.begin(), w.end()), d32(diag.begin(), diag.end());
+    CK(cudaMemcpy(c.clin, lin.data(), lin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.coff, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.cw64, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.cw32, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.cnt, cnt.data(), cnt.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.cdiag64, diag.data(), diag.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.cdiag32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c.cnt_host = cnt;
+    prev.swap(cur);
+    Rprev = c.R;
+  }
+  h->class_valid = true;
+  h->class_dt = dt;
+  return SL_OK;
+}
+
+template <typename T>
+sl_status build_hierarchy_T(sl_hjb *h, double dt, cudaStream_t s) {
+  for (int l = 1; l < h->L; ++l) {
+    CoarseBuf &c = h->cl[l];
+    CoarseBuf &p = h->cl[l - 1];
+    CK(cudaMemsetAsync(h->d_count, 0, sizeof(int), s));
+    launch_classify(l, h->tab, h->policy, p.cls, p.n, c.cls, c.n, c.erow, h->d_count, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_count, h->d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c.nexpl = *h->h_count;
+    CoarseLev<T> prevv = lev_view<T>(h, l - 1), curv = lev_view<T>(h, l);
+    CK(launch_rap_explicit<T>(l, h->tab, h->d_off, h->policy, T(dt), prevv, p.coff, curv, c.nexpl,
+                              pick<T>(c.ewin64, c.ewin32), s));
+  }
+  const int lc = h->L - 1;
+  CoarseLev<T> cv = lev_view<T>(h, lc);
+  launch_coarsest_setup<T>(lc, h->tab, h->policy, T(dt), cv, lc == 0 ? h->d_off : h->cl[lc].coff,
+                           h->cwork, pick<T>(h->Ainv64, h->Ainv32), s);
+  CK(cudaGetLastError());
+  return SL_OK;
+}
+
+sl_status build_hierarchy(sl_hjb *h, double dt, cudaStream_t s) {
+  if (!h->class_valid || h->class_dt != dt) {
+    sl_status st = build_class_tables(h, dt);
+    if (st != SL_OK) return st;
+  }
+  sl_status st = (h->o.precision == 0) ? build_hierarchy_T<double>(h, dt, s)
+                                       : build_hierarchy_T<float>(h, dt, s);
+  if (st != SL_OK) return st;
+  h->hier_valid = true;
+  h->hier_dt = dt;
+  h->changes_since_build = 0;
+  return SL_OK;
+}
+
+// ---------------------------------------------------------------------- V-cycle
+template <typename T>
+void level_op(sl_hjb *h, int l, int op, double dt, const T *x, const T *b, T *y, cudaStream_t s) {
+  if (l == 0)
+    launch_fine_op<T>(op, h->tab, h->policy, T(dt), T(h->o.omega), x, b, y, s);
+  else
+    launch_coarse_op<T>(op, lev_view<T>(h, l), h->cl[l].nexpl, T(h->o.omega), x, b, y, s);
+}
+
+template <typename T>
+void vbufs(VBuf &v, T **x, T **t, T **r, T **b);
+template <>
+void vbufs<double>(VBuf &v, double **x, double **t, double **r, double **b) {
+  *x = v.x64; *t = v.t64; *r = v.r64; *b = v.b64;
+}
+template <>
+void vbufs<float>(VBuf &v, float **x, float **t, float **r, float **b) {
+  *x = v.x32; *t = v.t32; *r = v.r32; *b = v.b32;
+}
+
+// x = M_l^{-1} b: V(nu1, nu2) from a zero initial guess, exact solve on the coarsest level.
+template <typename T>
+sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) {
+  const size_t N = NN(h, l);
+  if (l == h->L - 1) {
+    launch_coarsest_apply<T>(pick<T>(h->Ainv64, h->Ainv32), h->cl[l].n, b, x, s);
+    return SL_OK;
+  }
+  T *bx, *bt, *br, *bb;
+  vbufs<T>(h->vb[l], &bx, &bt, &br, &bb);
+  T *cur = x, *other = bt;
+  if (h->o.nu1 == 0) {
+    launch_fill<T>(x, N, T(0), s);
+  } else {
+    level_op<T>(h, l, OP_JACOBI0, dt, nullptr, b, cur, s);
+    for (int it = 1; it < h->o.nu1; ++it) {
+      level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s);
+      std::swap(cur, other);
+    }
+  }
+  level_op<T>(h, l, OP_RESID, dt, cur, b, br, s);
+  T *cx, *ct, *cr, *cb;
+  vbufs<T>(h->vb[l + 1], &cx, &ct, &cr, &cb);
+  launch_restrict<T>(br, h->cl[l].n, cb, h->cl[l + 1].n, s);
+  sl_status st = vcycle<T>(h, l + 1, dt, cb, cx, s);
+  if (st != SL_OK) return st;
+  launch_prolong_add<T>(cx, h->cl[l + 1].n, cur, h->cl[l].n, s);
+  for (int it = 0; it < h->o.nu2; ++it) {
+    level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s);
+    std::swap(cur, other);
+  }
+  if (cur != x) CK(cudaMemcpyAsync(x, cur, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CK(cudaGetLastError());
+  return SL_OK;
+}
+
+// ---------------------------------------------------------------------- BiCGSTAB
+// Right-preconditioned BiCGSTAB for A e = r0 with x += e accumulated in place (x may be FP64
+// while the Krylov vectors are FP32: TX / T).  On entry r holds the initial residual and S
+// carries ||b||^2 and the stop threshold (tol ||b||)^2.  Returns SL_OK on convergence,
+// SL_ENOCONV_KRYLOV at the cap, SL_EBREAKDOWN, or SL_ENAN; only SL_ENAN is recorded as an error.
+template <typename T, typename TX>
+sl_status bicgstab(sl_hjb *h, double dt, TX *x, T *r, T *rh, T *p, T *v, T *sv, T *t, T *ph, T *sh,
+                   BicgScalars *S, int maxit, int *iters, cudaStream_t s) {
+  const size_t N = NN(h, 0);
+  CK(cudaMemcpyAsync(rh, r, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  launch_dot2<T>(r, r, r, r, N, POST_RHO_INIT, S, h->partials, h->counter, s);
+  *iters = 0;
+  for (int it = 1; it <= maxit; ++it) {
+    launch_bicg_p<T>(p, r, v, N, it == 1, S, s);
+    sl_status st = vcycle<T>(h, 0, dt, p, ph, s);
+    if (st != SL_OK) return st;
+    level_op<T>(h, 0, OP_APPLY, dt, ph, nullptr, v, s);
+    launch_dot2<T>(rh, v, nullptr, nullptr, N, POST_ALPHA, S, h->partials, h->counter, s);
+    launch_bicg_s<T>(sv, r, v, N, S, h->partials, h->counter, s);
+    st = vcycle<T>(h, 0, dt, sv, sh, s);
+    if (st != SL_OK) return st;
+    level_op<T>(h, 0, OP_APPLY, dt, sh, nullptr, t, s);
+    launch_dot2<T>(t, sv, t, t, N, POST_OMEGA, S, h->partials, h->counter, s);
+    launch_bicg_xr<T, TX>(x, ph, sh, sv, t, r, rh, N, S, h->partials, h->counter, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->hS, S, sizeof(BicgScalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *iters = it;
+    const BicgScalars &hs = *h->hS;
+    if (hs.nonfinite) return fail(h, SL_ENAN, "non-finite value in BiCGSTAB");
+    if (hs.rr <= hs.tol2) return SL_OK;
+    if (hs.breakdown) return SL_EBREAKDOWN;
+  }
+  return SL_ENOCONV_KRYLOV;
+}
+
+// True FP64 residual of the step system at h->X into `r`, with ||r||_2^2, ||r||_inf and the
+// matching norms of F.
+struct ResNorms {
+  double rr, rmax, bn2, bmax;
+};
+
+sl_status true_residual(sl_hjb *h, double dt, double tolk, double *r, ResNorms *nr, cudaStream_t s) {
+  const size_t N = NN(h, 0);
+  launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r, s);
+  launch_init_scalars(h->S, tolk * tolk, s);
+  launch_norms(h->Fvec, N, 0, h->S, h->partials, h->counter, s);
+  launch_norms(r, N, 1, h->S, h->partials, h->counter, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->hS, h->S, sizeof(BicgScalars), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  nr->bn2 = h->hS->bnorm2;
+  nr->bmax = h->hS->bmax;
+  nr->rr = h->hS->rr;
+  nr->rmax = h->hS->rmax;
+  if (h->hS->nonfinite || !std::isfinite(nr->rr)) return fail(h, SL_ENAN, "non-finite residual");
+  return SL_OK;
+}
+
+// Solves A^alpha X = F^alpha at the current policy from the iterate h->X (psi on the boundary).
+// Stop test on the true FP64 residual r = F - A X:
+//   ||r||_2 <= krylov_tol ||F||_2  and  ||r||_inf <= krylov_tol ||F||_inf.
+// A^alpha is an M-matrix with row sums >= 1 - dt c (Section 3.4), so for c = 0 the max-norm
+// test bounds the error of the step: ||X - X*||_inf <= ||r||_inf.  When the Krylov recurrence
+// meets the 2-norm test but the true max-norm test fails, the inner threshold is tightened
+// tenfold and BiCGSTAB restarts from the true residual.
+sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
+  const size_t N = NN(h, 0);
+  // ||F||: the residual at X = (0 inside, psi on the boundary) is F itself
+  launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, s);
+  CK(cudaGetLastError());
+  KBuf &k = h->kb;
+  const double tol = h->o.krylov_tol;
+  double tolk = tol;   // threshold handed to BiCGSTAB's recurrence
+  int total = 0;
+  const bool fp64 = h->o.precision == 0;
+  const int rounds = fp64 ? 12 : h->o.ir_max + 1;
+  for (int round = 0; round < rounds; ++round) {
+    ResNorms nr{};
+    double *r64 = fp64 ? k.r64 : h->R;
+    sl_status r = true_residual(h, dt, tolk, r64, &nr, s);
+    if (r != SL_OK) return r;
+    const double rel2 = nr.bn2 > 0 ? std::sqrt(nr.rr / nr.bn2) : std::sqrt(nr.rr);
+    if (st) st->res_final = rel2;
+    const bool ok2 = nr.rr <= tol * tol * nr.bn2;
+    const bool okinf = nr.rmax <= tol * nr.bmax;
+    if (ok2 && okinf) return SL_OK;
+    if (ok2 && !okinf) tolk *= 0.1;
+    if (fp64 && total >= h->o.kry_max) break;
+    int it = 0;
+    if (fp64) {
+      // BiCGSTAB on the true residual; S holds ||F||_2 and the threshold (tolk ||F||_2)^2
+      r = bicgstab<double, double>(h, dt, h->X, k.r64, k.rh64, k.p64, k.v64, k.s64, k.t64, k.ph64,
+                                   k.sh64, h->S, h->o.kry_max - total, &it, s);
+    } else {
+      // refinement: FP32 inner solve of A e = fp32(r) from e = 0, then X += e in FP64
+      if (st) st->ir_iters += 1;
+      launch_convert<double, float>(h->R, k.r32, N, s);
+      launch_fill<float>(k.e32, N, 0.0f, s);
+      launch_init_scalars(h->S32, h->o.inner_tol * h->o.inner_tol, s);
+      launch_dot2<float>(k.r32, k.r32, nullptr, nullptr, N, POST_BNORM, h->S32, h->partials, h->counter, s);
+      r = bicgstab<float, float>(h, dt, k.e32, k.r32, k.rh32, k.p32, k.v32, k.s32, k.t32, k.ph32,
+                                 k.sh32, h->S32, h->o.kry_max, &it, s);
+      launch_add_f32_to_f64(h->X, k.e32, N, s);
+      CK(cudaGetLastError());
+    }
+    total += it;
+    if (st) st->krylov_iters += it;
+    if (r == SL_ENAN) return r;
+    if (r != SL_OK && r != SL_ENOCONV_KRYLOV && r != SL_EBREAKDOWN) return r;
+    if (fp64 && r == SL_ENOCONV_KRYLOV) break;
+  }
+  return fail(h, SL_ENOCONV_KRYLOV, fp64 ? "BiCGSTAB reached its iteration cap"
+                                         : "iterative refinement reached ir_max");
+}
+
+// ---------------------------------------------------------------------- one step
+sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out, sl_stats *st,
+                    cudaStream_t s) {
+  if (!(dt > 0)) return fail(h, SL_EINVAL, "dt must be positive");
+  for (double c : h->cvec)
+    if (dt * c > 1.0) return fail(h, SL_ECFL, "dt * c > 1 violates the positivity condition");
+  const size_t N = NN(h, 0);
+  double t0 = now_ms();
+  CK(cudaMemcpyAsync(h->Uprev, u, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->X, u, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  sl_status r = coef(h, t, h->X, s);
+  if (r != SL_OK) return r;
+  if (!h->have_policy) {
+    long long ch = 0;
+    r = improve(h, h->X, &ch, s);
+    if (r != SL_OK) return r;
+    h->hier_valid = false;
+  }
+  CK(cudaMemcpyAsync(h->Xpi, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (st) st->steps += 1;
+  for (int it = 1; it <= h->o.pi_max; ++it) {
+    const long long thresh = (long long)(h->o.rebuild_frac * double(h->m) * h->m);
+    if (!h->hier_valid || h->hier_dt != dt || h->changes_since_build > thresh) {
+      double tb = now_ms();
+      r = build_hierarchy(h, dt, s);
+      if (r != SL_OK) return r;
+      CK(cudaStreamSynchronize(s));
+      if (st) {
+        st->rebuilds += 1;
+        st->t_hier_ms += now_ms() - tb;
+        long long ex = 0;
+        for (int l = 1; l < h->L; ++l) ex += h->cl[l].nexpl;
+        st->explicit_rows = ex;
+      }
+    }
+    double ts = now_ms();
+    r = linear_solve(h, dt, st, s);
+    if (st) st->t_solve_ms += now_ms() - ts;
+    if (r != SL_OK) return r;
+    double ta = now_ms();
+    long long ch = 0;
+    r = improve(h, h->X, &ch, s);
+    if (r != SL_OK) return r;
+    h->changes_since_build += ch;
+    launch_maxabs_diff(h->X, h->Xpi, h->n, h->d_maxd, h->counter, h->partials, s);
+    CK(cudaMemcpyAsync(h->h_maxd, h->d_maxd, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (st) {
+      st->t_argmin_ms += now_ms() - ta;
+      st->pi_iters += 1;
+      st->policy_changes += ch;
+    }
+    if (!std::isfinite(h->h_maxd[0])) return fail(h, SL_ENAN, "non-finite iterate");
+    const bool small = h->h_maxd[0] <= h->o.pi_tol * std::max(1.0, h->h_maxd[1]);
+    if (ch == 0 || small) {
+      CK(cudaMemcpyAsync(u, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (pol_out)
+        CK(cudaMemcpyAsync(pol_out, h->policy, size_t(h->m) * h->m, cudaMemcpyDeviceToDevice, s));
+      (void)t0;
+      return SL_OK;
+    }
+    CK(cudaMemcpyAsync(h->Xpi, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  CK(cudaMemcpyAsync(u, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return fail(h, SL_ENOCONV_PI, "Howard iteration reached pi_max");
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void sl_opts_default(sl_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = 0;
+  o->levels = 0;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->omega = 0.8;
+  o->krylov_tol = 1e-12;
+  o->kry_max = 200;
+  o->inner_tol = 1e-5;
+  o->ir_max = 30;
+  o->pi_tol = 1e-10;
+  o->pi_max = 100;
+  o->tie_rel = 1e-12;
+  o->argmin_screen = 0;
+  o->rebuild_frac = 0.0;
+}
+
+const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
+
+void sl_hjb_destroy(sl_hjb *h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (void *p : h->allocs) cudaFree(p);
+  if (h->hS) cudaFreeHost(h->hS);
+  if (h->h_maxd) cudaFreeHost(h->h_maxd);
+  if (h->h_changes) cudaFreeHost(h->h_changes);
+  if (h->h_flags) cudaFreeHost(h->h_flags);
+  if (h->h_count) cudaFreeHost(h->h_count);
+  delete h;
+}
+
+static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, const sl_source *src,
+                             const sl_opts *opts) {
+  if (!g || !c || !src) return fail(h, SL_EINVAL, "null argument");
+  if (g->nx != g->ny || g->nx < 5) return fail(h, SL_EINVAL, "grid must be square with nx >= 5");
+  const double hx = (g->x_hi - g->x_lo) / (g->nx - 1), hy = (g->y_hi - g->y_lo) / (g->ny - 1);
+  if (!(hx > 0) || std::fabs(hx - hy) > 1e-12 * hx) return fail(h, SL_EINVAL, "cells must be square");
+  if (c->K < 1 || c->K > 255) return fail(h, SL_EINVAL, "K must be in 1..255");
+  if (c->P < 1 || c->P > 4 || !c->sigma) return fail(h, SL_EINVAL, "P must be in 1..4 with sigma given");
+  if (src->nf < 1 || src->nf > 4 || src->nq < 1 || !src->phi || !src->G_dev || !src->tau_kind || !src->tau_rate)
+    return fail(h, SL_EINVAL, "source: need 1 <= nf <= 4, nq >= 1, phi, G, tau");
+  if (src->npsi < 0 || (src->npsi > 0 && (!src->Psi_dev || !src->psi_kind || !src->psi_rate)))
+    return fail(h, SL_EINVAL, "boundary data incomplete");
+  if (opts) h->o = *opts; else sl_opts_default(&h->o);
+  if (h->o.precision != 0 && h->o.precision != 1) return fail(h, SL_EINVAL, "precision must be 0 or 1");
+  if (h->o.nu1 < 0 || h->o.nu2 < 0 || h->o.kry_max < 1 || h->o.pi_max < 1 || !(h->o.omega > 0))
+    return fail(h, SL_EINVAL, "bad iteration options");
+  h->n = g->nx;
+  h->m = g->nx - 2;
+  h->h = hx;
+  h->K = c->K;
+  h->P = c->P;
+  h->nf = src->nf;
+  h->nq = src->nq;
+  h->npsi = src->npsi;
+  h->G = src->G_dev;
+  h->Psi = src->Psi_dev;
+  h->phi.assign(src->phi, src->phi + size_t(c->K) * src->nf);
+  h->tau_kind.assign(src->tau_kind, src->tau_kind + src->nq);
+  h->tau_rate.assign(src->tau_rate, src->tau_rate + src->nq);
+  if (src->npsi > 0) {
+    h->psi_kind.assign(src->psi_kind, src->psi_kind + src->npsi);
+    h->psi_rate.assign(src->psi_rate, src->psi_rate + src->npsi);
+  }
+  h->cvec.assign(c->K, 0.0);
+  if (c->c) h->cvec.assign(c->c, c->c + c->K);
+  h->phimax.assign(h->nf, 0.0);
+  for (int k = 0; k < h->K; ++k)
+    for (int mm = 0; mm < h->nf; ++mm)
+      h->phimax[mm] = std::max(h->phimax[mm], std::fabs(h->phi[size_t(k) * h->nf + mm]));
+  // levels
+  int maxL = 1;
+  {
+    int nn = h->n;
+    while (nn > 5 && (nn - 1) % 2 == 0) { nn = (nn + 1) / 2; ++maxL; }
+  }
+  h->L = h->o.levels > 0 ? h->o.levels : maxL;
+  if (h->L > maxL || h->L > kMaxLevels) return fail(h, SL_EINVAL, "too many levels for this grid (need n = 2^j + 1)");
+  {
+    int nn = h->n;
+    for (int l = 0; l < h->L; ++l) {
+      h->cl[l].n = nn;
+      h->cl[l].m = nn - 2;
+      nn = (nn + 1) / 2;
+    }
+    const int mc = h->cl[h->L - 1].m;
+    if (mc * mc > kCoarsestMax) return fail(h, SL_EINVAL, "coarsest level too large for the dense solve: use more levels");
+  }
+  // stencil tables
+  try {
+    h->ft = build_fine_tables(h->n, h->h, h->K, h->P, c->sigma, c->b, c->c);
+  } catch (const std::exception &e) {
+    return fail(h, SL_EINVAL, e.what());
+  }
+  const FineTabHost &ft = h->ft;
+  h->halo = std::max(1, ft.R0);
+  h->SW = 32 + 2 * h->halo;
+  h->SH = 8 + 2 * h->halo;
+  if (size_t(h->SW) * h->SH * sizeof(double) > 200 * 1024)
+    return fail(h, SL_EINVAL, "stencil too wide for the shared-memory tile of the argmin");
+  const size_t ET = ft.dx.size();
+  std::vector<int32_t> lin(ET), slin(ET), off(ET);
+  for (size_t i = 0; i < ET; ++i) {
+    lin[i] = ft.dy[i] * h->n + ft.dx[i];
+    slin[i] = ft.dy[i] * h->SW + ft.dx[i];
+    off[i] = (ft.dy[i] << 16) | (ft.dx[i] & 0xffff);
+  }
+  std::vector<float> w32(ft.w.begin(), ft.w.end()), W32(ft.W.begin(), ft.W.end()),
+      ws32(ft.ws.begin(), ft.ws.end()), c32(ft.c.begin(), ft.c.end()),
+      phi32(h->phi.begin(), h->phi.end());
+  UP(h->d_lin, lin);
+  UP(h->d_slin, slin);
+  UP(h->d_off, off);
+  UP(h->d_w64, ft.w);
+  UP(h->d_w32, w32);
+  UP(h->d_nt, ft.nt);
+  UP(h->d_W64, ft.W);
+  UP(h->d_W32, W32);
+  UP(h->d_ws64, ft.ws);
+  UP(h->d_ws32, ws32);
+  UP(h->d_c64, ft.c);
+  UP(h->d_c32, c32);
+  UP(h->d_Wmaxc, ft.Wmax_class);
+  UP(h->d_phi, h->phi);
+  UP(h->d_phi32, phi32);
+  UP(h->d_phimax, h->phimax);
+  AL(h->d_tau, size_t(h->nq + h->npsi + 2));
+  FineTab &t = h->tab;
+  t.n = h->n; t.m = h->m; t.B = ft.B; t.Q = ft.Q; t.tmax = ft.tmax; t.K = h->K;
+  t.lin = h->d_lin; t.w64 = h->d_w64; t.w32 = h->d_w32; t.nt = h->d_nt; t.W64 = h->d_W64;
+  t.W32 = h->d_W32; t.ws64 = h->d_ws64; t.ws32 = h->d_ws32; t.c64 = h->d_c64; t.c32 = h->d_c32;
+  // vectors
+  const size_t N = size_t(h->n) * h->n;
+  AL(h->X, N);
+  AL(h->Xb, N);
+  AL(h->Uprev, N);
+  AL(h->R, N);
+  AL(h->Xpi, N);
+  AL(h->Fvec, N);
+  AL(h->F, N * h->nf);
+  AL(h->F32, N * h->nf);
+  AL(h->policy, size_t(h->m) * h->m);
+  const bool p64 = h->o.precision == 0;
+  KBuf &k = h->kb;
+  if (p64) {
+    AL(k.r64, N); AL(k.rh64, N); AL(k.p64, N); AL(k.v64, N); AL(k.s64, N); AL(k.t64, N);
+    AL(k.ph64, N); AL(k.sh64, N);
+  } else {
+    AL(k.r32, N); AL(k.rh32, N); AL(k.p32, N); AL(k.v32, N); AL(k.s32, N); AL(k.t32, N);
+    AL(k.ph32, N); AL(k.sh32, N); AL(k.e32, N);
+  }
+  // multigrid levels
+  h->cl[0].R = ft.R0;
+  for (int l = 0; l < h->L; ++l) {
+    CoarseBuf &cb = h->cl[l];
+    const size_t Nl = size_t(cb.n) * cb.n;
+    VBuf &v = h->vb[l];
+    if (p64) { AL(v.x64, Nl); AL(v.t64, Nl); AL(v.r64, Nl); AL(v.b64, Nl); }
+    else { AL(v.x32, Nl); AL(v.t32, Nl); AL(v.r32, Nl); AL(v.b32, Nl); }
+    if (l == 0) continue;
+    cb.R = (h->cl[l - 1].R + 2) / 2;
+    cb.win = (2 * cb.R + 1) * (2 * cb.R + 1);
+    cb.cap = cb.m * cb.m;
+    AL(cb.cls, size_t(cb.m) * cb.m);
+    AL(cb.erow, size_t(cb.cap));
+    if (p64) AL(cb.ewin64, size_t(cb.win) * cb.cap);
+    else AL(cb.ewin32, size_t(cb.win) * cb.cap);
+  }
+  const int mc = h->cl[h->L - 1].m;
+  AL(h->cwork, size_t(2) * mc * mc * mc * mc);
+  if (p64) AL(h->Ainv64, size_t(mc) * mc * mc * mc);
+  else AL(h->Ainv32, size_t(mc) * mc * mc * mc);
+  // reductions
+  AL(h->S, 1);
+  AL(h->S32, 1);
+  AL(h->partials, size_t(2) * kRedBlocks + 2 * 65536);
+  AL(h->counter, 1);
+  AL(h->d_maxd, 2);
+  AL(h->d_changes, 1);
+  AL(h->d_flags, 1);
+  AL(h->d_count, 1);
+  CK(cudaMallocHost(reinterpret_cast<void **>(&h->hS), sizeof(BicgScalars)));
+  CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_maxd), 2 * sizeof(double)));
+  CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_changes), sizeof(unsigned long long)));
+  CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_flags), sizeof(int)));
+  CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_count), sizeof(int)));
+  CK(cudaDeviceSynchronize());
+  return SL_OK;
+}
+
+sl_status sl_hjb_create(sl_hjb **out, const sl_grid *g, const sl_controls *c, const sl_source *src,
+                        const sl_opts *opts, void *stream) {
+  (void)stream;
+  if (!out) return SL_EINVAL;
+  *out = nullptr;
+  sl_hjb *h = new (std::nothrow) sl_hjb();
+  if (!h) return SL_ENOMEM;
+  sl_status st = create_impl(h, g, c, src, opts);
+  if (st != SL_OK) {
+    std::fprintf(stderr, "sl_hjb_create: %s\n", h->err.c_str());
+    sl_hjb_destroy(h);
+    return st;
+  }
+  *out = h;
+  return SL_OK;
+}
+
+sl_status sl_hjb_step(sl_hjb *h, double *u, double t_n, double dt, uint8_t *pol_out, sl_stats *st,
+                      void *stream) {
+  if (!h || !u) return SL_EINVAL;
+  if (st) std::memset(st, 0, sizeof(*st));
+  return step_impl(h, u, t_n, dt, pol_out, st, static_cast<cudaStream_t>(stream));
+}
+
+sl_status sl_hjb_solve(sl_hjb *h, double *u, double t0, double T, int n_steps, uint8_t *pol_out,
+                       sl_stats *st, void *stream) {
+  if (!h || !u || n_steps < 1 || !(T > 0)) return SL_EINVAL;
+  if (st) std::memset(st, 0, sizeof(*st));
+  const double dt = T / n_steps;
+  for (int i = 1; i <= n_steps; ++i) {
+    sl_status r = step_impl(h, u, t0 + i * dt, dt, pol_out, st, static_cast<cudaStream_t>(stream));
+    if (r != SL_OK) return r;
+  }
+  return SL_OK;
+}
+
+sl_status sl_hjb_improve(sl_hjb *h, const double *x_ext, double t, uint8_t *pol_out,
+                         long long *changes, void *stream) {
+  if (!h || !x_ext) return SL_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  sl_status r = coef(h, t, h->X, s);
+  if (r != SL_OK) return r;
+  long long ch = 0;
+  r = improve(h, x_ext, &ch, s);
+  if (r != SL_OK) return r;
+  h->changes_since_build += ch;
+  h->hier_valid = h->hier_valid && ch == 0;
+  if (changes) *changes = ch;
+  if (pol_out) CK(cudaMemcpyAsync(pol_out, h->policy, size_t(h->m) * h->m, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return SL_OK;
+}
+
+sl_status sl_hjb_set_policy(sl_hjb *h, const uint8_t *pol, void *stream) {
+  if (!h || !pol) return SL_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(h->policy, pol, size_t(h->m) * h->m, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  h->have_policy = true;
+  h->hier_valid = false;
+  return SL_OK;
+}
+
+sl_status sl_hjb_build_hierarchy(sl_hjb *h, double dt, void *stream) {
+  if (!h || !(dt > 0)) return SL_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  sl_status r = build_hierarchy(h, dt, s);
+  if (r != SL_OK) return r;
+  CK(cudaStreamSynchronize(s));
+  return SL_OK;
+}
+
+sl_status sl_hjb_apply(sl_hjb *h, int level, int precision, const void *x, void *y, void *stream) {
+  if (!h || !x || !y || level < 0 || level >= h->L) return SL_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (level > 0 && (!h->hier_valid || precision != h->o.precision))
+    return fail(h, SL_EINVAL, "coarse levels need a built hierarchy in the handle's precision");
+  const double dt = h->hier_valid ? h->hier_dt : (h->class_valid ? h->class_dt : -1.0);
+  if (level == 0 && !(dt > 0)) return fail(h, SL_EINVAL, "build the hierarchy first (it fixes dt)");
+  if (precision == 0)
+    level_op<double>(h, level, OP_APPLY, dt, static_cast<const double *>(x), nullptr,
+                     static_cast<double *>(y), s);
+  else
+    level_op<float>(h, level, OP_APPLY, dt, static_cast<const float *>(x), nullptr,
+                    static_cast<float *>(y), s);
+  CK(cudaGetLastError());
+  return SL_OK;
+}
+
+sl_status sl_hjb_vcycle(sl_hjb *h, int precision, const void *b, void *x, void *stream) {
+  if (!h || !b || !x) return SL_EINVAL;
+  if (!h->hier_valid || precision != h->o.precision)
+    return fail(h, SL_EINVAL, "V-cycle needs a built hierarchy in the handle's precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  sl_status r = precision == 0
+                    ? vcycle<double>(h, 0, h->hier_dt, static_cast<const double *>(b), static_cast<double *>(x), s)
+                    : vcycle<float>(h, 0, h->hier_dt, static_cast<const float *>(b), static_cast<float *>(x), s);
+  if (r != SL_OK) return r;
+  CK(cudaStreamSynchronize(s));
+  return SL_OK;
+}
+
+sl_status sl_hjb_linear_solve(sl_hjb *h, const double *u_prev, double *x_ext, double t, double dt,
+                              sl_stats *st, void *stream) {
+  if (!h || !u_prev || !x_ext || !(dt > 0)) return SL_EINVAL;
+  if (!h->have_policy) return fail(h, SL_EINVAL, "no policy set");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (st) std::memset(st, 0, sizeof(*st));
+  const size_t N = NN(h, 0);
+  CK(cudaMemcpyAsync(h->Uprev, u_prev, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->X, x_ext, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  sl_status r = coef(h, t, h->X, s);
+  if (r != SL_OK) return r;
+  if (!h->hier_valid || h->hier_dt != dt) {
+    r = build_hierarchy(h, dt, s);
+    if (r != SL_OK) return r;
+  }
+  r = linear_solve(h, dt, st, s);
+  CK(cudaMemcpyAsync(x_ext, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return r;
+}
+
+sl_status sl_hjb_level_info(const sl_hjb *h, int level, int *n, long long *explicit_rows, long long *nnz) {
+  if (!h || level < 0 || level >= h->L) return SL_EINVAL;
+  const CoarseBuf &c = h->cl[level];
+  if (n) *n = c.n;
+  if (explicit_rows) *explicit_rows = level == 0 ? 0 : c.nexpl;
+  if (nnz) *nnz = -1;
+  return SL_OK;
+}
+
+int sl_hjb_num_levels(const sl_hjb *h) { return h ? h->L : 0; }
+
+long long sl_launch_count(void) { return launch_count(); }
+
+}  // extern "C"

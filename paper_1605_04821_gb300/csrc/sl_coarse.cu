@@ -1,0 +1,344 @@
+// sl_coarse.cu - Galerkin coarse levels A_l = R A_{l-1} P (Section 3.3) on the device.
+#include <cmath>
+
+#include "sl_launch.h"
+
+namespace sl {
+
+// ----------------------------------------------------------------------------- classification
+// Coarse row I is class k when all nine rows 2I + a of the previous level are class-k interior
+// rows (level 0: untruncated band-free rows with control k); otherwise it gets an explicit slot.
+__global__ void k_classify(int level, FineTab tab, const uint8_t *__restrict__ policy,
+                           const int32_t *__restrict__ cls_prev, int n_prev,
+                           int32_t *__restrict__ cls, int n, int32_t *__restrict__ erow,
+                           int *__restrict__ count) {
+  const int I1 = 1 + blockIdx.x * 32 + threadIdx.x;
+  const int I2 = 1 + blockIdx.y * 8 + threadIdx.y;
+  const int m = n - 2;
+  if (I1 > m || I2 > m) return;
+  int k0 = -1;
+  bool uniform = true;
+  for (int a2 = -1; a2 <= 1 && uniform; ++a2)
+    for (int a1 = -1; a1 <= 1 && uniform; ++a1) {
+      const int i1 = 2 * I1 + a1, i2 = 2 * I2 + a2;
+      int k;
+      if (level == 1) {
+        const bool interior = (tab.n - 1 >= 2 * tab.B) && class_q(i1, tab.n, tab.B) == tab.B &&
+                              class_q(i2, tab.n, tab.B) == tab.B;
+        k = interior ? int(policy[(i2 - 1) * tab.m + (i1 - 1)]) : -1;
+      } else {
+        k = cls_prev[(i2 - 1) * (n_prev - 2) + (i1 - 1)];
+        if (k < 0) k = -1;
+      }
+      if (k < 0) uniform = false;
+      else if (k0 < 0) k0 = k;
+      else if (k != k0) uniform = false;
+    }
+  const int I = (I2 - 1) * m + (I1 - 1);
+  if (uniform) {
+    cls[I] = k0;
+  } else {
+    const int slot = atomicAdd(count, 1);
+    cls[I] = -slot - 1;
+    erow[slot] = I2 * n + I1;
+  }
+}
+
+void launch_classify(int level, const FineTab &tab, const uint8_t *policy, const int32_t *cls_prev,
+                     int n_prev, int32_t *cls, int n, int32_t *erow, int *count, cudaStream_t s) {
+  dim3 blk(32, 8), grd((n - 2 + 31) / 32, (n - 2 + 7) / 8);
+  note_launch();
+  k_classify<<<grd, blk, 0, s>>>(level, tab, policy, cls_prev, n_prev, cls, n, erow, count);
+}
+
+// ----------------------------------------------------------------------------- explicit RAP
+// Thread per explicit coarse row; the (2R+1)^2 window accumulates in shared memory.  Row
+// 2I + a of the previous level contributes R_a * (its coefficient at column j) * P_{jJ}.
+template <typename T>
+__global__ void k_rap_explicit(int level, FineTab tab, const int32_t *__restrict__ fine_off,
+                               const uint8_t *__restrict__ policy, T dt, CoarseLev<T> prev,
+                               const int32_t *__restrict__ prev_coff, CoarseLev<T> cur, int count,
+                               T *__restrict__ ewin_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= count) return;
+  T *win = reinterpret_cast<T *>(smem_raw) + size_t(threadIdx.x) * cur.win;
+  for (int e = 0; e < cur.win; ++e) win[e] = T(0);
+  const int jr = cur.erow[slot];
+  const int I1 = jr % cur.n, I2 = jr / cur.n;
+  const int R = cur.R;
+  for (int a2 = -1; a2 <= 1; ++a2)
+    for (int a1 = -1; a1 <= 1; ++a1) {
+      const T ra = T(fw_weight(a1) * fw_weight(a2));
+      const int i1 = 2 * I1 + a1, i2 = 2 * I2 + a2;
+      if (level == 1) {
+        const int k = policy[(i2 - 1) * tab.m + (i1 - 1)];
+        const int e = (k * tab.Q + class_q(i2, tab.n, tab.B)) * tab.Q + class_q(i1, tab.n, tab.B);
+        const T W = tab_W<T>(tab)[e], c = tab_c<T>(tab)[k];
+        rap_scatter<T>(win, R, I1, I2, i1, i2, ra * (T(1) + dt * (W - c)));
+        const T *w = tab_w<T>(tab);
+        for (int t = 0; t < tab.nt[e]; ++t) {
+          const int ix = e * tab.tmax + t;
+          const int off = fine_off[ix];
+          const int dx = int(int16_t(off & 0xffff)), dy = off >> 16;
+          rap_scatter<T>(win, R, I1, I2, i1 + dx, i2 + dy, -ra * dt * w[ix]);
+        }
+      } else {
+        const int cp = prev.cls[(i2 - 1) * prev.m + (i1 - 1)];
+        if (cp >= 0) {
+          for (int t = 0; t < prev.cnt[cp]; ++t) {
+            const int off = prev_coff[cp * prev.ctmax + t];
+            const int dx = int(int16_t(off & 0xffff)), dy = off >> 16;
+            rap_scatter<T>(win, R, I1, I2, i1 + dx, i2 + dy, ra * prev.cw[cp * prev.ctmax + t]);
+          }
+        } else {
+          const int ps = -cp - 1;
+          const int Wp = 2 * prev.R + 1;
+          for (int e = 0; e < prev.win; ++e) {
+            const T v = prev.ewin[size_t(e) * prev.cap + ps];
+            if (v == T(0)) continue;
+            const int dy = e / Wp - prev.R, dx = e % Wp - prev.R;
+            rap_scatter<T>(win, R, I1, I2, i1 + dx, i2 + dy, ra * v);
+          }
+        }
+      }
+    }
+  for (int e = 0; e < cur.win; ++e) ewin_out[size_t(e) * cur.cap + slot] = win[e];
+}
+
+template <typename T>
+cudaError_t launch_rap_explicit(int level, const FineTab &tab, const int32_t *fine_off,
+                                const uint8_t *policy, T dt, const CoarseLev<T> &prev,
+                                const int32_t *prev_coff, const CoarseLev<T> &cur, int count,
+                                T *ewin_out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const size_t per = size_t(cur.win) * sizeof(T);
+  int threads = int((200 * 1024) / per);
+  threads = threads > 128 ? 128 : threads;
+  if (threads < 1) return cudaErrorInvalidValue;
+  const size_t bytes = per * threads;
+  cudaError_t err = cudaFuncSetAttribute(k_rap_explicit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(bytes));
+  if (err != cudaSuccess) return err;
+  note_launch();
+  k_rap_explicit<T><<<(count + threads - 1) / threads, threads, bytes, s>>>(
+      level, tab, fine_off, policy, dt, prev, prev_coff, cur, count, ewin_out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_rap_explicit<double>(int, const FineTab &, const int32_t *, const uint8_t *,
+                                                 double, const CoarseLev<double> &, const int32_t *,
+                                                 const CoarseLev<double> &, int, double *, cudaStream_t);
+template cudaError_t launch_rap_explicit<float>(int, const FineTab &, const int32_t *, const uint8_t *,
+                                                float, const CoarseLev<float> &, const int32_t *,
+                                                const CoarseLev<float> &, int, float *, cudaStream_t);
+
+// ----------------------------------------------------------------------------- coarse operator
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) k_coarse_class_op(CoarseLev<T> L, T omega, const T *__restrict__ x,
+                                                         const T *__restrict__ b, T *__restrict__ y) {
+  const int I1 = 1 + blockIdx.x * 32 + threadIdx.x;
+  const int I2 = 1 + blockIdx.y * 8 + threadIdx.y;
+  if (I1 > L.m || I2 > L.m) return;
+  const int k = L.cls[(I2 - 1) * L.m + (I1 - 1)];
+  if (k < 0) return;
+  const int j = I2 * L.n + I1;
+  const T d = L.cdiag[k];
+  if (OP == OP_JACOBI0) {
+    y[j] = omega * b[j] / d;
+    return;
+  }
+  T acc = T(0);
+  const int nt = L.cnt[k];
+  for (int t = 0; t < nt; ++t) {
+    const int ix = k * L.ctmax + t;
+    acc = fma(__ldg(L.cw + ix), __ldg(x + j + __ldg(L.clin + ix)), acc);
+  }
+  if (OP == OP_APPLY) y[j] = acc;
+  else if (OP == OP_RESID) y[j] = b[j] - acc;
+  else y[j] = x[j] + omega * (b[j] - acc) / d;
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) k_coarse_expl_op(CoarseLev<T> L, int nexpl, T omega,
+                                                        const T *__restrict__ x, const T *__restrict__ b,
+                                                        T *__restrict__ y) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nexpl) return;
+  const int j = L.erow[slot];
+  const int I1 = j % L.n, I2 = j / L.n;
+  const int R = L.R, Wd = 2 * R + 1;
+  const T d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
+  if (OP == OP_JACOBI0) {
+    y[j] = omega * b[j] / d;
+    return;
+  }
+  const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
+  const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
+  T acc = T(0);
+  for (int dy = ylo; dy <= yhi; ++dy) {
+    const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
+    const T *xrow = x + j + dy * L.n;
+    for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[size_t(dx) * L.cap], __ldg(xrow + dx), acc);
+  }
+  if (OP == OP_APPLY) y[j] = acc;
+  else if (OP == OP_RESID) y[j] = b[j] - acc;
+  else y[j] = x[j] + omega * (b[j] - acc) / d;
+}
+
+template <typename T>
+void launch_coarse_op(int op, const CoarseLev<T> &L, int nexpl, T omega, const T *x, const T *b,
+                      T *y, cudaStream_t s) {
+  dim3 blk(32, 8), grd((L.m + 31) / 32, (L.m + 7) / 8);
+  const int eg = (nexpl + 255) / 256;
+  switch (op) {
+    case OP_APPLY:
+      note_launch();
+      k_coarse_class_op<T, OP_APPLY><<<grd, blk, 0, s>>>(L, omega, x, b, y);
+      if (eg) { note_launch(); k_coarse_expl_op<T, OP_APPLY><<<eg, 256, 0, s>>>(L, nexpl, omega, x, b, y); }
+      break;
+    case OP_RESID:
+      note_launch();
+      k_coarse_class_op<T, OP_RESID><<<grd, blk, 0, s>>>(L, omega, x, b, y);
+      if (eg) { note_launch(); k_coarse_expl_op<T, OP_RESID><<<eg, 256, 0, s>>>(L, nexpl, omega, x, b, y); }
+      break;
+    case OP_JACOBI:
+      note_launch();
+      k_coarse_class_op<T, OP_JACOBI><<<grd, blk, 0, s>>>(L, omega, x, b, y);
+      if (eg) { note_launch(); k_coarse_expl_op<T, OP_JACOBI><<<eg, 256, 0, s>>>(L, nexpl, omega, x, b, y); }
+      break;
+    default:
+      note_launch();
+      k_coarse_class_op<T, OP_JACOBI0><<<grd, blk, 0, s>>>(L, omega, x, b, y);
+      if (eg) { note_launch(); k_coarse_expl_op<T, OP_JACOBI0><<<eg, 256, 0, s>>>(L, nexpl, omega, x, b, y); }
+      break;
+  }
+}
+template void launch_coarse_op<double>(int, const CoarseLev<double> &, int, double, const double *,
+                                       const double *, double *, cudaStream_t);
+template void launch_coarse_op<float>(int, const CoarseLev<float> &, int, float, const float *,
+                                      const float *, float *, cudaStream_t);
+
+// ----------------------------------------------------------------------------- coarsest level
+// Dense matrix of the coarsest level (interior unknowns, row-major) and its inverse by
+// Gauss-Jordan elimination with partial pivoting in one thread block; the V-cycle then
+// applies x = A^{-1} b.
+template <typename T>
+__global__ void k_coarsest_setup(int level, FineTab tab, const uint8_t *__restrict__ policy, T dt,
+                                 CoarseLev<T> L, const int32_t *__restrict__ coff,
+                                 double *__restrict__ work, T *__restrict__ Ainv) {
+  const int m = (level == 0) ? tab.m : L.m;
+  const int n = (level == 0) ? tab.n : L.n;
+  const int N = m * m;
+  double *A = work;            // N x N
+  double *Inv = work + N * N;  // N x N
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    A[idx] = 0.0;
+    Inv[idx] = (idx / N == idx % N) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    const int i1 = 1 + r % m, i2 = 1 + r / m;
+    auto put = [&](int dx, int dy, double v) {
+      const int c1 = i1 + dx, c2 = i2 + dy;
+      if (c1 < 1 || c1 > m || c2 < 1 || c2 > m) return;  // boundary columns multiply zero
+      A[size_t(r) * N + (c2 - 1) * m + (c1 - 1)] += v;
+    };
+    if (level == 0) {
+      const int k = policy[r];
+      const int e = (k * tab.Q + class_q(i2, n, tab.B)) * tab.Q + class_q(i1, n, tab.B);
+      put(0, 0, 1.0 + double(dt) * (double(tab_W<T>(tab)[e]) - double(tab_c<T>(tab)[k])));
+      for (int t = 0; t < tab.nt[e]; ++t) {
+        const int ix = e * tab.tmax + t;
+        const int off = coff[ix];
+        put(int(int16_t(off & 0xffff)), off >> 16, -double(dt) * double(tab_w<T>(tab)[ix]));
+      }
+    } else {
+      const int c = L.cls[r];
+      if (c >= 0) {
+        for (int t = 0; t < L.cnt[c]; ++t) {
+          const int off = coff[c * L.ctmax + t];
+          put(int(int16_t(off & 0xffff)), off >> 16, double(L.cw[c * L.ctmax + t]));
+        }
+      } else {
+        const int s = -c - 1, Wd = 2 * L.R + 1;
+        for (int e = 0; e < L.win; ++e)
+          put(e % Wd - L.R, e / Wd - L.R, double(L.ewin[size_t(e) * L.cap + s]));
+      }
+    }
+  }
+  __syncthreads();
+  __shared__ int piv;
+  for (int col = 0; col < N; ++col) {
+    if (threadIdx.x == 0) {
+      int p = col;
+      double best = fabs(A[size_t(col) * N + col]);
+      for (int r = col + 1; r < N; ++r) {
+        const double v = fabs(A[size_t(r) * N + col]);
+        if (v > best) { best = v; p = r; }
+      }
+      piv = p;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != col) {
+      for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        double t0 = A[size_t(col) * N + c]; A[size_t(col) * N + c] = A[size_t(p) * N + c]; A[size_t(p) * N + c] = t0;
+        double t1 = Inv[size_t(col) * N + c]; Inv[size_t(col) * N + c] = Inv[size_t(p) * N + c]; Inv[size_t(p) * N + c] = t1;
+      }
+    }
+    __syncthreads();
+    const double inv = 1.0 / A[size_t(col) * N + col];
+    __syncthreads();
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+      A[size_t(col) * N + c] *= inv;
+      Inv[size_t(col) * N + c] *= inv;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      if (r == col) continue;
+      const double f = A[size_t(r) * N + col];
+      if (f == 0.0) continue;
+      for (int c = 0; c < N; ++c) {
+        A[size_t(r) * N + c] -= f * A[size_t(col) * N + c];
+        Inv[size_t(r) * N + c] -= f * Inv[size_t(col) * N + c];
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) Ainv[idx] = T(Inv[idx]);
+}
+
+template <typename T>
+void launch_coarsest_setup(int level, const FineTab &tab, const uint8_t *policy, T dt,
+                           const CoarseLev<T> &L, const int32_t *coff, double *work, T *Ainv,
+                           cudaStream_t s) {
+  note_launch();
+  k_coarsest_setup<T><<<1, 256, 0, s>>>(level, tab, policy, dt, L, coff, work, Ainv);
+}
+template void launch_coarsest_setup<double>(int, const FineTab &, const uint8_t *, double,
+                                            const CoarseLev<double> &, const int32_t *, double *,
+                                            double *, cudaStream_t);
+template void launch_coarsest_setup<float>(int, const FineTab &, const uint8_t *, float,
+                                           const CoarseLev<float> &, const int32_t *, double *,
+                                           float *, cudaStream_t);
+
+template <typename T>
+__global__ void k_coarsest_apply(const T *__restrict__ Ainv, int n, const T *__restrict__ b,
+                                 T *__restrict__ x) {
+  const int m = n - 2, N = m * m;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    T acc = T(0);
+    for (int c = 0; c < N; ++c) acc = fma(Ainv[size_t(r) * N + c], b[(1 + c / m) * n + 1 + c % m], acc);
+    x[(1 + r / m) * n + 1 + r % m] = acc;
+  }
+}
+
+template <typename T>
+void launch_coarsest_apply(const T *Ainv, int n, const T *b, T *x, cudaStream_t s) {
+  note_launch();
+  k_coarsest_apply<T><<<1, 256, 0, s>>>(Ainv, n, b, x);
+}
+template void launch_coarsest_apply<double>(const double *, int, const double *, double *, cudaStream_t);
+template void launch_coarsest_apply<float>(const float *, int, const float *, float *, cudaStream_t);
+
+}  // namespace sl

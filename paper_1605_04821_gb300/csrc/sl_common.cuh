@@ -1,0 +1,135 @@
+// sl_common.cuh - data layout shared by the host orchestration and the sm_103a kernels.
+//
+// Fine level (level 0): matrix-free.  Row j = (i1, i2) of A^alpha (Eq. FullScheme, theta = 1)
+// is described by its control k = alpha_j and its boundary-distance class (q1, q2):
+//   (A x)_j = (1 + dt (W - c_k)) x_j - dt sum_t w_t x_{j + o_t}
+// where the taps (o_t, w_t) are the bilinear interpolation weights of the truncated Scheme-2
+// endpoints scaled by A_p/(2h), B_p/(2h) (Proposition 2.2, Eq. Lhat), and
+// W = sum_p (A_p + B_p)/(2h).  Rows farther than B cells from the boundary in both
+// dimensions are never truncated and share one table entry per control; rows in the band
+// get one entry per (distance to the low side, distance to the high side) pair, so every
+// row of the grid reads its stencil from a small table that stays in L1/L2.
+//
+// Coarse levels: row I of A_l = R A_{l-1} P is either "class k" (every row of level l-1 in
+// the support of the full-weighting stencil at 2I is a class-k interior row, so the row is
+// the translation-invariant Galerkin stencil S_k^l) or explicit (a dense window of
+// (2 R_l + 1)^2 coefficients around I).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define SL_HD __host__ __device__ __forceinline__
+
+namespace sl {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxCand = 8;       // argmin candidate list length (then full FP64 fallback)
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs: grid of the vector kernels / reductions
+constexpr int kCoarsestMax = 256; // largest coarsest level solved by a dense inverse
+
+// Boundary-distance class of a coordinate i in [1, n-2] (band width B).
+SL_HD int class_q(int i, int n, int B) {
+  if (n - 1 >= 2 * B) {
+    if (i < B) return i;
+    int e = n - 1 - i;
+    if (e < B) return 2 * B - e;
+    return B;
+  }
+  return i;
+}
+
+// A representative coordinate of class q.
+SL_HD int class_rep(int q, int n, int B) {
+  if (n - 1 >= 2 * B) {
+    if (q <= B) return q;
+    return n - 1 - (2 * B - q);
+  }
+  return q;
+}
+
+SL_HD int class_count(int n, int B) { return (n - 1 >= 2 * B) ? 2 * B : n - 1; }
+
+// Device view of the fine-level stencil tables (entry e = (k*Q + q2)*Q + q1).
+struct FineTab {
+  int n, m, B, Q, tmax, K;
+  const int32_t *lin;     // [e*tmax + t] linear offset dy*n + dx
+  const double *w64;      // [e*tmax + t] tap weight (already / (2h))
+  const float *w32;
+  const uint8_t *nt;      // [e] number of taps
+  const double *W64;      // [e] sum_p (A_p + B_p)/(2h)
+  const float *W32;
+  const double *ws64;     // [e] weight of the tap at offset 0 (node itself)
+  const float *ws32;
+  const double *c64;      // [K] discount
+  const float *c32;
+};
+
+template <typename T> SL_HD const T *tab_w(const FineTab &t);
+template <> SL_HD const double *tab_w<double>(const FineTab &t) { return t.w64; }
+template <> SL_HD const float *tab_w<float>(const FineTab &t) { return t.w32; }
+template <typename T> SL_HD const T *tab_W(const FineTab &t);
+template <> SL_HD const double *tab_W<double>(const FineTab &t) { return t.W64; }
+template <> SL_HD const float *tab_W<float>(const FineTab &t) { return t.W32; }
+template <typename T> SL_HD const T *tab_ws(const FineTab &t);
+template <> SL_HD const double *tab_ws<double>(const FineTab &t) { return t.ws64; }
+template <> SL_HD const float *tab_ws<float>(const FineTab &t) { return t.ws32; }
+template <typename T> SL_HD const T *tab_c(const FineTab &t);
+template <> SL_HD const double *tab_c<double>(const FineTab &t) { return t.c64; }
+template <> SL_HD const float *tab_c<float>(const FineTab &t) { return t.c32; }
+
+// Device view of one coarse level.
+template <typename T>
+struct CoarseLev {
+  int n, m, R, win;        // nodes per dim, interior per dim, window reach, (2R+1)^2
+  const int32_t *cls;      // [m*m] >= 0: class k; < 0: explicit slot -cls-1
+  // class tables: sparse taps of S_k (entry k), including the centre coefficient
+  const int32_t *clin;     // [k*ctmax + t]
+  const T *cw;             // [k*ctmax + t]
+  const int32_t *cnt;      // [k]
+  const T *cdiag;          // [k]
+  int ctmax;
+  // explicit rows
+  const T *ewin;           // [e*cap + slot], e = (dy+R)*(2R+1) + (dx+R)
+  const int32_t *erow;     // [slot] linear full-grid index of the row
+  int cap;
+};
+
+// Full-weighting and bilinear 1-D weights: R uses (1, 2, 1)/4 per dimension, P uses 1 at
+// even fine indices and (1/2, 1/2) at odd ones.
+SL_HD double fw_weight(int a) { return a == 0 ? 0.5 : 0.25; }
+
+// Scatters one level-(l-1) matrix entry v at column j (level-(l-1) coordinates) of the fine
+// row 2I + a into the Galerkin window of coarse row I:
+// window[J - I] += R_a * v * P_{j,J} over the bilinear parents J of j.
+template <typename T>
+SL_HD void rap_scatter(T *win, int R, int I1, int I2, int j1, int j2, T rv) {
+  int W = 2 * R + 1;
+  int J1a, J1b, J2a, J2b;
+  T p1a, p1b, p2a, p2b;
+  if ((j1 & 1) == 0) { J1a = j1 >> 1; J1b = J1a; p1a = T(1); p1b = T(0); }
+  else { J1a = (j1 - 1) >> 1; J1b = J1a + 1; p1a = T(0.5); p1b = T(0.5); }
+  if ((j2 & 1) == 0) { J2a = j2 >> 1; J2b = J2a; p2a = T(1); p2b = T(0); }
+  else { J2a = (j2 - 1) >> 1; J2b = J2a + 1; p2a = T(0.5); p2b = T(0.5); }
+  int d1a = J1a - I1 + R, d1b = J1b - I1 + R, d2a = J2a - I2 + R, d2b = J2b - I2 + R;
+  win[d2a * W + d1a] += rv * p1a * p2a;
+  if (p1b != T(0)) win[d2a * W + d1b] += rv * p1b * p2a;
+  if (p2b != T(0)) {
+    win[d2b * W + d1a] += rv * p1a * p2b;
+    if (p1b != T(0)) win[d2b * W + d1b] += rv * p1b * p2b;
+  }
+}
+
+// Scalars of one BiCGSTAB run, kept in device memory so that no iteration needs the host.
+struct BicgScalars {
+  double rho, rho_old, alpha, omega;
+  double rv, ts, tt, ss, rr;   // (r^, v), (t, s), (t, t), (s, s), (r, r)
+  double bnorm2;               // ||b||^2 of the system
+  double tolrel2;              // tol^2 (set by the host before the run)
+  double tol2;                 // (tol ||b||)^2
+  double rmax, bmax;           // ||r||_inf, ||b||_inf (true-residual checks)
+  int breakdown;               // 1: rho or (r^, v) or (t, t) vanished
+  int nonfinite;               // 1: a NaN / Inf was seen
+};
+
+}  // namespace sl

@@ -1,0 +1,172 @@
+// sl_geometry.cpp - Scheme-2 stencils with boundary truncation, evaluated once in FP64.
+//
+// For control k and a node at integer grid index i = (i1, i2), every diffusion column
+// sigma_p contributes the directions +-s_p with s_p = sigma_p / sqrt(h) in grid-index units
+// (the stencil length of Eq. def_mAlpha), and a drift b contributes s = b (y = h b).  The
+// truncation factor mu in (0, 1] is the largest value keeping i + mu s inside [0, n-1]^2
+// (Proposition 2.2); a component that hits the boundary is placed exactly on it.  Weights:
+// A_p = 2/(mu+^2 + mu+ mu-), B_p = 2/(mu-^2 + mu- mu+) (Eq. eqn_Ap), A = B = 1/mu for the
+// drift (Eq. eqn_APp1).  The endpoint value is the bilinear interpolant of the four nodes of
+// its cell (Eq. monotone_int); each tap weight is A_p w_i / (2h) (Eq. Lhat) and
+// W = sum_p (A_p + B_p) / (2h).
+#include "sl_geometry.h"
+
+#include <algorithm>
+#include <cmath>
+#include <limits>
+#include <map>
+#include <stdexcept>
+#include <utility>
+
+#include "sl_common.cuh"
+
+namespace sl {
+namespace {
+
+struct Endpoint {
+  double mu, z1, z2;
+};
+
+Endpoint truncate_endpoint(double i1, double i2, double s1, double s2, int n) {
+  const double top = double(n - 1);
+  const double inf = std::numeric_limits<double>::infinity();
+  double b1 = inf, b2 = inf;
+  if (s1 > 0) b1 = (top - i1) / s1; else if (s1 < 0) b1 = (0.0 - i1) / s1;
+  if (s2 > 0) b2 = (top - i2) / s2; else if (s2 < 0) b2 = (0.0 - i2) / s2;
+  Endpoint e;
+  e.mu = std::min(1.0, std::min(b1, b2));
+  e.z1 = i1 + e.mu * s1;
+  e.z2 = i2 + e.mu * s2;
+  if (e.mu < 1.0) {
+    if (b1 == e.mu) e.z1 = s1 > 0 ? top : 0.0;
+    if (b2 == e.mu) e.z2 = s2 > 0 ? top : 0.0;
+  }
+  return e;
+}
+
+using TapMap = std::map<std::pair<int, int>, double>;  // (dy, dx) -> weight
+
+void add_bilinear(TapMap &taps, int i1, int i2, double z1, double z2, int n, double scale) {
+  double c1 = std::min(std::max(std::floor(z1), 0.0), double(n - 2));
+  double c2 = std::min(std::max(std::floor(z2), 0.0), double(n - 2));
+  double t1 = z1 - c1, t2 = z2 - c2;
+  int a1 = int(c1) - i1, a2 = int(c2) - i2;
+  const double wts[4] = {(1 - t1) * (1 - t2), t1 * (1 - t2), (1 - t1) * t2, t1 * t2};
+  const int o1[4] = {0, 1, 0, 1}, o2[4] = {0, 0, 1, 1};
+  for (int c = 0; c < 4; ++c) {
+    if (wts[c] == 0.0) continue;
+    taps[{a2 + o2[c], a1 + o1[c]}] += wts[c] * scale;
+  }
+}
+
+}  // namespace
+
+FineTabHost build_fine_tables(int n, double h, int K, int P, const double *sigma,
+                              const double *b, const double *c) {
+  FineTabHost t;
+  t.n = n;
+  t.m = n - 2;
+  t.K = K;
+  const double sqh = std::sqrt(h);
+  // band width: one more than the longest untruncated displacement component
+  double reach = 0.0;
+  for (int k = 0; k < K; ++k) {
+    for (int p = 0; p < P; ++p)
+      for (int d = 0; d < 2; ++d)
+        reach = std::max(reach, std::fabs(sigma[(k * 2 + d) * P + p]) / sqh);
+    if (b)
+      for (int d = 0; d < 2; ++d) reach = std::max(reach, std::fabs(b[k * 2 + d]));
+  }
+  t.B = int(std::ceil(reach)) + 1;
+  t.Q = class_count(n, t.B);
+  t.tmax = 4 * (2 * P + (b ? 1 : 0));
+  const int E = K * t.Q * t.Q;
+  t.dx.assign(size_t(E) * t.tmax, 0);
+  t.dy.assign(size_t(E) * t.tmax, 0);
+  t.w.assign(size_t(E) * t.tmax, 0.0);
+  t.nt.assign(E, 0);
+  t.W.assign(E, 0.0);
+  t.ws.assign(E, 0.0);
+  t.c.assign(K, 0.0);
+  t.Wmax_class.assign(size_t(t.Q) * t.Q, 0.0);
+  if (c)
+    for (int k = 0; k < K; ++k) t.c[k] = c[k];
+  const int qlo = 1;  // class 0 is never used by an interior coordinate
+  for (int k = 0; k < K; ++k) {
+    for (int q2 = qlo; q2 < t.Q; ++q2) {
+      for (int q1 = qlo; q1 < t.Q; ++q1) {
+        const int i1 = class_rep(q1, n, t.B), i2 = class_rep(q2, n, t.B);
+        if (i1 < 1 || i1 > n - 2 || i2 < 1 || i2 > n - 2) continue;
+        TapMap taps;
+        double W = 0.0;
+        for (int p = 0; p < P; ++p) {
+          const double s1 = sigma[(k * 2 + 0) * P + p] / sqh;
+          const double s2 = sigma[(k * 2 + 1) * P + p] / sqh;
+          Endpoint ep = truncate_endpoint(i1, i2, s1, s2, n);
+          Endpoint em = truncate_endpoint(i1, i2, -s1, -s2, n);
+          const double A = 2.0 / (ep.mu * ep.mu + ep.mu * em.mu);
+          const double Bw = 2.0 / (em.mu * em.mu + em.mu * ep.mu);
+          add_bilinear(taps, i1, i2, ep.z1, ep.z2, n, A / (2.0 * h));
+          add_bilinear(taps, i1, i2, em.z1, em.z2, n, Bw / (2.0 * h));
+          W += (A + Bw) / (2.0 * h);
+        }
+        if (b) {
+          Endpoint e = truncate_endpoint(i1, i2, b[k * 2 + 0], b[k * 2 + 1], n);
+          const double AB = 2.0 / e.mu;
+          add_bilinear(taps, i1, i2, e.z1, e.z2, n, AB / (2.0 * h));
+          W += AB / (2.0 * h);
+        }
+        const int e = t.entry(k, q1, q2);
+        if (int(taps.size()) > t.tmax) throw std::runtime_error("stencil table overflow");
+        int slot = 0;
+        for (const auto &kv : taps) {
+          const int ddy = kv.first.first, ddx = kv.first.second;
+          t.dy[size_t(e) * t.tmax + slot] = ddy;
+          t.dx[size_t(e) * t.tmax + slot] = ddx;
+          t.w[size_t(e) * t.tmax + slot] = kv.second;
+          if (ddx == 0 && ddy == 0) t.ws[e] = kv.second;
+          t.R0 = std::max(t.R0, std::max(std::abs(ddx), std::abs(ddy)));
+          ++slot;
+        }
+        t.nt[e] = uint8_t(slot);
+        t.W[e] = W;
+        double &wm = t.Wmax_class[size_t(q2) * t.Q + q1];
+        wm = std::max(wm, W);
+      }
+    }
+  }
+  return t;
+}
+
+std::vector<double> fine_interior_window(const FineTabHost &t, int k, double dt) {
+  const int R = t.R0, Wd = 2 * R + 1;
+  std::vector<double> win(size_t(Wd) * Wd, 0.0);
+  const int e = t.entry(k, class_q(t.B, t.n, t.B), class_q(t.B, t.n, t.B));
+  win[size_t(R) * Wd + R] = 1.0 + dt * (t.W[e] - t.c[k]);
+  for (int s = 0; s < t.nt[e]; ++s) {
+    const size_t ix = size_t(e) * t.tmax + s;
+    win[size_t(t.dy[ix] + R) * Wd + (t.dx[ix] + R)] -= dt * t.w[ix];
+  }
+  return win;
+}
+
+std::vector<double> rap_class_window(const std::vector<double> &prev, int Rprev, int R) {
+  // Coarse row I = (I0, I0) with all nine level-(l-1) rows 2I + a having the window `prev`.
+  const int Wp = 2 * Rprev + 1, Wd = 2 * R + 1;
+  std::vector<double> win(size_t(Wd) * Wd, 0.0);
+  const int I0 = 4 * (R + Rprev + 4);
+  for (int a2 = -1; a2 <= 1; ++a2)
+    for (int a1 = -1; a1 <= 1; ++a1) {
+      const double ra = fw_weight(a1) * fw_weight(a2);
+      const int i1 = 2 * I0 + a1, i2 = 2 * I0 + a2;
+      for (int o2 = -Rprev; o2 <= Rprev; ++o2)
+        for (int o1 = -Rprev; o1 <= Rprev; ++o1) {
+          const double v = prev[size_t(o2 + Rprev) * Wp + (o1 + Rprev)];
+          if (v == 0.0) continue;
+          rap_scatter<double>(win.data(), R, I0, I0, i1 + o1, i2 + o2, ra * v);
+        }
+    }
+  return win;
+}
+
+}  // namespace sl

@@ -1,0 +1,35 @@
+// sl_geometry.h - host-side construction of the Scheme-2 stencil tables (FP64, at create
+// time) and of the translation-invariant Galerkin class stencils (per hierarchy build).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace sl {
+
+struct FineTabHost {
+  int n = 0, m = 0, B = 0, Q = 0, tmax = 0, K = 0;
+  int R0 = 0;                       // largest |dx|, |dy| of any tap
+  std::vector<int32_t> dx, dy;      // [e*tmax + t]
+  std::vector<double> w;            // [e*tmax + t]
+  std::vector<uint8_t> nt;          // [e]
+  std::vector<double> W, ws;        // [e]
+  std::vector<double> c;            // [K]
+  std::vector<double> Wmax_class;   // [q2*Q + q1] max_k W of that class (argmin screen bound)
+  int entry(int k, int q1, int q2) const { return (k * Q + q2) * Q + q1; }
+};
+
+// sigma: K*2*P (column p of control k is (sigma[(k*2)*P+p], sigma[(k*2+1)*P+p])),
+// b: K*2 or null, c: K or null; grid n x n with spacing h.
+FineTabHost build_fine_tables(int n, double h, int K, int P, const double *sigma,
+                              const double *b, const double *c);
+
+// Dense (2R+1)^2 window of the level-l class-k Galerkin stencil, built from the level-(l-1)
+// class-k row `prev` (dense window of reach Rprev; for level 1 the fine interior row).
+std::vector<double> rap_class_window(const std::vector<double> &prev, int Rprev, int R);
+
+// Fine interior row of control k as a dense window of reach R0 (matrix coefficients:
+// centre 1 + dt (W - c) - dt w_self, off-centre -dt w).
+std::vector<double> fine_interior_window(const FineTabHost &t, int k, double dt);
+
+}  // namespace sl

@@ -1,0 +1,389 @@
+// sl_krylov.cu - BiCGSTAB vector updates with fused dot products (van der Vorst's method,
+// right preconditioning), conversions and norms.
+//
+// Every reduction writes one FP64 partial per block; the last block to finish (atomic ticket)
+// adds the partials in block order, so results do not depend on scheduling, and then updates
+// the scalars of the iteration in device memory (alpha, omega, rho), so that the host reads
+// only the residual norm once per iteration.
+#include <atomic>
+#include <cmath>
+
+#include "sl_launch.h"
+
+namespace sl {
+
+constexpr int kVecThreads = 256;
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of NF values; returns the sums in thread 0.
+template <int NF>
+__device__ __forceinline__ void block_sum(double (&v)[NF]) {
+  __shared__ double sh[NF][kVecThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    v[f] = warp_sum(v[f]);
+    if (lane == 0) sh[f][wid] = v[f];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      double s = 0.0;
+      for (int w = 0; w < kVecThreads / 32; ++w) s += sh[f][w];
+      v[f] = s;
+    }
+  }
+}
+
+__device__ void apply_post(int post, const double *tot, BicgScalars *S) {
+  bool bad = false;
+  switch (post) {
+    case POST_RHO_INIT:
+      S->rho = tot[0];
+      S->rr = tot[1];
+      S->rho_old = 1.0;
+      S->alpha = 1.0;
+      S->omega = 1.0;
+      S->breakdown = 0;
+      S->nonfinite = 0;
+      bad = !isfinite(tot[0]) || !isfinite(tot[1]);
+      break;
+    case POST_ALPHA:
+      S->rv = tot[0];
+      bad = !isfinite(tot[0]);
+      if (tot[0] == 0.0 || fabs(S->rho) < 1e-300) {
+        S->breakdown = 1;
+        S->alpha = 0.0;
+      } else {
+        S->alpha = S->rho / tot[0];
+      }
+      break;
+    case POST_SS:
+      S->ss = tot[0];
+      bad = !isfinite(tot[0]);
+      break;
+    case POST_OMEGA:
+      S->ts = tot[0];
+      S->tt = tot[1];
+      bad = !isfinite(tot[0]) || !isfinite(tot[1]);
+      if (S->ss <= S->tol2) S->omega = 0.0;          // s already small: x += alpha p^, r = s
+      else if (tot[1] == 0.0) { S->omega = 0.0; S->breakdown = 1; }
+      else S->omega = tot[0] / tot[1];
+      break;
+    case POST_RHO:
+      S->rho_old = S->rho;
+      S->rho = tot[0];
+      S->rr = tot[1];
+      bad = !isfinite(tot[0]) || !isfinite(tot[1]);
+      if (S->omega == 0.0 && S->ss > S->tol2) S->breakdown = 1;
+      break;
+    case POST_BNORM:
+      S->bnorm2 = tot[0];
+      S->tol2 = S->tolrel2 * tot[0];
+      bad = !isfinite(tot[0]);
+      break;
+    case POST_RR:
+      S->rr = tot[0];
+      bad = !isfinite(tot[0]);
+      break;
+  }
+  if (bad) S->nonfinite = 1;
+}
+
+template <int NF>
+__device__ void finish(double (&v)[NF], int post, BicgScalars *S, double *partials,
+                       unsigned *counter) {
+  block_sum<NF>(v);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) partials[blockIdx.x * NF + f] = v[f];
+    __threadfence();
+    const unsigned ticket = atomicAdd(counter, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double tot[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) tot[f] = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) tot[f] += ((volatile double *)partials)[b * NF + f];
+    apply_post(post, tot, S);
+    *counter = 0u;
+  }
+}
+
+// (a, b) and optionally (c, d)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_dot2(const T *__restrict__ a, const T *__restrict__ b,
+                                                      const T *__restrict__ c, const T *__restrict__ d,
+                                                      size_t N, int post, BicgScalars *S,
+                                                      double *partials, unsigned *counter) {
+  double v[2] = {0.0, 0.0};
+  T s0 = T(0), s1 = T(0);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
+    s0 = fma(a[i], b[i], s0);
+    if (c) s1 = fma(c[i], d[i], s1);
+  }
+  v[0] = double(s0);
+  v[1] = double(s1);
+  finish<2>(v, post, S, partials, counter);
+}
+
+template <typename T>
+void launch_dot2(const T *a, const T *b, const T *c, const T *d, size_t N, int post,
+                 BicgScalars *S, double *partials, unsigned *counter, cudaStream_t s) {
+  note_launch();
+  k_dot2<T><<<kRedBlocks, kVecThreads, 0, s>>>(a, b, c, d, N, post, S, partials, counter);
+}
+
+// p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega); first iteration p = r.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_bicg_p(T *__restrict__ p, const T *__restrict__ r,
+                                                        const T *__restrict__ v, size_t N, int first,
+                                                        const BicgScalars *S) {
+  const double beta_d = first ? 0.0 : (S->rho / S->rho_old) * (S->alpha / S->omega);
+  const T beta = T(beta_d), om = T(S->omega);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
+    if (first) p[i] = r[i];
+    else p[i] = r[i] + beta * (p[i] - om * v[i]);
+  }
+}
+
+template <typename T>
+void launch_bicg_p(T *p, const T *r, const T *v, size_t N, int first, const BicgScalars *S,
+                   cudaStream_t s) {
+  note_launch();
+  k_bicg_p<T><<<kRedBlocks, kVecThreads, 0, s>>>(p, r, v, N, first, S);
+}
+
+// s = r - alpha v, (s, s)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_bicg_s(T *__restrict__ sv, const T *__restrict__ r,
+                                                        const T *__restrict__ v, size_t N, BicgScalars *S,
+                                                        double *partials, unsigned *counter) {
+  const T alpha = T(S->alpha);
+  T acc = T(0);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
+    const T si = r[i] - alpha * v[i];
+    sv[i] = si;
+    acc = fma(si, si, acc);
+  }
+  double vv[1] = {double(acc)};
+  finish<1>(vv, POST_SS, S, partials, counter);
+}
+
+template <typename T>
+void launch_bicg_s(T *sv, const T *r, const T *v, size_t N, BicgScalars *S, double *partials,
+                   unsigned *counter, cudaStream_t s) {
+  note_launch();
+  k_bicg_s<T><<<kRedBlocks, kVecThreads, 0, s>>>(sv, r, v, N, S, partials, counter);
+}
+
+// x += alpha p^ + omega s^ ; r = s - omega t ; (r^, r), (r, r)
+template <typename T, typename TX>
+__global__ void __launch_bounds__(kVecThreads) k_bicg_xr(TX *__restrict__ x, const T *__restrict__ phat,
+                                                         const T *__restrict__ shat, const T *__restrict__ sv,
+                                                         const T *__restrict__ t, T *__restrict__ r,
+                                                         const T *__restrict__ rhat, size_t N,
+                                                         BicgScalars *S, double *partials,
+                                                         unsigned *counter) {
+  const double alpha = S->alpha, omega = S->omega;
+  const T om = T(omega);
+  T a0 = T(0), a1 = T(0);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
+    x[i] = x[i] + TX(alpha) * TX(phat[i]) + TX(omega) * TX(shat[i]);
+    const T ri = sv[i] - om * t[i];
+    r[i] = ri;
+    a0 = fma(rhat[i], ri, a0);
+    a1 = fma(ri, ri, a1);
+  }
+  double vv[2] = {double(a0), double(a1)};
+  finish<2>(vv, POST_RHO, S, partials, counter);
+}
+
+template <typename T, typename TX>
+void launch_bicg_xr(TX *x, const T *phat, const T *shat, const T *sv, const T *t, T *r,
+                    const T *rhat, size_t N, BicgScalars *S, double *partials, unsigned *counter,
+                    cudaStream_t s) {
+  note_launch();
+  k_bicg_xr<T, TX><<<kRedBlocks, kVecThreads, 0, s>>>(x, phat, shat, sv, t, r, rhat, N, S, partials,
+                                                      counter);
+}
+
+__global__ void k_init_scalars(BicgScalars *S, double tolrel2) {
+  BicgScalars z = {};
+  z.rho_old = 1.0;
+  z.alpha = 1.0;
+  z.omega = 1.0;
+  z.tolrel2 = tolrel2;
+  *S = z;
+}
+void launch_init_scalars(BicgScalars *S, double tolrel2, cudaStream_t s) {
+  note_launch();
+  k_init_scalars<<<1, 1, 0, s>>>(S, tolrel2);
+}
+
+template <typename T>
+__global__ void k_fill(T *x, size_t N, T v) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x)
+    x[i] = v;
+}
+template <typename T>
+void launch_fill(T *x, size_t N, T v, cudaStream_t s) {
+  note_launch();
+  k_fill<T><<<kRedBlocks, kVecThreads, 0, s>>>(x, N, v);
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin *__restrict__ x, Tout *__restrict__ y, size_t N) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x)
+    y[i] = Tout(x[i]);
+}
+template <typename Tin, typename Tout>
+void launch_convert(const Tin *x, Tout *y, size_t N, cudaStream_t s) {
+  note_launch();
+  k_convert<Tin, Tout><<<kRedBlocks, kVecThreads, 0, s>>>(x, y, N);
+}
+
+__global__ void k_add_f32(double *__restrict__ x, const float *__restrict__ e, size_t N) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x)
+    x[i] += double(e[i]);
+}
+void launch_add_f32_to_f64(double *x, const float *e, size_t N, cudaStream_t s) {
+  note_launch();
+  k_add_f32<<<kRedBlocks, kVecThreads, 0, s>>>(x, e, N);
+}
+
+// Sum of squares and max-abs of one vector: which = 0 stores (||b||^2, ||b||_inf) and the
+// stop threshold; which = 1 stores (||r||^2, ||r||_inf).
+__global__ void __launch_bounds__(kVecThreads) k_norms(const double *__restrict__ a, size_t N, int which,
+                                                       BicgScalars *S, double *partials,
+                                                       unsigned *counter) {
+  double s2 = 0.0, mx = 0.0;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
+    s2 = fma(a[i], a[i], s2);
+    mx = fmax(mx, fabs(a[i]));
+    if (!(a[i] == a[i])) mx = INFINITY;
+  }
+  s2 = warp_sum(s2);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ double ss[kVecThreads / 32], sm[kVecThreads / 32];
+  __shared__ bool last;
+  if ((threadIdx.x & 31) == 0) { ss[threadIdx.x >> 5] = s2; sm[threadIdx.x >> 5] = mx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s2 = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) { s2 += ss[w]; mx = fmax(mx, sm[w]); }
+    partials[2 * blockIdx.x] = s2;
+    partials[2 * blockIdx.x + 1] = mx;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double T2 = 0.0, M = 0.0;
+    for (unsigned b2 = 0; b2 < gridDim.x; ++b2) {
+      T2 += ((volatile double *)partials)[2 * b2];
+      M = fmax(M, ((volatile double *)partials)[2 * b2 + 1]);
+    }
+    if (which == 0) {
+      S->bnorm2 = T2;
+      S->bmax = M;
+      S->tol2 = S->tolrel2 * T2;
+    } else {
+      S->rr = T2;
+      S->rmax = M;
+    }
+    if (!isfinite(T2) || !isfinite(M)) S->nonfinite = 1;
+    *counter = 0u;
+  }
+}
+void launch_norms(const double *a, size_t N, int which, BicgScalars *S, double *partials,
+                  unsigned *counter, cudaStream_t s) {
+  note_launch();
+  k_norms<<<kRedBlocks, kVecThreads, 0, s>>>(a, N, which, S, partials, counter);
+}
+
+// out[0] = max_j |a_j - b_j| over interior nodes, out[1] = max_j |a_j| (Howard stop test).
+__global__ void __launch_bounds__(kVecThreads) k_maxabs_diff(const double *__restrict__ a,
+                                                             const double *__restrict__ b, int n,
+                                                             double *out, unsigned *counter,
+                                                             double *partials) {
+  double d = 0.0, x = 0.0;
+  const size_t N = size_t(n) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
+    const int i1 = int(i % n), i2 = int(i / n);
+    if (i1 == 0 || i2 == 0 || i1 == n - 1 || i2 == n - 1) continue;
+    d = fmax(d, fabs(a[i] - b[i]));
+    x = fmax(x, fabs(a[i]));
+    if (!(a[i] == a[i])) d = INFINITY;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  }
+  __shared__ double sd[kVecThreads / 32], sx[kVecThreads / 32];
+  __shared__ bool last;
+  if ((threadIdx.x & 31) == 0) { sd[threadIdx.x >> 5] = d; sx[threadIdx.x >> 5] = x; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < kVecThreads / 32; ++w) { d = fmax(d, sd[w]); x = fmax(x, sx[w]); }
+    partials[2 * blockIdx.x] = d;
+    partials[2 * blockIdx.x + 1] = x;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double D = 0.0, Xm = 0.0;
+    for (unsigned b2 = 0; b2 < gridDim.x; ++b2) {
+      D = fmax(D, ((volatile double *)partials)[2 * b2]);
+      Xm = fmax(Xm, ((volatile double *)partials)[2 * b2 + 1]);
+    }
+    out[0] = D;
+    out[1] = Xm;
+    *counter = 0u;
+  }
+}
+void launch_maxabs_diff(const double *a, const double *b, int n, double *out2, unsigned *counter,
+                        double *partials, cudaStream_t s) {
+  note_launch();
+  k_maxabs_diff<<<kRedBlocks, kVecThreads, 0, s>>>(a, b, n, out2, counter, partials);
+}
+
+#define SL_INST(T)                                                                                 \
+  template void launch_dot2<T>(const T *, const T *, const T *, const T *, size_t, int,            \
+                               BicgScalars *, double *, unsigned *, cudaStream_t);                 \
+  template void launch_bicg_p<T>(T *, const T *, const T *, size_t, int, const BicgScalars *,      \
+                                 cudaStream_t);                                                    \
+  template void launch_bicg_s<T>(T *, const T *, const T *, size_t, BicgScalars *, double *,       \
+                                 unsigned *, cudaStream_t);                                        \
+  template void launch_fill<T>(T *, size_t, T, cudaStream_t);
+SL_INST(double)
+SL_INST(float)
+template void launch_bicg_xr<double, double>(double *, const double *, const double *, const double *,
+                                             const double *, double *, const double *, size_t,
+                                             BicgScalars *, double *, unsigned *, cudaStream_t);
+template void launch_bicg_xr<float, float>(float *, const float *, const float *, const float *,
+                                           const float *, float *, const float *, size_t,
+                                           BicgScalars *, double *, unsigned *, cudaStream_t);
+template void launch_convert<double, float>(const double *, float *, size_t, cudaStream_t);
+template void launch_convert<float, double>(const float *, double *, size_t, cudaStream_t);
+template void launch_fill<int32_t>(int32_t *, size_t, int32_t, cudaStream_t);
+
+}  // namespace sl

@@ -1,0 +1,104 @@
+// sl_launch.h - host launchers of the sm_103a kernels (one declaration per kernel family).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sl_common.cuh"
+
+namespace sl {
+
+// Host-side count of kernel launches issued by the library (all handles).
+void note_launch(int n = 1);
+long long launch_count();
+
+enum FineOp { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_JACOBI0 = 3 };
+
+struct ArgminArgs {
+  FineTab tab;
+  const int32_t *slin;     // [e*tmax + t] offset in the staged tile (dy*SW + dx)
+  const int32_t *off;      // [e*tmax + t] packed (dy << 16) | (dx & 0xffff)
+  const double *X;         // full grid, psi on the boundary
+  const double *F;         // [nf][n*n] source basis values at t
+  const float *F32;
+  const double *phi;       // [K*nf]
+  const float *phi32;
+  const double *phimax;    // [nf] max_k |phi_km|
+  int nf;
+  double tie_rel;
+  double cmax;             // max_k |c_k|
+  const double *Wmax_class;  // [Q*Q]
+  uint8_t *policy;         // in: current, out: improved
+  unsigned long long *changes;
+  int *flags;              // bit 0: non-finite control value
+  int halo, SW, SH;        // staged tile: (32 + 2 halo) x (8 + 2 halo)
+  int screen;
+};
+
+void launch_coef(const double *G, int nf, int nq, const double *tau, const double *Psi, int npsi,
+                 const double *tau_psi, int n, double *F, float *F32, double *Xext, double *Xb,
+                 cudaStream_t s);
+cudaError_t launch_argmin(const ArgminArgs &a, cudaStream_t s);
+
+template <typename T>
+void launch_fine_op(int op, const FineTab &tab, const uint8_t *policy, T dt, T omega,
+                    const T *x, const T *b, T *y, cudaStream_t s);
+
+// r = U_prev - X + dt (L X + c X + f) for the current policy (interior), FP64.
+void launch_hjb_resid(const FineTab &tab, const uint8_t *policy, const double *X,
+                      const double *Uprev, const double *F, const double *phi, int nf, double dt,
+                      double *r, cudaStream_t s);
+
+template <typename T>
+void launch_restrict(const T *rf, int nf, T *bc, int nc, cudaStream_t s);
+template <typename T>
+void launch_prolong_add(const T *xc, int nc, T *xf, int nf, cudaStream_t s);
+
+// coarse levels
+void launch_classify(int level, const FineTab &tab, const uint8_t *policy, const int32_t *cls_prev,
+                     int n_prev, int32_t *cls, int n, int32_t *erow, int *count, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rap_explicit(int level, const FineTab &tab, const int32_t *fine_off,
+                                const uint8_t *policy, T dt, const CoarseLev<T> &prev,
+                                const int32_t *prev_coff, const CoarseLev<T> &cur, int count,
+                                T *ewin_out, cudaStream_t s);
+template <typename T>
+void launch_coarse_op(int op, const CoarseLev<T> &L, int nexpl, T omega, const T *x, const T *b,
+                      T *y, cudaStream_t s);
+template <typename T>
+void launch_coarsest_setup(int level, const FineTab &tab, const uint8_t *policy, T dt,
+                           const CoarseLev<T> &L, const int32_t *coff, double *work, T *Ainv,
+                           cudaStream_t s);
+template <typename T>
+void launch_coarsest_apply(const T *Ainv, int n, const T *b, T *x, cudaStream_t s);
+
+// vectors and reductions
+template <typename T>
+void launch_fill(T *x, size_t N, T v, cudaStream_t s);
+template <typename Tin, typename Tout>
+void launch_convert(const Tin *x, Tout *y, size_t N, cudaStream_t s);
+void launch_add_f32_to_f64(double *x, const float *e, size_t N, cudaStream_t s);
+
+enum Post { POST_RHO_INIT = 0, POST_ALPHA = 1, POST_SS = 2, POST_OMEGA = 3, POST_RHO = 4,
+            POST_BNORM = 5, POST_RR = 6 };
+
+template <typename T>
+void launch_dot2(const T *a, const T *b, const T *c, const T *d, size_t N, int post,
+                 BicgScalars *S, double *partials, unsigned *counter, cudaStream_t s);
+template <typename T>
+void launch_bicg_p(T *p, const T *r, const T *v, size_t N, int first, const BicgScalars *S,
+                   cudaStream_t s);
+template <typename T>
+void launch_bicg_s(T *sv, const T *r, const T *v, size_t N, BicgScalars *S, double *partials,
+                   unsigned *counter, cudaStream_t s);
+template <typename T, typename TX>
+void launch_bicg_xr(TX *x, const T *phat, const T *shat, const T *sv, const T *t, T *r,
+                    const T *rhat, size_t N, BicgScalars *S, double *partials, unsigned *counter,
+                    cudaStream_t s);
+void launch_norms(const double *a, size_t N, int which, BicgScalars *S, double *partials,
+                  unsigned *counter, cudaStream_t s);
+void launch_init_scalars(BicgScalars *S, double tolrel2, cudaStream_t s);
+void launch_maxabs_diff(const double *a, const double *b, int n, double *out2,
+                        unsigned *counter, double *partials, cudaStream_t s);
+
+}  // namespace sl
