@@ -111,6 +111,8 @@ typedef struct {
                            decide in FP64 among the survivors (identical result); 0: all FP64 */
   double rebuild_frac;  /* rebuild the Galerkin hierarchy when more than rebuild_frac * N
                            rows changed control since the last build (0: on any change) */
+  int use_graphs;       /* 1: each BiCGSTAB iteration is one CUDA-graph launch (captured once
+                           per precision and step size); 0: plain stream launches */
 } sl_opts;
 
 typedef struct {
@@ -127,7 +129,7 @@ typedef struct {
 
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 1e-5, ir_max 30, pi_tol 1e-10, pi_max 100,
- * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0. */
+ * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0, use_graphs 1. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every

@@ -50,7 +50,8 @@ class SlOpts(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("krylov_tol", ctypes.c_double),
                 ("kry_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("ir_max", ctypes.c_int),
                 ("pi_tol", ctypes.c_double), ("pi_max", ctypes.c_int), ("tie_rel", ctypes.c_double),
-                ("argmin_screen", ctypes.c_int), ("rebuild_frac", ctypes.c_double)]
+                ("argmin_screen", ctypes.c_int), ("rebuild_frac", ctypes.c_double),
+                ("use_graphs", ctypes.c_int)]
 
 
 class SlStats(ctypes.Structure):

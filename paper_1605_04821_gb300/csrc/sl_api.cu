@@ -20,6 +20,7 @@ namespace {
 
 struct CoarseBuf {
   int n = 0, m = 0, R = 0, win = 0, cap = 0, nexpl = 0, ctmax = 0;
+  int *d_nexpl = nullptr;  // explicit-row count on the device (read by the explicit kernels)
   int32_t *cls = nullptr, *erow = nullptr, *clin = nullptr, *coff = nullptr, *cnt = nullptr;
   double *ewin64 = nullptr, *cw64 = nullptr, *cdiag64 = nullptr;
   float *ewin32 = nullptr, *cw32 = nullptr, *cdiag32 = nullptr;
@@ -34,6 +35,12 @@ template <> float *pick<float>(double *, float *b) { return b; }
 struct VBuf {  // V-cycle vectors of one level
   double *x64 = nullptr, *t64 = nullptr, *r64 = nullptr, *b64 = nullptr;
   float *x32 = nullptr, *t32 = nullptr, *r32 = nullptr, *b32 = nullptr;
+};
+
+struct IterGraph {  // one captured BiCGSTAB iteration
+  cudaGraphExec_t exec = nullptr;
+  double dt = -1.0;
+  long long kernels = 0;
 };
 
 struct KBuf {  // BiCGSTAB vectors on the finest level
@@ -84,6 +91,8 @@ struct sl_hjb {
   unsigned *counter = nullptr;
   unsigned long long *d_changes = nullptr, *h_changes = nullptr;
   int *d_flags = nullptr, *h_flags = nullptr, *d_count = nullptr, *h_count = nullptr;
+  IterGraph graph[2];           // [precision]
+  cudaStream_t cap_stream = nullptr;
   std::vector<void *> allocs;
   std::string err;
   sl_status sticky = SL_OK;
@@ -296,10 +305,10 @@ sl_status build_hierarchy_T(sl_hjb *h, double dt, cudaStream_t s) {
   for (int l = 1; l < h->L; ++l) {
     CoarseBuf &c = h->cl[l];
     CoarseBuf &p = h->cl[l - 1];
-    CK(cudaMemsetAsync(h->d_count, 0, sizeof(int), s));
-    launch_classify(l, h->tab, h->policy, p.cls, p.n, c.cls, c.n, c.erow, h->d_count, s);
+    CK(cudaMemsetAsync(c.d_nexpl, 0, sizeof(int), s));
+    launch_classify(l, h->tab, h->policy, p.cls, p.n, c.cls, c.n, c.erow, c.d_nexpl, s);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(h->h_count, h->d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->h_count, c.d_nexpl, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     c.nexpl = *h->h_count;
     CoarseLev<T> prevv = lev_view<T>(h, l - 1), curv = lev_view<T>(h, l);
@@ -334,7 +343,7 @@ void level_op(sl_hjb *h, int l, int op, double dt, const T *x, const T *b, T *y,
   if (l == 0)
     launch_fine_op<T>(op, h->tab, h->policy, T(dt), T(h->o.omega), x, b, y, s);
   else
-    launch_coarse_op<T>(op, lev_view<T>(h, l), h->cl[l].nexpl, T(h->o.omega), x, b, y, s);
+    launch_coarse_op<T>(op, lev_view<T>(h, l), h->cl[l].d_nexpl, T(h->o.omega), x, b, y, s);
 }
 
 template <typename T>
@@ -389,26 +398,79 @@ sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) 
 // while the Krylov vectors are FP32: TX / T).  On entry r holds the initial residual and S
 // carries ||b||^2 and the stop threshold (tol ||b||)^2.  Returns SL_OK on convergence,
 // SL_ENOCONV_KRYLOV at the cap, SL_EBREAKDOWN, or SL_ENAN; only SL_ENAN is recorded as an error.
+// The work of one BiCGSTAB iteration (no host synchronisation inside).
+template <typename T, typename TX>
+sl_status issue_iteration(sl_hjb *h, double dt, TX *x, T *r, T *rh, T *p, T *v, T *sv, T *t, T *ph,
+                          T *sh, BicgScalars *S, cudaStream_t s) {
+  const size_t N = NN(h, 0);
+  launch_bicg_p<T>(p, r, v, N, 0, S, s);
+  sl_status st = vcycle<T>(h, 0, dt, p, ph, s);
+  if (st != SL_OK) return st;
+  level_op<T>(h, 0, OP_APPLY, dt, ph, nullptr, v, s);
+  launch_dot2<T>(rh, v, nullptr, nullptr, N, POST_ALPHA, S, h->partials, h->counter, s);
+  launch_bicg_s<T>(sv, r, v, N, S, h->partials, h->counter, s);
+  st = vcycle<T>(h, 0, dt, sv, sh, s);
+  if (st != SL_OK) return st;
+  level_op<T>(h, 0, OP_APPLY, dt, sh, nullptr, t, s);
+  launch_dot2<T>(t, sv, t, t, N, POST_OMEGA, S, h->partials, h->counter, s);
+  launch_bicg_xr<T, TX>(x, ph, sh, sv, t, r, rh, N, S, h->partials, h->counter, s);
+  CK(cudaGetLastError());
+  return SL_OK;
+}
+
+// Captures one iteration into a CUDA graph (once per precision and step size: pointers,
+// launch shapes and dt are fixed; counts and scalars live in device memory).
+template <typename T, typename TX>
+sl_status ensure_graph(sl_hjb *h, int prec, double dt, TX *x, T *r, T *rh, T *p, T *v, T *sv, T *t,
+                       T *ph, T *sh, BicgScalars *S) {
+  IterGraph &g = h->graph[prec];
+  if (g.exec && g.dt == dt) return SL_OK;
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  const long long before = launch_count();
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  sl_status st = issue_iteration<T, TX>(h, dt, x, r, rh, p, v, sv, t, ph, sh, S, h->cap_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (st != SL_OK) return st;
+  CK(e);
+  g.kernels = launch_count() - before;
+  note_launch(int(-g.kernels));  // captured, not executed
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+  g.dt = dt;
+  return SL_OK;
+}
+
+// Right-preconditioned BiCGSTAB for A e = r0 with x += e accumulated in place (x may be FP64
+// while the Krylov vectors are FP32: TX / T).  On entry r holds the initial residual and S
+// carries ||b||^2 and the stop threshold (tol ||b||)^2.  Returns SL_OK on convergence,
+// SL_ENOCONV_KRYLOV at the cap, SL_EBREAKDOWN, or SL_ENAN; only SL_ENAN is recorded as an error.
+// Each iteration is one CUDA-graph launch followed by a read of the residual norm.
 template <typename T, typename TX>
 sl_status bicgstab(sl_hjb *h, double dt, TX *x, T *r, T *rh, T *p, T *v, T *sv, T *t, T *ph, T *sh,
                    BicgScalars *S, int maxit, int *iters, cudaStream_t s) {
   const size_t N = NN(h, 0);
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  if (h->o.use_graphs) {
+    sl_status st = ensure_graph<T, TX>(h, prec, dt, x, r, rh, p, v, sv, t, ph, sh, S);
+    if (st != SL_OK) return st;
+  }
   CK(cudaMemcpyAsync(rh, r, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
   launch_dot2<T>(r, r, r, r, N, POST_RHO_INIT, S, h->partials, h->counter, s);
   *iters = 0;
   for (int it = 1; it <= maxit; ++it) {
-    launch_bicg_p<T>(p, r, v, N, it == 1, S, s);
-    sl_status st = vcycle<T>(h, 0, dt, p, ph, s);
-    if (st != SL_OK) return st;
-    level_op<T>(h, 0, OP_APPLY, dt, ph, nullptr, v, s);
-    launch_dot2<T>(rh, v, nullptr, nullptr, N, POST_ALPHA, S, h->partials, h->counter, s);
-    launch_bicg_s<T>(sv, r, v, N, S, h->partials, h->counter, s);
-    st = vcycle<T>(h, 0, dt, sv, sh, s);
-    if (st != SL_OK) return st;
-    level_op<T>(h, 0, OP_APPLY, dt, sh, nullptr, t, s);
-    launch_dot2<T>(t, sv, t, t, N, POST_OMEGA, S, h->partials, h->counter, s);
-    launch_bicg_xr<T, TX>(x, ph, sh, sv, t, r, rh, N, S, h->partials, h->counter, s);
-    CK(cudaGetLastError());
+    if (h->o.use_graphs) {
+      CK(cudaGraphLaunch(h->graph[prec].exec, s));
+      note_launch(int(h->graph[prec].kernels));
+    } else {
+      sl_status st = issue_iteration<T, TX>(h, dt, x, r, rh, p, v, sv, t, ph, sh, S, s);
+      if (st != SL_OK) return st;
+    }
     CK(cudaMemcpyAsync(h->hS, S, sizeof(BicgScalars), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     *iters = it;
@@ -589,6 +651,7 @@ void sl_opts_default(sl_opts *o) {
   o->tie_rel = 1e-12;
   o->argmin_screen = 0;
   o->rebuild_frac = 0.0;
+  o->use_graphs = 1;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -596,6 +659,9 @@ const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "nu
 void sl_hjb_destroy(sl_hjb *h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  for (auto &g : h->graph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void *p : h->allocs) cudaFree(p);
   if (h->hS) cudaFreeHost(h->hS);
   if (h->h_maxd) cudaFreeHost(h->h_maxd);
@@ -738,6 +804,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
     cb.win = (2 * cb.R + 1) * (2 * cb.R + 1);
     cb.cap = cb.m * cb.m;
     AL(cb.cls, size_t(cb.m) * cb.m);
+    AL(cb.d_nexpl, 1);
     AL(cb.erow, size_t(cb.cap));
     if (p64) AL(cb.ewin64, size_t(cb.win) * cb.cap);
     else AL(cb.ewin32, size_t(cb.win) * cb.cap);

@@ -1,4 +1,5 @@
 // sl_coarse.cu - Galerkin coarse levels A_l = R A_{l-1} P (Section 3.3) on the device.
+#include <algorithm>
 #include <cmath>
 
 #include "sl_launch.h"
@@ -158,64 +159,64 @@ __global__ void __launch_bounds__(256) k_coarse_class_op(CoarseLev<T> L, T omega
   else y[j] = x[j] + omega * (b[j] - acc) / d;
 }
 
+// Explicit rows: grid-stride over the slots, whose number is read from device memory so that
+// the launch configuration does not depend on the current hierarchy (CUDA-graph friendly).
 template <typename T, int OP>
-__global__ void __launch_bounds__(256) k_coarse_expl_op(CoarseLev<T> L, int nexpl, T omega,
-                                                        const T *__restrict__ x, const T *__restrict__ b,
-                                                        T *__restrict__ y) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= nexpl) return;
-  const int j = L.erow[slot];
-  const int I1 = j % L.n, I2 = j / L.n;
+__global__ void __launch_bounds__(256) k_coarse_expl_op(CoarseLev<T> L, const int *__restrict__ nexpl_dev,
+                                                        T omega, const T *__restrict__ x,
+                                                        const T *__restrict__ b, T *__restrict__ y) {
+  const int nexpl = *nexpl_dev;
   const int R = L.R, Wd = 2 * R + 1;
-  const T d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
-  if (OP == OP_JACOBI0) {
-    y[j] = omega * b[j] / d;
-    return;
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < nexpl; slot += gridDim.x * blockDim.x) {
+    const int j = L.erow[slot];
+    const int I1 = j % L.n, I2 = j / L.n;
+    const T d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
+    if (OP == OP_JACOBI0) {
+      y[j] = omega * b[j] / d;
+      continue;
+    }
+    const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
+    const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
+    T acc = T(0);
+    for (int dy = ylo; dy <= yhi; ++dy) {
+      const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
+      const T *xrow = x + j + dy * L.n;
+      for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[size_t(dx) * L.cap], __ldg(xrow + dx), acc);
+    }
+    if (OP == OP_APPLY) y[j] = acc;
+    else if (OP == OP_RESID) y[j] = b[j] - acc;
+    else y[j] = x[j] + omega * (b[j] - acc) / d;
   }
-  const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
-  const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
-  T acc = T(0);
-  for (int dy = ylo; dy <= yhi; ++dy) {
-    const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
-    const T *xrow = x + j + dy * L.n;
-    for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[size_t(dx) * L.cap], __ldg(xrow + dx), acc);
-  }
-  if (OP == OP_APPLY) y[j] = acc;
-  else if (OP == OP_RESID) y[j] = b[j] - acc;
-  else y[j] = x[j] + omega * (b[j] - acc) / d;
 }
 
 template <typename T>
-void launch_coarse_op(int op, const CoarseLev<T> &L, int nexpl, T omega, const T *x, const T *b,
-                      T *y, cudaStream_t s) {
+void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T omega, const T *x,
+                      const T *b, T *y, cudaStream_t s) {
   dim3 blk(32, 8), grd((L.m + 31) / 32, (L.m + 7) / 8);
-  const int eg = (nexpl + 255) / 256;
+  const int eg = std::max(1, std::min(kRedBlocks, (L.cap + 255) / 256));
+  note_launch(2);
   switch (op) {
     case OP_APPLY:
-      note_launch();
       k_coarse_class_op<T, OP_APPLY><<<grd, blk, 0, s>>>(L, omega, x, b, y);
-      if (eg) { note_launch(); k_coarse_expl_op<T, OP_APPLY><<<eg, 256, 0, s>>>(L, nexpl, omega, x, b, y); }
+      k_coarse_expl_op<T, OP_APPLY><<<eg, 256, 0, s>>>(L, nexpl_dev, omega, x, b, y);
       break;
     case OP_RESID:
-      note_launch();
       k_coarse_class_op<T, OP_RESID><<<grd, blk, 0, s>>>(L, omega, x, b, y);
-      if (eg) { note_launch(); k_coarse_expl_op<T, OP_RESID><<<eg, 256, 0, s>>>(L, nexpl, omega, x, b, y); }
+      k_coarse_expl_op<T, OP_RESID><<<eg, 256, 0, s>>>(L, nexpl_dev, omega, x, b, y);
       break;
     case OP_JACOBI:
-      note_launch();
       k_coarse_class_op<T, OP_JACOBI><<<grd, blk, 0, s>>>(L, omega, x, b, y);
-      if (eg) { note_launch(); k_coarse_expl_op<T, OP_JACOBI><<<eg, 256, 0, s>>>(L, nexpl, omega, x, b, y); }
+      k_coarse_expl_op<T, OP_JACOBI><<<eg, 256, 0, s>>>(L, nexpl_dev, omega, x, b, y);
       break;
     default:
-      note_launch();
       k_coarse_class_op<T, OP_JACOBI0><<<grd, blk, 0, s>>>(L, omega, x, b, y);
-      if (eg) { note_launch(); k_coarse_expl_op<T, OP_JACOBI0><<<eg, 256, 0, s>>>(L, nexpl, omega, x, b, y); }
+      k_coarse_expl_op<T, OP_JACOBI0><<<eg, 256, 0, s>>>(L, nexpl_dev, omega, x, b, y);
       break;
   }
 }
-template void launch_coarse_op<double>(int, const CoarseLev<double> &, int, double, const double *,
-                                       const double *, double *, cudaStream_t);
-template void launch_coarse_op<float>(int, const CoarseLev<float> &, int, float, const float *,
+template void launch_coarse_op<double>(int, const CoarseLev<double> &, const int *, double,
+                                       const double *, const double *, double *, cudaStream_t);
+template void launch_coarse_op<float>(int, const CoarseLev<float> &, const int *, float, const float *,
                                       const float *, float *, cudaStream_t);
 
 // ----------------------------------------------------------------------------- coarsest level

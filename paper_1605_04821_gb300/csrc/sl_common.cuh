@@ -128,6 +128,7 @@ struct BicgScalars {
   double tolrel2;              // tol^2 (set by the host before the run)
   double tol2;                 // (tol ||b||)^2
   double rmax, bmax;           // ||r||_inf, ||b||_inf (true-residual checks)
+  int first;                   // 1 until the first search direction has been formed
   int breakdown;               // 1: rho or (r^, v) or (t, t) vanished
   int nonfinite;               // 1: a NaN / Inf was seen
 };

@@ -159,7 +159,11 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
     const double E0 = SCREEN ? 1.001 * u * ((6.0 + 2.0 * tab.tmax) * a.Wmax_class[q2 * tab.Q + q1] * double(D)
                                              + (nf + 3.0) * Fabs + 3.0 * a.cmax * fabs(Xj))
                              : 0.0;
-    // pass 1
+    // pass 1.  The candidate window is 2 (2 E0 + 4 u |v|) + 2 tie_rel max(1, |v|): twice what
+    // two bounded values can differ by, so it stays rigorous when the comparison itself is
+    // evaluated in the screening precision (its rounding is below the slack).
+    const TS c1 = SCREEN ? TS(8.0 * u + 2.0 * a.tie_rel) : TS(2.0 * a.tie_rel * (1.0 + 1e-9));
+    const TS M0 = SCREEN ? TS(4.0 * E0 * 1.0001 + 2.0 * a.tie_rel) : TS(0);
     TS vmin = TS(INFINITY);
     unsigned long long cand = 0ull;
     int ncand = 0;
@@ -171,19 +175,19 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
       if (SCREEN) {
         float f = 0.f;
         for (int mm = 0; mm < nf && mm < 4; ++mm) f = fmaf(__ldg(a.phi32 + k * nf + mm), Fv32[mm], f);
-        fk = f + tab.c32[k] * float(Xj);
+        fk = fmaf(tab.c32[k], float(Xj), f);
       } else {
         double f = 0.0;
         for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
-        fk = f + tab.c64[k] * Xj;
+        fk = fma(tab.c64[k], Xj, f);
       }
       v = v + fk;
       if (!(v == v)) continue;  // NaN never enters the candidate list
-      const double av = fabs(double(v < vmin ? v : vmin));
-      const double margin = SCREEN ? 2.0 * (2.0 * E0 + 4.0 * u * (av + 1e-30)) + 2.0 * a.tie_rel * fmax(1.0, av)
-                                   : 2.0 * a.tie_rel * fmax(1.0, av) * (1.0 + 1e-9);
+      const TS av = v < vmin ? (v < TS(0) ? -v : v) : (vmin < TS(0) ? -vmin : vmin);
+      const TS av1 = av > TS(1) ? av : TS(1);
+      const TS margin = SCREEN ? M0 + c1 * av1 : c1 * av1;
       if (v < vmin) {
-        if (double(v) < double(vmin) - margin) {
+        if (v < vmin - margin) {
           cand = (unsigned long long)k;
           ncand = 1;
           overflow = false;
@@ -192,7 +196,7 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
           else overflow = true;
         }
         vmin = v;
-      } else if (double(v) <= double(vmin) + margin) {
+      } else if (v <= vmin + margin) {
         if (ncand < kMaxCand) cand |= (unsigned long long)k << (8 * ncand++);
         else overflow = true;
       }
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
         const int e = (k * tab.Q + q2) * tab.Q + q1;
         double f = 0.0;
         for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
-        const double v = eval_global64(tab, e, a.X, j) + (f + tab.c64[k] * Xj);
+        const double v = eval_global64(tab, e, a.X, j) + fma(tab.c64[k], Xj, f);
         vm = fmin(vm, v);
       }
       const double thr = vm + a.tie_rel * fmax(1.0, fabs(vm));
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
         const int e = (k * tab.Q + q2) * tab.Q + q1;
         double f = 0.0;
         for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
-        const double v = eval_global64(tab, e, a.X, j) + (f + tab.c64[k] * Xj);
+        const double v = eval_global64(tab, e, a.X, j) + fma(tab.c64[k], Xj, f);
         if (v <= thr) best = k;
       }
     }

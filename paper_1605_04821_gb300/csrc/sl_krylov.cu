@@ -23,11 +23,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block sum of NF values; returns the sums in thread 0.
+// Block sum of NF values in a fixed order; returns the sums in thread 0.
 template <int NF>
 __device__ __forceinline__ void block_sum(double (&v)[NF]) {
   __shared__ double sh[NF][kVecThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();  // sh may still be read by thread 0 from a previous call
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     v[f] = warp_sum(v[f]);
@@ -55,9 +56,11 @@ __device__ void apply_post(int post, const double *tot, BicgScalars *S) {
       S->omega = 1.0;
       S->breakdown = 0;
       S->nonfinite = 0;
+      S->first = 1;
       bad = !isfinite(tot[0]) || !isfinite(tot[1]);
       break;
     case POST_ALPHA:
+      S->first = 0;
       S->rv = tot[0];
       bad = !isfinite(tot[0]);
       if (tot[0] == 0.0 || fabs(S->rho) < 1e-300) {
@@ -99,6 +102,9 @@ __device__ void apply_post(int post, const double *tot, BicgScalars *S) {
   if (bad) S->nonfinite = 1;
 }
 
+// Each block writes its partial sums; the last block to arrive adds all partials with all of
+// its threads (thread t takes blocks t, t + 256, ... in order, then a fixed-order tree), so
+// the totals do not depend on which block finishes last.
 template <int NF>
 __device__ void finish(double (&v)[NF], int post, BicgScalars *S, double *partials,
                        unsigned *counter) {
@@ -112,14 +118,16 @@ __device__ void finish(double (&v)[NF], int post, BicgScalars *S, double *partia
     last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double tot[NF];
+  if (!last) return;
+  __threadfence();
+  double tot[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) tot[f] = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b)
+  for (int f = 0; f < NF; ++f) tot[f] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
 #pragma unroll
-      for (int f = 0; f < NF; ++f) tot[f] += ((volatile double *)partials)[b * NF + f];
+    for (int f = 0; f < NF; ++f) tot[f] += ((volatile double *)partials)[b * NF + f];
+  block_sum<NF>(tot);
+  if (threadIdx.x == 0) {
     apply_post(post, tot, S);
     *counter = 0u;
   }
@@ -149,11 +157,13 @@ void launch_dot2(const T *a, const T *b, const T *c, const T *d, size_t N, int p
   k_dot2<T><<<kRedBlocks, kVecThreads, 0, s>>>(a, b, c, d, N, post, S, partials, counter);
 }
 
-// p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega); first iteration p = r.
+// p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega); first iteration p = r
+// (the device flag S->first, so that one captured iteration serves every iteration).
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_bicg_p(T *__restrict__ p, const T *__restrict__ r,
-                                                        const T *__restrict__ v, size_t N, int first,
+                                                        const T *__restrict__ v, size_t N, int first_host,
                                                         const BicgScalars *S) {
+  const int first = first_host || S->first;
   const double beta_d = first ? 0.0 : (S->rho / S->rho_old) * (S->alpha / S->omega);
   const T beta = T(beta_d), om = T(S->omega);
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
@@ -293,13 +303,22 @@ __global__ void __launch_bounds__(kVecThreads) k_norms(const double *__restrict_
     last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double T2 = 0.0, M = 0.0;
-    for (unsigned b2 = 0; b2 < gridDim.x; ++b2) {
-      T2 += ((volatile double *)partials)[2 * b2];
-      M = fmax(M, ((volatile double *)partials)[2 * b2 + 1]);
-    }
+  if (!last) return;
+  __threadfence();
+  double T2 = 0.0, M = 0.0;
+  for (unsigned b2 = threadIdx.x; b2 < gridDim.x; b2 += blockDim.x) {
+    T2 += ((volatile double *)partials)[2 * b2];
+    M = fmax(M, ((volatile double *)partials)[2 * b2 + 1]);
+  }
+  __syncthreads();
+  T2 = warp_sum(T2);
+  for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xffffffffu, M, o));
+  if ((threadIdx.x & 31) == 0) { ss[threadIdx.x >> 5] = T2; sm[threadIdx.x >> 5] = M; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T2 = 0.0;
+    M = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) { T2 += ss[w]; M = fmax(M, sm[w]); }
     if (which == 0) {
       S->bnorm2 = T2;
       S->bmax = M;
@@ -348,13 +367,24 @@ __global__ void __launch_bounds__(kVecThreads) k_maxabs_diff(const double *__res
     last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double D = 0.0, Xm = 0.0;
-    for (unsigned b2 = 0; b2 < gridDim.x; ++b2) {
-      D = fmax(D, ((volatile double *)partials)[2 * b2]);
-      Xm = fmax(Xm, ((volatile double *)partials)[2 * b2 + 1]);
-    }
+  if (!last) return;
+  __threadfence();
+  double D = 0.0, Xm = 0.0;
+  for (unsigned b2 = threadIdx.x; b2 < gridDim.x; b2 += blockDim.x) {
+    D = fmax(D, ((volatile double *)partials)[2 * b2]);
+    Xm = fmax(Xm, ((volatile double *)partials)[2 * b2 + 1]);
+  }
+  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    D = fmax(D, __shfl_xor_sync(0xffffffffu, D, o));
+    Xm = fmax(Xm, __shfl_xor_sync(0xffffffffu, Xm, o));
+  }
+  if ((threadIdx.x & 31) == 0) { sd[threadIdx.x >> 5] = D; sx[threadIdx.x >> 5] = Xm; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    D = 0.0;
+    Xm = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) { D = fmax(D, sd[w]); Xm = fmax(Xm, sx[w]); }
     out[0] = D;
     out[1] = Xm;
     *counter = 0u;

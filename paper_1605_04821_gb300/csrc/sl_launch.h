@@ -63,8 +63,8 @@ cudaError_t launch_rap_explicit(int level, const FineTab &tab, const int32_t *fi
                                 const int32_t *prev_coff, const CoarseLev<T> &cur, int count,
                                 T *ewin_out, cudaStream_t s);
 template <typename T>
-void launch_coarse_op(int op, const CoarseLev<T> &L, int nexpl, T omega, const T *x, const T *b,
-                      T *y, cudaStream_t s);
+void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T omega, const T *x,
+                      const T *b, T *y, cudaStream_t s);
 template <typename T>
 void launch_coarsest_setup(int level, const FineTab &tab, const uint8_t *policy, T dt,
                            const CoarseLev<T> &L, const int32_t *coff, double *work, T *Ainv,
