@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--opt", action="append", default=[],
+                   help="solver option override key=value (sl_opts field), repeatable")
     return p.parse_args()
 
 
@@ -217,8 +219,15 @@ def run_ours(args):
     dt = 1.0 / 128
     stream = torch.cuda.current_stream()
 
+    extra = {}
+    for kv in args.opt:
+        k, v = kv.split("=", 1)
+        extra[k] = float(v) if "." in v or "e" in v else int(v)
+
     def make(precision):
-        return slp.solver_from_problem(prob, device=dev, precision=precision, argmin_screen=precision)
+        kw = dict(precision=precision, argmin_screen=precision)
+        kw.update(extra)
+        return slp.solver_from_problem(prob, device=dev, **kw)
 
     # ---- mixed path (the metric)
     s = make(1)
@@ -255,6 +264,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * n * n * args.steps / (ms / 1e3)
+    explicit_rows = [s.level_info(l)[1] for l in range(s.num_levels())]
 
     # ---- roofline: the fine-level FP32 operator (matrix-free SpMV), timed alone with events
     m = n - 2
@@ -362,7 +372,8 @@ def run_ours(args):
                        "l2": "working set > L2 (no flush needed)",
                        "levels": int(make_levels(n)), "pi_iters": stats["pi_iters"],
                        "krylov_iters": stats["krylov_iters"], "ir_iters": stats["ir_iters"],
-                       "rebuilds": stats["rebuilds"]},
+                       "rebuilds": stats["rebuilds"], "opts": extra,
+                       "explicit_rows_per_level": explicit_rows},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

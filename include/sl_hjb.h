@@ -113,6 +113,9 @@ typedef struct {
                            rows changed control since the last build (0: on any change) */
   int use_graphs;       /* 1: each BiCGSTAB iteration is one CUDA-graph launch (captured once
                            per precision and step size); 0: plain stream launches */
+  int coarse_tail_rows; /* levels with at most this many rows run, from the first such level
+                           down, in one thread block per V-cycle; 0: never; -1: default
+                           (1024 rows in mixed precision, 0 in FP64, whose per-SM rate is low) */
 } sl_opts;
 
 typedef struct {
@@ -129,7 +132,7 @@ typedef struct {
 
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 1e-5, ir_max 30, pi_tol 1e-10, pi_max 100,
- * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0, use_graphs 1. */
+ * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0, use_graphs 1, coarse_tail_rows -1. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every
@@ -184,7 +187,9 @@ sl_status sl_hjb_apply(sl_hjb *h, int level, int precision, const void *x_dev, v
                        void *stream);
 
 /* One V(nu1, nu2) cycle from x = 0 for A_0 x = b (the preconditioner application).
- * b_dev, x_dev: n*n full-grid vectors, FP64 (precision 0) or FP32 (precision 1). */
+ * b_dev, x_dev: n*n full-grid vectors, FP64 (precision 0) or FP32 (precision 1).  The
+ * boundary entries of x_dev must be zero on entry (they are read as the Dirichlet zero of
+ * the correction) and are left unchanged; every interior entry is written. */
 sl_status sl_hjb_vcycle(sl_hjb *h, int precision, const void *b_dev, void *x_dev, void *stream);
 
 /* Solves A^alpha X = F^alpha of the step at time t with step dt for the current policy,

@@ -92,6 +92,8 @@ struct sl_hjb {
   unsigned long long *d_changes = nullptr, *h_changes = nullptr;
   int *d_flags = nullptr, *h_flags = nullptr, *d_count = nullptr, *h_count = nullptr;
   IterGraph graph[2];           // [precision]
+  int *chunk_scratch = nullptr; // classification counts / offsets
+  int tail_l0 = 0;              // first level run by the single-block V-cycle tail (0: none)
   cudaStream_t cap_stream = nullptr;
   std::vector<void *> allocs;
   std::string err;
@@ -305,8 +307,7 @@ sl_status build_hierarchy_T(sl_hjb *h, double dt, cudaStream_t s) {
   for (int l = 1; l < h->L; ++l) {
     CoarseBuf &c = h->cl[l];
     CoarseBuf &p = h->cl[l - 1];
-    CK(cudaMemsetAsync(c.d_nexpl, 0, sizeof(int), s));
-    launch_classify(l, h->tab, h->policy, p.cls, p.n, c.cls, c.n, c.erow, c.d_nexpl, s);
+    launch_classify(l, h->tab, h->policy, p.cls, p.n, c.cls, c.n, c.erow, c.d_nexpl, h->chunk_scratch, s);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_count, c.d_nexpl, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -361,6 +362,24 @@ void vbufs<float>(VBuf &v, float **x, float **t, float **r, float **b) {
 template <typename T>
 sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) {
   const size_t N = NN(h, l);
+  if (l > 0 && l == h->tail_l0 && l < h->L - 1) {
+    // coarse end of the cycle in one thread block; b and x are this level's own buffers
+    TailArgs<T> a{};
+    a.l0 = l;
+    a.L = h->L;
+    a.nu1 = h->o.nu1;
+    a.nu2 = h->o.nu2;
+    a.omega = T(h->o.omega);
+    for (int q = l; q < h->L; ++q) {
+      a.lev[q] = lev_view<T>(h, q);
+      vbufs<T>(h->vb[q], &a.x[q], &a.t[q], &a.r[q], &a.b[q]);
+    }
+    a.Ainv = pick<T>(h->Ainv64, h->Ainv32);
+    if (b != a.b[l] || x != a.x[l]) return fail(h, SL_EINVAL, "V-cycle tail called on foreign buffers");
+    launch_vcycle_tail<T>(a, s);
+    CK(cudaGetLastError());
+    return SL_OK;
+  }
   if (l == h->L - 1) {
     launch_coarsest_apply<T>(pick<T>(h->Ainv64, h->Ainv32), h->cl[l].n, b, x, s);
     return SL_OK;
@@ -652,6 +671,7 @@ void sl_opts_default(sl_opts *o) {
   o->argmin_screen = 0;
   o->rebuild_frac = 0.0;
   o->use_graphs = 1;
+  o->coarse_tail_rows = -1;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -809,6 +829,14 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
     if (p64) AL(cb.ewin64, size_t(cb.win) * cb.cap);
     else AL(cb.ewin32, size_t(cb.win) * cb.cap);
   }
+  if (h->L > 1) {
+    const size_t m1 = size_t(h->cl[1].m);
+    AL(h->chunk_scratch, 2 * ((m1 * m1 + 255) / 256) + 2);
+  }
+  h->tail_l0 = 0;
+  const int tail_rows = h->o.coarse_tail_rows >= 0 ? h->o.coarse_tail_rows : (p64 ? 0 : 1024);
+  for (int l = 1; l < h->L - 1 && tail_rows > 0; ++l)
+    if (h->cl[l].m * h->cl[l].m <= tail_rows) { h->tail_l0 = l; break; }
   const int mc = h->cl[h->L - 1].m;
   AL(h->cwork, size_t(2) * mc * mc * mc * mc);
   if (p64) AL(h->Ainv64, size_t(mc) * mc * mc * mc);

@@ -1,5 +1,6 @@
 // sl_coarse.cu - Galerkin coarse levels A_l = R A_{l-1} P (Section 3.3) on the device.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "sl_launch.h"
@@ -8,19 +9,17 @@ namespace sl {
 
 // ----------------------------------------------------------------------------- classification
 // Coarse row I is class k when all nine rows 2I + a of the previous level are class-k interior
-// rows (level 0: untruncated band-free rows with control k); otherwise it gets an explicit slot.
-__global__ void k_classify(int level, FineTab tab, const uint8_t *__restrict__ policy,
-                           const int32_t *__restrict__ cls_prev, int n_prev,
-                           int32_t *__restrict__ cls, int n, int32_t *__restrict__ erow,
-                           int *__restrict__ count) {
-  const int I1 = 1 + blockIdx.x * 32 + threadIdx.x;
-  const int I2 = 1 + blockIdx.y * 8 + threadIdx.y;
-  const int m = n - 2;
-  if (I1 > m || I2 > m) return;
+// rows (level 0: untruncated band-free rows with control k); otherwise it is stored explicitly.
+// Explicit rows get their slots in row-major order (count per 256-row chunk, scan, assign), so
+// the slot order is deterministic and neighbouring slots are neighbouring rows.
+constexpr int kChunk = 256;
+constexpr int kPending = INT32_MIN;
+
+__device__ __forceinline__ int coarse_class_of(int level, const FineTab &tab, const uint8_t *policy,
+                                               const int32_t *cls_prev, int n_prev, int I1, int I2) {
   int k0 = -1;
-  bool uniform = true;
-  for (int a2 = -1; a2 <= 1 && uniform; ++a2)
-    for (int a1 = -1; a1 <= 1 && uniform; ++a1) {
+  for (int a2 = -1; a2 <= 1; ++a2)
+    for (int a1 = -1; a1 <= 1; ++a1) {
       const int i1 = 2 * I1 + a1, i2 = 2 * I2 + a2;
       int k;
       if (level == 1) {
@@ -29,27 +28,90 @@ __global__ void k_classify(int level, FineTab tab, const uint8_t *__restrict__ p
         k = interior ? int(policy[(i2 - 1) * tab.m + (i1 - 1)]) : -1;
       } else {
         k = cls_prev[(i2 - 1) * (n_prev - 2) + (i1 - 1)];
-        if (k < 0) k = -1;
       }
-      if (k < 0) uniform = false;
-      else if (k0 < 0) k0 = k;
-      else if (k != k0) uniform = false;
+      if (k < 0) return -1;
+      if (k0 < 0) k0 = k;
+      else if (k != k0) return -1;
     }
-  const int I = (I2 - 1) * m + (I1 - 1);
-  if (uniform) {
-    cls[I] = k0;
-  } else {
-    const int slot = atomicAdd(count, 1);
+  return k0;
+}
+
+__global__ void __launch_bounds__(kChunk) k_classify_count(int level, FineTab tab, const uint8_t *__restrict__ policy,
+                                                           const int32_t *__restrict__ cls_prev, int n_prev,
+                                                           int32_t *__restrict__ cls, int n,
+                                                           int *__restrict__ chunk_count) {
+  const int m = n - 2;
+  const int I = blockIdx.x * kChunk + threadIdx.x;
+  int flag = 0;
+  if (I < m * m) {
+    const int k = coarse_class_of(level, tab, policy, cls_prev, n_prev, 1 + I % m, 1 + I / m);
+    cls[I] = k >= 0 ? k : kPending;
+    flag = k < 0;
+  }
+  const int c = __syncthreads_count(flag);
+  if (threadIdx.x == 0) chunk_count[blockIdx.x] = c;
+}
+
+// Exclusive scan of the chunk counts in one block; the total goes to *total.
+__global__ void __launch_bounds__(1024) k_scan_counts(const int *__restrict__ count, int nchunks,
+                                                      int *__restrict__ offset, int *__restrict__ total) {
+  __shared__ int part[1024];
+  const int per = (nchunks + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(nchunks, lo + per);
+  int sum = 0;
+  for (int c = lo; c < hi; ++c) sum += count[c];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan of the segment sums
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - sum;
+  for (int c = lo; c < hi; ++c) {
+    offset[c] = run;
+    run += count[c];
+  }
+  if (threadIdx.x == 1023) *total = part[1023];
+}
+
+__global__ void __launch_bounds__(kChunk) k_classify_assign(int32_t *__restrict__ cls, int n,
+                                                            int32_t *__restrict__ erow,
+                                                            const int *__restrict__ offset) {
+  __shared__ int warp_base[kChunk / 32];
+  const int m = n - 2;
+  const int I = blockIdx.x * kChunk + threadIdx.x;
+  const bool pend = I < m * m && cls[I] == kPending;
+  const unsigned mask = __ballot_sync(0xffffffffu, pend);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_base[wid] = __popc(mask);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int w = 0; w < kChunk / 32; ++w) {
+      const int c = warp_base[w];
+      warp_base[w] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (pend) {
+    const int slot = offset[blockIdx.x] + warp_base[wid] + __popc(mask & ((1u << lane) - 1u));
     cls[I] = -slot - 1;
-    erow[slot] = I2 * n + I1;
+    erow[slot] = (1 + I / m) * n + 1 + I % m;
   }
 }
 
 void launch_classify(int level, const FineTab &tab, const uint8_t *policy, const int32_t *cls_prev,
-                     int n_prev, int32_t *cls, int n, int32_t *erow, int *count, cudaStream_t s) {
-  dim3 blk(32, 8), grd((n - 2 + 31) / 32, (n - 2 + 7) / 8);
-  note_launch();
-  k_classify<<<grd, blk, 0, s>>>(level, tab, policy, cls_prev, n_prev, cls, n, erow, count);
+                     int n_prev, int32_t *cls, int n, int32_t *erow, int *count, int *chunk_scratch,
+                     cudaStream_t s) {
+  const int m = n - 2;
+  const int nchunks = (m * m + kChunk - 1) / kChunk;
+  note_launch(3);
+  k_classify_count<<<nchunks, kChunk, 0, s>>>(level, tab, policy, cls_prev, n_prev, cls, n, chunk_scratch);
+  k_scan_counts<<<1, 1024, 0, s>>>(chunk_scratch, nchunks, chunk_scratch + nchunks, count);
+  k_classify_assign<<<nchunks, kChunk, 0, s>>>(cls, n, erow, chunk_scratch + nchunks);
 }
 
 // ----------------------------------------------------------------------------- explicit RAP
@@ -134,15 +196,21 @@ template cudaError_t launch_rap_explicit<float>(int, const FineTab &, const int3
                                                 const CoarseLev<float> &, int, float *, cudaStream_t);
 
 // ----------------------------------------------------------------------------- coarse operator
+// One launch per operator application: the first blocks take the class rows in 32 x 8 tiles
+// (stencil S_k from the per-control table), the remaining blocks stride over the explicit
+// rows (dense window), whose number is read from device memory so that the launch shape does
+// not depend on the current hierarchy.
 template <typename T, int OP>
-__global__ void __launch_bounds__(256) k_coarse_class_op(CoarseLev<T> L, T omega, const T *__restrict__ x,
-                                                         const T *__restrict__ b, T *__restrict__ y) {
-  const int I1 = 1 + blockIdx.x * 32 + threadIdx.x;
-  const int I2 = 1 + blockIdx.y * 8 + threadIdx.y;
-  if (I1 > L.m || I2 > L.m) return;
-  const int k = L.cls[(I2 - 1) * L.m + (I1 - 1)];
-  if (k < 0) return;
-  const int j = I2 * L.n + I1;
+__device__ __forceinline__ void coarse_finish(T *y, const T *x, const T *b, int j, T acc, T d, T omega) {
+  if (OP == OP_APPLY) y[j] = acc;
+  else if (OP == OP_RESID) y[j] = b[j] - acc;
+  else y[j] = x[j] + omega * (b[j] - acc) / d;
+}
+
+template <typename T, int OP>
+__device__ __forceinline__ void coarse_class_row(const CoarseLev<T> &L, int k, int j, T omega,
+                                                 const T *__restrict__ x, const T *__restrict__ b,
+                                                 T *__restrict__ y) {
   const T d = L.cdiag[k];
   if (OP == OP_JACOBI0) {
     y[j] = omega * b[j] / d;
@@ -154,70 +222,164 @@ __global__ void __launch_bounds__(256) k_coarse_class_op(CoarseLev<T> L, T omega
     const int ix = k * L.ctmax + t;
     acc = fma(__ldg(L.cw + ix), __ldg(x + j + __ldg(L.clin + ix)), acc);
   }
-  if (OP == OP_APPLY) y[j] = acc;
-  else if (OP == OP_RESID) y[j] = b[j] - acc;
-  else y[j] = x[j] + omega * (b[j] - acc) / d;
+  coarse_finish<T, OP>(y, x, b, j, acc, d, omega);
 }
 
-// Explicit rows: grid-stride over the slots, whose number is read from device memory so that
-// the launch configuration does not depend on the current hierarchy (CUDA-graph friendly).
 template <typename T, int OP>
-__global__ void __launch_bounds__(256) k_coarse_expl_op(CoarseLev<T> L, const int *__restrict__ nexpl_dev,
-                                                        T omega, const T *__restrict__ x,
-                                                        const T *__restrict__ b, T *__restrict__ y) {
-  const int nexpl = *nexpl_dev;
+__device__ __forceinline__ void coarse_expl_row(const CoarseLev<T> &L, int slot, T omega,
+                                                const T *__restrict__ x, const T *__restrict__ b,
+                                                T *__restrict__ y) {
+  const int j = L.erow[slot];
+  const int I1 = j % L.n, I2 = j / L.n;
   const int R = L.R, Wd = 2 * R + 1;
-  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < nexpl; slot += gridDim.x * blockDim.x) {
-    const int j = L.erow[slot];
-    const int I1 = j % L.n, I2 = j / L.n;
-    const T d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
-    if (OP == OP_JACOBI0) {
-      y[j] = omega * b[j] / d;
-      continue;
-    }
-    const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
-    const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
-    T acc = T(0);
-    for (int dy = ylo; dy <= yhi; ++dy) {
-      const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
-      const T *xrow = x + j + dy * L.n;
-      for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[size_t(dx) * L.cap], __ldg(xrow + dx), acc);
-    }
-    if (OP == OP_APPLY) y[j] = acc;
-    else if (OP == OP_RESID) y[j] = b[j] - acc;
-    else y[j] = x[j] + omega * (b[j] - acc) / d;
+  const T d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
+  if (OP == OP_JACOBI0) {
+    y[j] = omega * b[j] / d;
+    return;
   }
+  const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
+  const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
+  T acc = T(0);
+  for (int dy = ylo; dy <= yhi; ++dy) {
+    const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
+    const T *xrow = x + j + dy * L.n;
+    for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[size_t(dx) * L.cap], __ldg(xrow + dx), acc);
+  }
+  coarse_finish<T, OP>(y, x, b, j, acc, d, omega);
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) k_coarse_op(CoarseLev<T> L, const int *__restrict__ nexpl_dev,
+                                                   int tiles_x, int tiles, T omega, const T *__restrict__ x,
+                                                   const T *__restrict__ b, T *__restrict__ y) {
+  if (int(blockIdx.x) < tiles) {
+    const int I1 = 1 + (blockIdx.x % tiles_x) * 32 + (threadIdx.x & 31);
+    const int I2 = 1 + (blockIdx.x / tiles_x) * 8 + (threadIdx.x >> 5);
+    if (I1 > L.m || I2 > L.m) return;
+    const int k = L.cls[(I2 - 1) * L.m + (I1 - 1)];
+    if (k >= 0) coarse_class_row<T, OP>(L, k, I2 * L.n + I1, omega, x, b, y);
+    return;
+  }
+  const int nexpl = *nexpl_dev;
+  const int nb = gridDim.x - tiles;
+  for (int slot = (blockIdx.x - tiles) * blockDim.x + threadIdx.x; slot < nexpl; slot += nb * blockDim.x)
+    coarse_expl_row<T, OP>(L, slot, omega, x, b, y);
 }
 
 template <typename T>
 void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T omega, const T *x,
                       const T *b, T *y, cudaStream_t s) {
-  dim3 blk(32, 8), grd((L.m + 31) / 32, (L.m + 7) / 8);
+  const int tx = (L.m + 31) / 32, tiles = tx * ((L.m + 7) / 8);
   const int eg = std::max(1, std::min(kRedBlocks, (L.cap + 255) / 256));
-  note_launch(2);
+  const int grid = tiles + eg;
+  note_launch();
   switch (op) {
-    case OP_APPLY:
-      k_coarse_class_op<T, OP_APPLY><<<grd, blk, 0, s>>>(L, omega, x, b, y);
-      k_coarse_expl_op<T, OP_APPLY><<<eg, 256, 0, s>>>(L, nexpl_dev, omega, x, b, y);
-      break;
-    case OP_RESID:
-      k_coarse_class_op<T, OP_RESID><<<grd, blk, 0, s>>>(L, omega, x, b, y);
-      k_coarse_expl_op<T, OP_RESID><<<eg, 256, 0, s>>>(L, nexpl_dev, omega, x, b, y);
-      break;
-    case OP_JACOBI:
-      k_coarse_class_op<T, OP_JACOBI><<<grd, blk, 0, s>>>(L, omega, x, b, y);
-      k_coarse_expl_op<T, OP_JACOBI><<<eg, 256, 0, s>>>(L, nexpl_dev, omega, x, b, y);
-      break;
-    default:
-      k_coarse_class_op<T, OP_JACOBI0><<<grd, blk, 0, s>>>(L, omega, x, b, y);
-      k_coarse_expl_op<T, OP_JACOBI0><<<eg, 256, 0, s>>>(L, nexpl_dev, omega, x, b, y);
-      break;
+    case OP_APPLY: k_coarse_op<T, OP_APPLY><<<grid, 256, 0, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
+    case OP_RESID: k_coarse_op<T, OP_RESID><<<grid, 256, 0, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
+    case OP_JACOBI: k_coarse_op<T, OP_JACOBI><<<grid, 256, 0, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
+    default: k_coarse_op<T, OP_JACOBI0><<<grid, 256, 0, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
   }
 }
 template void launch_coarse_op<double>(int, const CoarseLev<double> &, const int *, double,
                                        const double *, const double *, double *, cudaStream_t);
 template void launch_coarse_op<float>(int, const CoarseLev<float> &, const int *, float, const float *,
                                       const float *, float *, cudaStream_t);
+
+// ----------------------------------------------------------------------------- V-cycle tail
+// The coarse end of the V-cycle (every level from l0 down, each with at most a few thousand
+// rows) in one thread block: on these levels a grid-wide launch per operation costs more
+// than the work, so one CTA walks the levels with __syncthreads between phases.  Each row
+// uses the same device functions as the grid-wide kernels.
+template <typename T>
+__device__ void tail_op(const CoarseLev<T> &L, int op, T omega, const T *x, const T *b, T *y) {
+  const int rows = L.m * L.m;
+  for (int I = threadIdx.x; I < rows; I += blockDim.x) {
+    const int j = (1 + I / L.m) * L.n + 1 + I % L.m;
+    const int c = L.cls[I];
+    if (c >= 0) {
+      switch (op) {
+        case OP_RESID: coarse_class_row<T, OP_RESID>(L, c, j, omega, x, b, y); break;
+        case OP_JACOBI: coarse_class_row<T, OP_JACOBI>(L, c, j, omega, x, b, y); break;
+        default: coarse_class_row<T, OP_JACOBI0>(L, c, j, omega, x, b, y); break;
+      }
+    } else {
+      switch (op) {
+        case OP_RESID: coarse_expl_row<T, OP_RESID>(L, -c - 1, omega, x, b, y); break;
+        case OP_JACOBI: coarse_expl_row<T, OP_JACOBI>(L, -c - 1, omega, x, b, y); break;
+        default: coarse_expl_row<T, OP_JACOBI0>(L, -c - 1, omega, x, b, y); break;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a) {
+  T *cur[kMaxLevels];
+  for (int l = a.l0; l < a.L - 1; ++l) {
+    const CoarseLev<T> &L = a.lev[l];
+    T *c = a.x[l], *o = a.t[l];
+    if (a.nu1 == 0) {
+      for (int I = threadIdx.x; I < L.m * L.m; I += blockDim.x) c[(1 + I / L.m) * L.n + 1 + I % L.m] = T(0);
+      __syncthreads();
+    } else {
+      tail_op<T>(L, OP_JACOBI0, a.omega, nullptr, a.b[l], c);
+      for (int it = 1; it < a.nu1; ++it) {
+        tail_op<T>(L, OP_JACOBI, a.omega, c, a.b[l], o);
+        T *sw = c; c = o; o = sw;
+      }
+    }
+    tail_op<T>(L, OP_RESID, a.omega, c, a.b[l], a.r[l]);
+    const CoarseLev<T> &C = a.lev[l + 1];
+    for (int I = threadIdx.x; I < C.m * C.m; I += blockDim.x) {
+      const int I1 = 1 + I % C.m, I2 = 1 + I / C.m;
+      a.b[l + 1][I2 * C.n + I1] = restrict_point<T>(a.r[l], L.n, I1, I2);
+    }
+    __syncthreads();
+    cur[l] = c;
+  }
+  {  // coarsest: x = A^{-1} b
+    const CoarseLev<T> &C = a.lev[a.L - 1];
+    const int N = C.m * C.m;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      T acc = T(0);
+      for (int c = 0; c < N; ++c) acc = fma(a.Ainv[size_t(r) * N + c], a.b[a.L - 1][(1 + c / C.m) * C.n + 1 + c % C.m], acc);
+      a.x[a.L - 1][(1 + r / C.m) * C.n + 1 + r % C.m] = acc;
+    }
+    __syncthreads();
+    cur[a.L - 1] = a.x[a.L - 1];
+  }
+  for (int l = a.L - 2; l >= a.l0; --l) {
+    const CoarseLev<T> &L = a.lev[l];
+    const CoarseLev<T> &C = a.lev[l + 1];
+    T *c = cur[l], *o = (c == a.x[l]) ? a.t[l] : a.x[l];
+    for (int I = threadIdx.x; I < L.m * L.m; I += blockDim.x) {
+      const int i1 = 1 + I % L.m, i2 = 1 + I / L.m;
+      c[i2 * L.n + i1] += prolong_point<T>(cur[l + 1], C.n, i1, i2);
+    }
+    __syncthreads();
+    for (int it = 0; it < a.nu2; ++it) {
+      tail_op<T>(L, OP_JACOBI, a.omega, c, a.b[l], o);
+      T *sw = c; c = o; o = sw;
+    }
+    cur[l] = c;
+  }
+  if (cur[a.l0] != a.x[a.l0]) {
+    const CoarseLev<T> &L = a.lev[a.l0];
+    for (int I = threadIdx.x; I < L.m * L.m; I += blockDim.x) {
+      const int j = (1 + I / L.m) * L.n + 1 + I % L.m;
+      a.x[a.l0][j] = cur[a.l0][j];
+    }
+  }
+}
+
+template <typename T>
+void launch_vcycle_tail(const TailArgs<T> &a, cudaStream_t s) {
+  note_launch();
+  k_vcycle_tail<T><<<1, 1024, 0, s>>>(a);
+}
+template void launch_vcycle_tail<double>(const TailArgs<double> &, cudaStream_t);
+template void launch_vcycle_tail<float>(const TailArgs<float> &, cudaStream_t);
 
 // ----------------------------------------------------------------------------- coarsest level
 // Dense matrix of the coarsest level (interior unknowns, row-major) and its inverse by

@@ -120,6 +120,29 @@ SL_HD void rap_scatter(T *win, int R, int I1, int I2, int j1, int j2, T rv) {
   }
 }
 
+// Full weighting at coarse interior node (I1, I2):
+// b_c(I) = sum_{a in {-1,0,1}^2} w_a1 w_a2 r_f(2I + a), w = (1/4, 1/2, 1/4).
+template <typename T>
+SL_HD T restrict_point(const T *rf, int nf, int I1, int I2) {
+  const T *r0 = rf + size_t(2 * I2) * nf + 2 * I1;
+  const T rowm = T(0.25) * r0[-nf - 1] + T(0.5) * r0[-nf] + T(0.25) * r0[-nf + 1];
+  const T row0 = T(0.25) * r0[-1] + T(0.5) * r0[0] + T(0.25) * r0[1];
+  const T rowp = T(0.25) * r0[nf - 1] + T(0.5) * r0[nf] + T(0.25) * r0[nf + 1];
+  return T(0.25) * rowm + T(0.5) * row0 + T(0.25) * rowp;
+}
+
+// Bilinear prolongation at fine interior node (i1, i2): sum_J P_{iJ} x_c(J).
+template <typename T>
+SL_HD T prolong_point(const T *xc, int nc, int i1, int i2) {
+  const int J1 = i1 >> 1, J2 = i2 >> 1;
+  const bool odd1 = i1 & 1, odd2 = i2 & 1;
+  const T *c0 = xc + size_t(J2) * nc + J1;
+  if (!odd1 && !odd2) return c0[0];
+  if (odd1 && !odd2) return T(0.5) * (c0[0] + c0[1]);
+  if (!odd1 && odd2) return T(0.5) * (c0[0] + c0[nc]);
+  return T(0.25) * ((c0[0] + c0[1]) + (c0[nc] + c0[nc + 1]));
+}
+
 // Scalars of one BiCGSTAB run, kept in device memory so that no iteration needs the host.
 struct BicgScalars {
   double rho, rho_old, alpha, omega;

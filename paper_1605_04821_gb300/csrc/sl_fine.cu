@@ -45,37 +45,25 @@ void launch_coef(const double *G, int nf, int nq, const double *tau, const doubl
 //   v_k(j) = sum_t w_t (X_{j+o_t} - X_j) + c_k X_j + sum_m phi_km F_m(j)
 // alpha_j = lowest k with v_k <= v_min + tie_rel max(1, |v_min|), decided in FP64.
 //
-// Pass 1 screens all controls from a shared-memory tile of X (tile 32 x 8 nodes plus a halo
-// of the longest tap).  With screen = 0 it is FP64; with screen = 1 it is FP32 on
-// X - X_ref (X_ref the tile's centre value) and every screened value carries the rigorous
-// rounding bound E described below, so the FP64 minimiser and all its FP64 near-ties lie in
-// the candidate list.  Pass 2 re-evaluates the candidates in FP64 only when more than one
-// survives; with one survivor it is the FP64 answer.
+// Pass 1 screens all controls from a shared-memory tile of X (tile 32 x 8 nodes plus a halo of
+// the longest tap).  With screen = 0 it is FP64.  With screen = 1 it is FP32 on the split
+// X = hi + lo (hi = fp32(X), lo = fp32(X - hi)), and each screened value carries a rigorous
+// bound E_k on its distance from the exact value; pass 2 decides in FP64 among the controls
+// that the bounds cannot exclude, and with a single survivor that survivor is the FP64 answer.
 //
-// Rounding bound of the FP32 screen (unit roundoff u = 2^-24), D = max |X - X_ref| over the
-// staged tile, W = sum_t w_t, n_t taps:
-//   |d_t - (X_nb - X_j)| <= 4 u D for the staged differences,
-//   |sum w32 d - sum w (X_nb - X_j)| <= u D W (6 + 2 n_t)       (FMA chain, weights rounded),
-//   |f32_k - f_k| <= (nf + 3) u sum_m |phi_km| |F_m|,  |c32 x32 - c x| <= 3 u |c| |X_j|,
-//   final additions <= 2 u |v|.
-// Two values that are both within their bounds differ by at most the sum of the bounds; the
-// candidate window uses twice that sum plus the FP64 tie window.
+// Bound of the FP32 screen (unit roundoff u = 2^-24, n_t taps, d_t = X_{j+o_t} - X_j):
+//   X = hi + lo + eta, |eta| <= u^2 |X|;  the staged difference dd_t = (hi_nb - hi_j) + (lo_nb - lo_j)
+//   satisfies |dd_t - d_t| <= 2 u |d_t| + 6 u^2 |X|max;
+//   |sum_t w32_t dd_t - sum_t w_t d_t| <= (n_t + 4) u S + 6 u^2 W |X|max,  S = sum_t w_t |d_t|;
+//   |f32_k - f_k| <= (nf + 3) u sum_m |phi_km| |F_m|;  |c32 x32 - c x| <= 3 u |c| |X_j|;
+//   the two final additions <= 2 u |v~_k|.
+// E_k doubles the sum of these terms (S taken from its FP32 evaluation), which also absorbs
+// the rounding of the FP32 comparisons below.  With lb_k = v~_k - E_k and ub_k = v~_k + E_k the
+// exact minimiser and its FP64 near-ties always satisfy lb_k <= min_l ub_l + tie window, and a
+// control is dropped from the list only when another control's upper bound lies below its
+// lower bound by more than the tie window.
 
 constexpr int kTX = 32, kTY = 8;
-
-template <typename T>
-__device__ __forceinline__ T eval_smem(const FineTab &tab, const int32_t *__restrict__ slin,
-                                       int e, const T *__restrict__ xs, int sidx) {
-  const int nt = tab.nt[e];
-  const T *w = tab_w<T>(tab);
-  const T x0 = xs[sidx];
-  T acc = T(0);
-  for (int t = 0; t < nt; ++t) {
-    const int ix = e * tab.tmax + t;
-    acc = fma(__ldg(w + ix), xs[sidx + __ldg(slin + ix)] - x0, acc);
-  }
-  return acc;
-}
 
 __device__ __forceinline__ double eval_global64(const FineTab &tab, int e, const double *__restrict__ X,
                                                 int j) {
@@ -89,52 +77,79 @@ __device__ __forceinline__ double eval_global64(const FineTab &tab, int e, const
   return acc;
 }
 
+__device__ __forceinline__ double eval_smem64(const FineTab &tab, const int32_t *__restrict__ slin, int e,
+                                              const double *__restrict__ xs, int sidx) {
+  const int nt = tab.nt[e];
+  const double x0 = xs[sidx];
+  double acc = 0.0;
+  for (int t = 0; t < nt; ++t) {
+    const int ix = e * tab.tmax + t;
+    acc = fma(__ldg(tab.w64 + ix), xs[sidx + __ldg(slin + ix)] - x0, acc);
+  }
+  return acc;
+}
+
+// FP32 screen of one control: returns sum_t w (dd_t) and S = sum_t w |dd_t|.
+__device__ __forceinline__ float eval_smem32(const FineTab &tab, const int32_t *__restrict__ slin, int e,
+                                             const float *__restrict__ hs, const float *__restrict__ ls,
+                                             int sidx, float &S) {
+  const int nt = tab.nt[e];
+  const float h0 = hs[sidx], l0 = ls[sidx];
+  float acc = 0.f, sa = 0.f;
+  for (int t = 0; t < nt; ++t) {
+    const int ix = e * tab.tmax + t;
+    const int o = sidx + __ldg(slin + ix);
+    const float w = __ldg(tab.w32 + ix);
+    const float dd = (hs[o] - h0) + (ls[o] - l0);
+    acc = fmaf(w, dd, acc);
+    sa = fmaf(w, fabsf(dd), sa);
+  }
+  S = sa;
+  return acc;
+}
+
+__device__ __forceinline__ void cand_push(unsigned long long &cand, int &ncand, bool &overflow, int k) {
+  if (ncand < kMaxCand) cand |= (unsigned long long)k << (8 * ncand++);
+  else overflow = true;
+}
+
 template <int SCREEN>
 __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
-  using TS = typename std::conditional<SCREEN, float, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TS *xs = reinterpret_cast<TS *>(smem_raw);
-  __shared__ float red_max[kTX * kTY / 32];
   __shared__ unsigned red_cnt[kTX * kTY / 32];
+  __shared__ float red_max[kTX * kTY / 32];
+  const int S_ = a.SW * a.SH;
+  double *xs64 = reinterpret_cast<double *>(smem_raw);
+  float *hs = reinterpret_cast<float *>(smem_raw);
+  float *ls = hs + S_;
 
   const FineTab &tab = a.tab;
   const int n = tab.n, m = tab.m;
   const int tid = threadIdx.y * kTX + threadIdx.x;
   const int o1 = 1 + blockIdx.x * kTX - a.halo;  // grid coordinate of staged column 0
   const int o2 = 1 + blockIdx.y * kTY - a.halo;
-  // reference value of the tile (its centre node, clamped into the grid)
-  double xref = 0.0;
-  if (SCREEN) {
-    const int c1 = min(1 + int(blockIdx.x) * kTX + kTX / 2, n - 1);
-    const int c2 = min(1 + int(blockIdx.y) * kTY + kTY / 2, n - 1);
-    xref = a.X[size_t(c2) * n + c1];
-  }
-  float dmax = 0.f;
-  const int S = a.SW * a.SH;
-  for (int s = tid; s < S; s += kTX * kTY) {
+  float xmax = 0.f;
+  for (int s = tid; s < S_; s += kTX * kTY) {
     const int g1 = o1 + s % a.SW, g2 = o2 + s / a.SW;
-    TS v = TS(0);
-    if (g1 >= 0 && g1 < n && g2 >= 0 && g2 < n) {
-      const double xv = a.X[size_t(g2) * n + g1];
-      if (SCREEN) {
-        const double d = xv - xref;
-        v = TS(d);
-        dmax = fmaxf(dmax, float(fabs(d)) * (1.0f + 1.2e-7f));
-      } else {
-        v = TS(xv);
-      }
+    double xv = 0.0;
+    if (g1 >= 0 && g1 < n && g2 >= 0 && g2 < n) xv = a.X[size_t(g2) * n + g1];
+    if (SCREEN) {
+      const float hi = float(xv);
+      hs[s] = hi;
+      ls[s] = float(xv - double(hi));
+      xmax = fmaxf(xmax, fabsf(hi));
+    } else {
+      xs64[s] = xv;
     }
-    xs[s] = v;
   }
   if (SCREEN) {
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    if ((tid & 31) == 0) red_max[tid >> 5] = dmax;
+    for (int o = 16; o > 0; o >>= 1) xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    if ((tid & 31) == 0) red_max[tid >> 5] = xmax;
   }
   __syncthreads();
-  float D = 0.f;
-  if (SCREEN) {
-    for (int w = 0; w < kTX * kTY / 32; ++w) D = fmaxf(D, red_max[w]);
-  }
+  float Xmax = 0.f;
+  if (SCREEN)
+    for (int w = 0; w < kTX * kTY / 32; ++w) Xmax = fmaxf(Xmax, red_max[w]);
 
   const int i1 = 1 + blockIdx.x * kTX + threadIdx.x;
   const int i2 = 1 + blockIdx.y * kTY + threadIdx.y;
@@ -147,58 +162,69 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
     const int nf = a.nf;
     double Fv[4];
     float Fv32[4];
-    double Fabs = 0.0;
+    float Fabs = 0.f;
     for (int mm = 0; mm < nf && mm < 4; ++mm) {
       Fv[mm] = a.F[mm * N + j];
       Fv32[mm] = a.F32[mm * N + j];
-      Fabs += a.phimax[mm] * fabs(Fv[mm]);
+      Fabs = fmaf(float(a.phimax[mm]), fabsf(Fv32[mm]), Fabs);
     }
     const double Xj = a.X[j];
-    // per-node part of the FP32 screen bound
-    const double u = 5.9604644775390625e-8;
-    const double E0 = SCREEN ? 1.001 * u * ((6.0 + 2.0 * tab.tmax) * a.Wmax_class[q2 * tab.Q + q1] * double(D)
-                                             + (nf + 3.0) * Fabs + 3.0 * a.cmax * fabs(Xj))
-                             : 0.0;
-    // pass 1.  The candidate window is 2 (2 E0 + 4 u |v|) + 2 tie_rel max(1, |v|): twice what
-    // two bounded values can differ by, so it stays rigorous when the comparison itself is
-    // evaluated in the screening precision (its rounding is below the slack).
-    const TS c1 = SCREEN ? TS(8.0 * u + 2.0 * a.tie_rel) : TS(2.0 * a.tie_rel * (1.0 + 1e-9));
-    const TS M0 = SCREEN ? TS(4.0 * E0 * 1.0001 + 2.0 * a.tie_rel) : TS(0);
-    TS vmin = TS(INFINITY);
     unsigned long long cand = 0ull;
     int ncand = 0;
     bool overflow = false;
-    for (int k = 0; k < tab.K; ++k) {
-      const int e = (k * tab.Q + q2) * tab.Q + q1;
-      TS v = eval_smem<TS>(tab, a.slin, e, xs, sidx);
-      TS fk;
-      if (SCREEN) {
+    if (SCREEN) {
+      const float u = 5.9604645e-8f;
+      const float xj32 = float(Xj);
+      // node-constant part of E_k: f-term, c-term and the u^2 term (Xmax * 1.001 covers |X|)
+      const float Ef = u * ((nf + 3.0f) * Fabs * 1.001f + 3.0f * float(a.cmax) * fabsf(xj32) * 1.001f);
+      const float eta = 6.0f * u * u * Xmax * 1.001f + 1e-30f;
+      const float tw_rel = float(a.tie_rel) * 2.0f;
+      float Umin = INFINITY, Lmin = INFINITY;
+      for (int k = 0; k < tab.K; ++k) {
+        const int e = (k * tab.Q + q2) * tab.Q + q1;
+        float S;
+        const float acc = eval_smem32(tab, a.slin, e, hs, ls, sidx, S);
         float f = 0.f;
         for (int mm = 0; mm < nf && mm < 4; ++mm) f = fmaf(__ldg(a.phi32 + k * nf + mm), Fv32[mm], f);
-        fk = fmaf(tab.c32[k], float(Xj), f);
-      } else {
-        double f = 0.0;
-        for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
-        fk = fma(tab.c64[k], Xj, f);
-      }
-      v = v + fk;
-      if (!(v == v)) continue;  // NaN never enters the candidate list
-      const TS av = v < vmin ? (v < TS(0) ? -v : v) : (vmin < TS(0) ? -vmin : vmin);
-      const TS av1 = av > TS(1) ? av : TS(1);
-      const TS margin = SCREEN ? M0 + c1 * av1 : c1 * av1;
-      if (v < vmin) {
-        if (v < vmin - margin) {
+        const float v = acc + fmaf(tab.c32[k], xj32, f);
+        if (!(v == v)) continue;  // NaN never enters the candidate list
+        const int nt = tab.nt[e];
+        const float E = 2.0f * (u * ((nt + 4.0f) * S * 1.001f + 2.0f * fabsf(v)) + Ef +
+                                eta * __ldg(tab.W32 + e)) + 4.0f * u * fabsf(v);
+        const float lb = v - E, ub = v + E;
+        const float tw = tw_rel * fmaxf(1.0f, fabsf(v)) + 4.0f * u * fabsf(v);
+        Umin = fminf(Umin, ub);
+        if (ub + tw < Lmin) {          // every listed control is excluded by this one
           cand = (unsigned long long)k;
           ncand = 1;
           overflow = false;
-        } else {
-          if (ncand < kMaxCand) cand |= (unsigned long long)k << (8 * ncand++);
-          else overflow = true;
+          Lmin = lb;
+        } else if (lb <= Umin + tw) {
+          cand_push(cand, ncand, overflow, k);
+          Lmin = fminf(Lmin, lb);
         }
-        vmin = v;
-      } else if (v <= vmin + margin) {
-        if (ncand < kMaxCand) cand |= (unsigned long long)k << (8 * ncand++);
-        else overflow = true;
+      }
+    } else {
+      double vmin = INFINITY;
+      for (int k = 0; k < tab.K; ++k) {
+        const int e = (k * tab.Q + q2) * tab.Q + q1;
+        double f = 0.0;
+        for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
+        const double v = eval_smem64(tab, a.slin, e, xs64, sidx) + fma(tab.c64[k], Xj, f);
+        if (!(v == v)) continue;
+        const double margin = 2.0 * a.tie_rel * fmax(1.0, fabs(v < vmin ? v : vmin)) * (1.0 + 1e-9);
+        if (v < vmin) {
+          if (v < vmin - margin) {
+            cand = (unsigned long long)k;
+            ncand = 1;
+            overflow = false;
+          } else {
+            cand_push(cand, ncand, overflow, k);
+          }
+          vmin = v;
+        } else if (v <= vmin + margin) {
+          cand_push(cand, ncand, overflow, k);
+        }
       }
     }
     int best = -1;
@@ -208,21 +234,28 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
       // pass 2: exact FP64 decision among the candidates (all controls on overflow)
       const int cnt = overflow ? tab.K : ncand;
       double vm = INFINITY;
+      double vals[kMaxCand];
       for (int c = 0; c < cnt; ++c) {
         const int k = overflow ? c : int((cand >> (8 * c)) & 0xffull);
         const int e = (k * tab.Q + q2) * tab.Q + q1;
         double f = 0.0;
         for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
         const double v = eval_global64(tab, e, a.X, j) + fma(tab.c64[k], Xj, f);
+        if (c < kMaxCand) vals[c] = v;
         vm = fmin(vm, v);
       }
       const double thr = vm + a.tie_rel * fmax(1.0, fabs(vm));
       for (int c = 0; c < cnt && best < 0; ++c) {
         const int k = overflow ? c : int((cand >> (8 * c)) & 0xffull);
-        const int e = (k * tab.Q + q2) * tab.Q + q1;
-        double f = 0.0;
-        for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
-        const double v = eval_global64(tab, e, a.X, j) + fma(tab.c64[k], Xj, f);
+        double v;
+        if (c < kMaxCand) {
+          v = vals[c];
+        } else {
+          const int e = (k * tab.Q + q2) * tab.Q + q1;
+          double f = 0.0;
+          for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
+          v = eval_global64(tab, e, a.X, j) + fma(tab.c64[k], Xj, f);
+        }
         if (v <= thr) best = k;
       }
     }
@@ -250,7 +283,7 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
 
 cudaError_t launch_argmin(const ArgminArgs &a, cudaStream_t s) {
   dim3 blk(kTX, kTY), grd((a.tab.m + kTX - 1) / kTX, (a.tab.m + kTY - 1) / kTY);
-  const size_t bytes = size_t(a.SW) * a.SH * (a.screen ? sizeof(float) : sizeof(double));
+  const size_t bytes = size_t(a.SW) * a.SH * (a.screen ? 2 * sizeof(float) : sizeof(double));
   cudaError_t err;
   if (a.screen) {
     err = cudaFuncSetAttribute(k_argmin<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
@@ -350,34 +383,21 @@ void launch_hjb_resid(const FineTab &tab, const uint8_t *policy, const double *X
 }
 
 // ----------------------------------------------------------------------------- transfers
-// Full weighting: b_c(I) = sum_{a in {-1,0,1}^2} w_a1 w_a2 r_f(2I + a), w = (1/4, 1/2, 1/4).
+// Full weighting (restrict_point) and bilinear prolongation with correction (prolong_point).
 template <typename T>
 __global__ void k_restrict(const T *__restrict__ rf, int nf, T *__restrict__ bc, int nc) {
   const int I1 = 1 + blockIdx.x * 32 + threadIdx.x;
   const int I2 = 1 + blockIdx.y * 8 + threadIdx.y;
   if (I1 > nc - 2 || I2 > nc - 2) return;
-  const T *r0 = rf + size_t(2 * I2) * nf + 2 * I1;
-  const T rowm = T(0.25) * r0[-nf - 1] + T(0.5) * r0[-nf] + T(0.25) * r0[-nf + 1];
-  const T row0 = T(0.25) * r0[-1] + T(0.5) * r0[0] + T(0.25) * r0[1];
-  const T rowp = T(0.25) * r0[nf - 1] + T(0.5) * r0[nf] + T(0.25) * r0[nf + 1];
-  bc[size_t(I2) * nc + I1] = T(0.25) * rowm + T(0.5) * row0 + T(0.25) * rowp;
+  bc[size_t(I2) * nc + I1] = restrict_point<T>(rf, nf, I1, I2);
 }
 
-// Bilinear prolongation and correction: x_f(i) += sum_J P_{iJ} x_c(J).
 template <typename T>
 __global__ void k_prolong_add(const T *__restrict__ xc, int nc, T *__restrict__ xf, int nf) {
   const int i1 = 1 + blockIdx.x * 32 + threadIdx.x;
   const int i2 = 1 + blockIdx.y * 8 + threadIdx.y;
   if (i1 > nf - 2 || i2 > nf - 2) return;
-  const int J1 = i1 >> 1, J2 = i2 >> 1;
-  const bool odd1 = i1 & 1, odd2 = i2 & 1;
-  T v;
-  const T *c0 = xc + size_t(J2) * nc + J1;
-  if (!odd1 && !odd2) v = c0[0];
-  else if (odd1 && !odd2) v = T(0.5) * (c0[0] + c0[1]);
-  else if (!odd1 && odd2) v = T(0.5) * (c0[0] + c0[nc]);
-  else v = T(0.25) * ((c0[0] + c0[1]) + (c0[nc] + c0[nc + 1]));
-  xf[size_t(i2) * nf + i1] += v;
+  xf[size_t(i2) * nf + i1] += prolong_point<T>(xc, nc, i1, i2);
 }
 
 template <typename T>

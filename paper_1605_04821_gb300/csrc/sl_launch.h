@@ -55,8 +55,10 @@ template <typename T>
 void launch_prolong_add(const T *xc, int nc, T *xf, int nf, cudaStream_t s);
 
 // coarse levels
+// chunk_scratch: 2 * ceil((n-2)^2 / 256) ints of device scratch.
 void launch_classify(int level, const FineTab &tab, const uint8_t *policy, const int32_t *cls_prev,
-                     int n_prev, int32_t *cls, int n, int32_t *erow, int *count, cudaStream_t s);
+                     int n_prev, int32_t *cls, int n, int32_t *erow, int *count, int *chunk_scratch,
+                     cudaStream_t s);
 template <typename T>
 cudaError_t launch_rap_explicit(int level, const FineTab &tab, const int32_t *fine_off,
                                 const uint8_t *policy, T dt, const CoarseLev<T> &prev,
@@ -65,6 +67,18 @@ cudaError_t launch_rap_explicit(int level, const FineTab &tab, const int32_t *fi
 template <typename T>
 void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T omega, const T *x,
                       const T *b, T *y, cudaStream_t s);
+// Levels l0 .. L-1 of one V-cycle in a single thread block (x[l0] = M_l0^{-1} b[l0]).
+template <typename T>
+struct TailArgs {
+  int l0, L, nu1, nu2;
+  T omega;
+  CoarseLev<T> lev[kMaxLevels];
+  T *x[kMaxLevels], *t[kMaxLevels], *r[kMaxLevels], *b[kMaxLevels];
+  const T *Ainv;
+};
+template <typename T>
+void launch_vcycle_tail(const TailArgs<T> &a, cudaStream_t s);
+
 template <typename T>
 void launch_coarsest_setup(int level, const FineTab &tab, const uint8_t *policy, T dt,
                            const CoarseLev<T> &L, const int32_t *coff, double *work, T *Ainv,
