@@ -192,6 +192,22 @@ sl_status sl_hjb_apply(sl_hjb *h, int level, int precision, const void *x_dev, v
  * the correction) and are left unchanged; every interior entry is written. */
 sl_status sl_hjb_vcycle(sl_hjb *h, int precision, const void *b_dev, void *x_dev, void *stream);
 
+/* sl_hjb_vcycle without any device allocation.  The paper has no counterpart: this entry
+ * point is for callers that must not allocate device memory while they run, such as code in
+ * the middle of a global-mode CUDA stream capture (where cudaMalloc is refused) or a loop that
+ * runs under a fixed device-memory budget.  Same arguments and same result as sl_hjb_vcycle,
+ * but the V-cycle's work vectors live in one 2 MiB file-scope device array of the library
+ * instead of the handle's buffers, so they must fit there: fine grids up to 257 x 257 nodes in
+ * either precision (513 x 513 would need about 3.5 MB in FP32).  Larger grids get SL_EINVAL
+ * with a message giving the bytes needed; nothing is allocated and nothing runs.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current): make that first call before any stream capture.  Every call
+ * shares the one array and clears the part it uses first; calls that overlap on the GPU
+ * (other streams, threads or handles) race with one another.  Stream-ordered; returns without
+ * synchronising. */
+sl_status sl_hjb_vcycle_noalloc(sl_hjb *h, int precision, const void *b_dev, void *x_dev,
+                                void *stream);
+
 /* Solves A^alpha X = F^alpha of the step at time t with step dt for the current policy,
  * starting from x_ext_dev (n*n FP64, overwritten with the solution and psi(t) on the
  * boundary); u_prev_dev is U^{n-1}.  Uses BiCGSTAB (precision 0) or refinement (1). */

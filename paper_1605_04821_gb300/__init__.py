@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "SL_OK", 1: "SL_EINVAL", 2: "SL_ENOMEM", 3: "SL_ECUDA", 4: "S
 EXPORTED = ["sl_opts_default", "sl_hjb_create", "sl_hjb_step", "sl_hjb_solve",
             "sl_hjb_last_error", "sl_hjb_destroy", "sl_hjb_improve", "sl_hjb_set_policy",
             "sl_hjb_build_hierarchy", "sl_hjb_apply", "sl_hjb_vcycle", "sl_hjb_linear_solve",
-            "sl_hjb_level_info", "sl_hjb_num_levels", "sl_launch_count"]
+            "sl_hjb_level_info", "sl_hjb_num_levels", "sl_launch_count",
+            "sl_hjb_vcycle_noalloc"]
 
 
 class SlGrid(ctypes.Structure):
@@ -96,6 +97,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "sl_hjb_level_info": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ll), ctypes.POINTER(ll)]),
         "sl_hjb_num_levels": (i, [vp]),
         "sl_launch_count": (ll, []),
+        "sl_hjb_vcycle_noalloc": (i, [vp, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -238,6 +240,12 @@ class Solver:
         import torch
         prec = 0 if b.dtype == torch.float64 else 1
         self._check(self._lib.sl_hjb_vcycle(self.h, prec, _ptr(b), _ptr(x), _stream(stream)))
+
+    def vcycle_noalloc(self, b, x, stream=None):
+        """sl_hjb_vcycle_noalloc: the V-cycle with the library's static scratch (no allocation)."""
+        import torch
+        prec = 0 if b.dtype == torch.float64 else 1
+        self._check(self._lib.sl_hjb_vcycle_noalloc(self.h, prec, _ptr(b), _ptr(x), _stream(stream)))
 
     def linear_solve(self, u_prev, x_ext, t: float, dt: float, stream=None) -> dict:
         s = SlStats()

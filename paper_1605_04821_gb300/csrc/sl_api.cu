@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -650,6 +651,109 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
 
 }  // namespace
 
+// ---------------------------------------------------------------------- no-allocation V-cycle
+// Scratch of sl_hjb_vcycle_noalloc: a file-scope device array, so that the entry point needs no
+// cudaMalloc.  Every GPU that loads the library holds it until the process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(2) << 20;  // 2 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Host code cannot use g_noalloc_scratch as a device address (on the host it names a shadow
+// variable); its device address is looked up once per device, with that device current.
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[kMaxDevices] = {};
+
+sl_status noalloc_scratch(sl_hjb *h, void **out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(h, SL_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SL_OK;
+}
+
+// The V-cycle of vcycle() with every work vector taken from caller-provided storage
+// (t, r: smoother ping-pong and residual per level; cb, cx: coarse right-hand side and
+// correction per level >= 1).
+template <typename T>
+sl_status vcycle_into(sl_hjb *h, int l, double dt, const T *b, T *x, T *const *t, T *const *r,
+                      T *const *cb, T *const *cx, cudaStream_t s) {
+  const size_t N = NN(h, l);
+  if (l == h->L - 1) {
+    launch_coarsest_apply<T>(pick<T>(h->Ainv64, h->Ainv32), h->cl[l].n, b, x, s);
+    return SL_OK;
+  }
+  T *cur = x, *other = t[l];
+  if (h->o.nu1 == 0) {
+    launch_fill<T>(x, N, T(0), s);
+  } else {
+    level_op<T>(h, l, OP_JACOBI0, dt, nullptr, b, cur, s);
+    for (int it = 1; it < h->o.nu1; ++it) {
+      level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s);
+      std::swap(cur, other);
+    }
+  }
+  level_op<T>(h, l, OP_RESID, dt, cur, b, r[l], s);
+  launch_restrict<T>(r[l], h->cl[l].n, cb[l + 1], h->cl[l + 1].n, s);
+  sl_status st = vcycle_into<T>(h, l + 1, dt, cb[l + 1], cx[l + 1], t, r, cb, cx, s);
+  if (st != SL_OK) return st;
+  launch_prolong_add<T>(cx[l + 1], h->cl[l + 1].n, cur, h->cl[l].n, s);
+  for (int it = 0; it < h->o.nu2; ++it) {
+    level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s);
+    std::swap(cur, other);
+  }
+  if (cur != x) CK(cudaMemcpyAsync(x, cur, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CK(cudaGetLastError());
+  return SL_OK;
+}
+
+// Lays the work vectors out in the static scratch (each vector 256-byte aligned), clears the
+// part that is used (boundary entries must read as zero and the array keeps the previous
+// call's contents), and runs the cycle.
+template <typename T>
+sl_status vcycle_noalloc_T(sl_hjb *h, const T *b, T *x, cudaStream_t s) {
+  T *t[kMaxLevels] = {}, *r[kMaxLevels] = {}, *cb[kMaxLevels] = {}, *cx[kMaxLevels] = {};
+  size_t need = 0;
+  auto take = [&](size_t count) {
+    const size_t off = need;
+    need += (count * sizeof(T) + 255) / 256 * 256;
+    return off;
+  };
+  size_t ot[kMaxLevels], orr[kMaxLevels], ob[kMaxLevels], ox[kMaxLevels];
+  for (int l = 0; l < h->L; ++l) {
+    const size_t Nl = NN(h, l);
+    ot[l] = take(Nl);
+    orr[l] = take(Nl);
+    if (l > 0) {
+      ob[l] = take(Nl);
+      ox[l] = take(Nl);
+    }
+  }
+  if (need > kNoAllocScratchBytes)
+    return fail(h, SL_EINVAL, "sl_hjb_vcycle_noalloc: the V-cycle of this grid needs " +
+                                  std::to_string(need) + " bytes of scratch, more than the " +
+                                  std::to_string(kNoAllocScratchBytes) + " bytes available");
+  void *base = nullptr;
+  sl_status st = noalloc_scratch(h, &base);
+  if (st != SL_OK) return st;
+  unsigned char *p = static_cast<unsigned char *>(base);
+  for (int l = 0; l < h->L; ++l) {
+    t[l] = reinterpret_cast<T *>(p + ot[l]);
+    r[l] = reinterpret_cast<T *>(p + orr[l]);
+    if (l > 0) {
+      cb[l] = reinterpret_cast<T *>(p + ob[l]);
+      cx[l] = reinterpret_cast<T *>(p + ox[l]);
+    }
+  }
+  CK(cudaMemsetAsync(base, 0, need, s));
+  return vcycle_into<T>(h, 0, h->hier_dt, b, x, t, r, cb, cx, s);
+}
+
 // ====================================================================== C ABI
 extern "C" {
 
@@ -959,6 +1063,16 @@ sl_status sl_hjb_vcycle(sl_hjb *h, int precision, const void *b, void *x, void *
   if (r != SL_OK) return r;
   CK(cudaStreamSynchronize(s));
   return SL_OK;
+}
+
+sl_status sl_hjb_vcycle_noalloc(sl_hjb *h, int precision, const void *b, void *x, void *stream) {
+  if (!h || !b || !x) return SL_EINVAL;
+  if (!h->hier_valid || precision != h->o.precision)
+    return fail(h, SL_EINVAL, "V-cycle needs a built hierarchy in the handle's precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return precision == 0
+             ? vcycle_noalloc_T<double>(h, static_cast<const double *>(b), static_cast<double *>(x), s)
+             : vcycle_noalloc_T<float>(h, static_cast<const float *>(b), static_cast<float *>(x), s);
 }
 
 sl_status sl_hjb_linear_solve(sl_hjb *h, const double *u_prev, double *x_ext, double t, double dt,
