@@ -116,6 +116,9 @@ typedef struct {
   int coarse_tail_rows; /* levels with at most this many rows run, from the first such level
                            down, in one thread block per V-cycle; 0: never; -1: default
                            (1024 rows in mixed precision, 0 in FP64, whose per-SM rate is low) */
+  int extrapolate;      /* 1: when a step continues the previous one (same dt, t = t_prev + dt)
+                           its first linear solve starts from 2 U^{n-1} - U^{n-2}; Howard's stop
+                           test still measures against U^{n-1}.  0: start from U^{n-1}. */
 } sl_opts;
 
 typedef struct {
@@ -131,8 +134,9 @@ typedef struct {
 } sl_stats;
 
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
- * krylov_tol 1e-12, kry_max 200, inner_tol 1e-5, ir_max 30, pi_tol 1e-10, pi_max 100,
- * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0, use_graphs 1, coarse_tail_rows -1. */
+ * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
+ * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0, use_graphs 1, coarse_tail_rows -1,
+ * extrapolate 1. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every

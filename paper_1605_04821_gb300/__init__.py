@@ -52,7 +52,8 @@ class SlOpts(ctypes.Structure):
                 ("kry_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("ir_max", ctypes.c_int),
                 ("pi_tol", ctypes.c_double), ("pi_max", ctypes.c_int), ("tie_rel", ctypes.c_double),
                 ("argmin_screen", ctypes.c_int), ("rebuild_frac", ctypes.c_double),
-                ("use_graphs", ctypes.c_int), ("coarse_tail_rows", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("coarse_tail_rows", ctypes.c_int),
+                ("extrapolate", ctypes.c_int)]
 
 
 class SlStats(ctypes.Structure):

@@ -248,16 +248,61 @@ __device__ __forceinline__ void coarse_expl_row(const CoarseLev<T> &L, int slot,
   coarse_finish<T, OP>(y, x, b, j, acc, d, omega);
 }
 
+// Class rows from a shared-memory tile of x: 32 x 32 rows per block (four per thread, one
+// column) plus a halo of R (the level's stencil reach).  Class taps are packed {tile offset,
+// weight}.
+constexpr int kCRowsY = 32;
+
 template <typename T, int OP>
 __global__ void __launch_bounds__(256) k_coarse_op(CoarseLev<T> L, const int *__restrict__ nexpl_dev,
                                                    int tiles_x, int tiles, T omega, const T *__restrict__ x,
                                                    const T *__restrict__ b, T *__restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   if (int(blockIdx.x) < tiles) {
-    const int I1 = 1 + (blockIdx.x % tiles_x) * 32 + (threadIdx.x & 31);
-    const int I2 = 1 + (blockIdx.x / tiles_x) * 8 + (threadIdx.x >> 5);
-    if (I1 > L.m || I2 > L.m) return;
-    const int k = L.cls[(I2 - 1) * L.m + (I1 - 1)];
-    if (k >= 0) coarse_class_row<T, OP>(L, k, I2 * L.n + I1, omega, x, b, y);
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    const int R = L.R, SW = 32 + 2 * R, SH = kCRowsY + 2 * R;
+    const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (OP != OP_JACOBI0) {
+      const int o1 = 1 + bx * 32 - R, o2 = 1 + by * kCRowsY - R;
+      for (int r = ty; r < SH; r += 8) {
+        const int g2 = o2 + r;
+        const bool rowin = g2 >= 0 && g2 < L.n;
+        for (int c = tx; c < SW; c += 32) {
+          const int g1 = o1 + c;
+          xs[r * SW + c] = (rowin && g1 >= 0 && g1 < L.n) ? x[size_t(g2) * L.n + g1] : T(0);
+        }
+      }
+      __syncthreads();
+    }
+    const int I1 = 1 + bx * 32 + tx;
+    if (I1 > L.m) return;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int I2 = 1 + by * kCRowsY + ty + 8 * r;
+      if (I2 > L.m) continue;
+      const int k = L.cls[(I2 - 1) * L.m + (I1 - 1)];
+      if (k < 0) continue;
+      const int j = I2 * L.n + I1;
+      const T d = L.cdiag[k];
+      if (OP == OP_JACOBI0) {
+        y[j] = omega * b[j] / d;
+        continue;
+      }
+      const int sidx = (ty + 8 * r + R) * SW + tx + R;
+      T acc = T(0);
+      const int nt = L.cnt[k];
+#pragma unroll 4
+      for (int t = 0; t < nt; ++t) {
+        int off;
+        T w;
+        ClassTap<T>::get(L, k * L.ctmax + t, off, w);
+        acc = fma(w, xs[sidx + off], acc);
+      }
+      if (OP == OP_APPLY) y[j] = acc;
+      else if (OP == OP_RESID) y[j] = b[j] - acc;
+      else y[j] = xs[sidx] + omega * (b[j] - acc) / d;
+    }
     return;
   }
   const int nexpl = *nexpl_dev;
@@ -269,15 +314,21 @@ __global__ void __launch_bounds__(256) k_coarse_op(CoarseLev<T> L, const int *__
 template <typename T>
 void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T omega, const T *x,
                       const T *b, T *y, cudaStream_t s) {
-  const int tx = (L.m + 31) / 32, tiles = tx * ((L.m + 7) / 8);
+  const int tx = (L.m + 31) / 32, tiles = tx * ((L.m + kCRowsY - 1) / kCRowsY);
   const int eg = std::max(1, std::min(kRedBlocks, (L.cap + 255) / 256));
   const int grid = tiles + eg;
+  const size_t bytes = op == OP_JACOBI0 ? 0 : size_t(32 + 2 * L.R) * (kCRowsY + 2 * L.R) * sizeof(T);
+  if (bytes > 48 * 1024) {
+    cudaFuncSetAttribute(k_coarse_op<T, OP_APPLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    cudaFuncSetAttribute(k_coarse_op<T, OP_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    cudaFuncSetAttribute(k_coarse_op<T, OP_JACOBI>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  }
   note_launch();
   switch (op) {
-    case OP_APPLY: k_coarse_op<T, OP_APPLY><<<grid, 256, 0, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
-    case OP_RESID: k_coarse_op<T, OP_RESID><<<grid, 256, 0, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
-    case OP_JACOBI: k_coarse_op<T, OP_JACOBI><<<grid, 256, 0, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
-    default: k_coarse_op<T, OP_JACOBI0><<<grid, 256, 0, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
+    case OP_APPLY: k_coarse_op<T, OP_APPLY><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
+    case OP_RESID: k_coarse_op<T, OP_RESID><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
+    case OP_JACOBI: k_coarse_op<T, OP_JACOBI><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
+    default: k_coarse_op<T, OP_JACOBI0><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
   }
 }
 template void launch_coarse_op<double>(int, const CoarseLev<double> &, const int *, double,

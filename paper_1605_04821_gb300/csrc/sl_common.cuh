@@ -63,7 +63,13 @@ struct FineTab {
   const float *ws32;
   const double *c64;      // [K] discount
   const float *c32;
+  const double *od64;     // [e] omega / d_e with d_e = 1 + dt (W - c - w_self) (per hierarchy dt)
+  const float *od32;
+  const int2 *pk32;       // [e*tmax + t] {staged-tile offset, fp32 weight bits}
+  const longlong2 *pk64;  // [e*tmax + t] {staged-tile offset, fp64 weight bits}
 };
+
+
 
 template <typename T> SL_HD const T *tab_w(const FineTab &t);
 template <> SL_HD const double *tab_w<double>(const FineTab &t) { return t.w64; }
@@ -74,6 +80,9 @@ template <> SL_HD const float *tab_W<float>(const FineTab &t) { return t.W32; }
 template <typename T> SL_HD const T *tab_ws(const FineTab &t);
 template <> SL_HD const double *tab_ws<double>(const FineTab &t) { return t.ws64; }
 template <> SL_HD const float *tab_ws<float>(const FineTab &t) { return t.ws32; }
+template <typename T> SL_HD const T *tab_od(const FineTab &t);
+template <> SL_HD const double *tab_od<double>(const FineTab &t) { return t.od64; }
+template <> SL_HD const float *tab_od<float>(const FineTab &t) { return t.od32; }
 template <typename T> SL_HD const T *tab_c(const FineTab &t);
 template <> SL_HD const double *tab_c<double>(const FineTab &t) { return t.c64; }
 template <> SL_HD const float *tab_c<float>(const FineTab &t) { return t.c32; }
@@ -84,7 +93,10 @@ struct CoarseLev {
   int n, m, R, win;        // nodes per dim, interior per dim, window reach, (2R+1)^2
   const int32_t *cls;      // [m*m] >= 0: class k; < 0: explicit slot -cls-1
   // class tables: sparse taps of S_k (entry k), including the centre coefficient
-  const int32_t *clin;     // [k*ctmax + t]
+  const int32_t *clin;     // [k*ctmax + t] linear offset dy*n + dx
+  const int32_t *coff;     // [k*ctmax + t] packed (dy << 16) | (dx & 0xffff)
+  const int2 *cpk32;       // [k*ctmax + t] {dy*(32+2R) + dx, fp32 weight bits} (staged tile)
+  const longlong2 *cpk64;  // [k*ctmax + t] {dy*(32+2R) + dx, fp64 weight bits}
   const T *cw;             // [k*ctmax + t]
   const int32_t *cnt;      // [k]
   const T *cdiag;          // [k]
@@ -94,6 +106,41 @@ struct CoarseLev {
   const int32_t *erow;     // [slot] linear full-grid index of the row
   int cap;
 };
+
+#ifdef __CUDACC__
+// One tap of a staged tile: offset in the tile and weight, loaded with a single vector load.
+template <typename T> struct PackedTap;
+template <> struct PackedTap<float> {
+  static __device__ __forceinline__ void get(const FineTab &t, int ix, int &off, float &w) {
+    const int2 p = __ldg(t.pk32 + ix);
+    off = p.x;
+    w = __int_as_float(p.y);
+  }
+};
+template <> struct PackedTap<double> {
+  static __device__ __forceinline__ void get(const FineTab &t, int ix, int &off, double &w) {
+    const longlong2 p = __ldg(t.pk64 + ix);
+    off = int(p.x);
+    w = __longlong_as_double(p.y);
+  }
+};
+
+template <typename T> struct ClassTap;
+template <> struct ClassTap<float> {
+  static __device__ __forceinline__ void get(const CoarseLev<float> &L, int ix, int &off, float &w) {
+    const int2 p = __ldg(L.cpk32 + ix);
+    off = p.x;
+    w = __int_as_float(p.y);
+  }
+};
+template <> struct ClassTap<double> {
+  static __device__ __forceinline__ void get(const CoarseLev<double> &L, int ix, int &off, double &w) {
+    const longlong2 p = __ldg(L.cpk64 + ix);
+    off = int(p.x);
+    w = __longlong_as_double(p.y);
+  }
+};
+#endif
 
 // Full-weighting and bilinear 1-D weights: R uses (1, 2, 1)/4 per dimension, P uses 1 at
 // even fine indices and (1/2, 1/2) at odd ones.

@@ -89,20 +89,33 @@ __device__ __forceinline__ double eval_smem64(const FineTab &tab, const int32_t 
   return acc;
 }
 
-// FP32 screen of one control: returns sum_t w (dd_t) and S = sum_t w |dd_t|.
-__device__ __forceinline__ float eval_smem32(const FineTab &tab, const int32_t *__restrict__ slin, int e,
-                                             const float *__restrict__ hs, const float *__restrict__ ls,
-                                             int sidx, float &S) {
-  const int nt = tab.nt[e];
+// FP32 screen of one control: returns sum_t w (dd_t) and S = sum_t w |dd_t|.  Taps are packed
+// {tile offset, weight}; with TMAX > 0 the loop runs over the padded width, fully unrolled.
+template <int TMAX>
+__device__ __forceinline__ float eval_smem32(const FineTab &tab, int e, const float *__restrict__ hs,
+                                             const float *__restrict__ ls, int sidx, float &S) {
   const float h0 = hs[sidx], l0 = ls[sidx];
   float acc = 0.f, sa = 0.f;
-  for (int t = 0; t < nt; ++t) {
-    const int ix = e * tab.tmax + t;
-    const int o = sidx + __ldg(slin + ix);
-    const float w = __ldg(tab.w32 + ix);
-    const float dd = (hs[o] - h0) + (ls[o] - l0);
-    acc = fmaf(w, dd, acc);
-    sa = fmaf(w, fabsf(dd), sa);
+  if (TMAX > 0) {
+#pragma unroll
+    for (int t = 0; t < TMAX; ++t) {
+      int o;
+      float w;
+      PackedTap<float>::get(tab, e * TMAX + t, o, w);
+      const float dd = (hs[sidx + o] - h0) + (ls[sidx + o] - l0);
+      acc = fmaf(w, dd, acc);
+      sa = fmaf(w, fabsf(dd), sa);
+    }
+  } else {
+    const int nt = tab.nt[e];
+    for (int t = 0; t < nt; ++t) {
+      int o;
+      float w;
+      PackedTap<float>::get(tab, e * tab.tmax + t, o, w);
+      const float dd = (hs[sidx + o] - h0) + (ls[sidx + o] - l0);
+      acc = fmaf(w, dd, acc);
+      sa = fmaf(w, fabsf(dd), sa);
+    }
   }
   S = sa;
   return acc;
@@ -113,7 +126,7 @@ __device__ __forceinline__ void cand_push(unsigned long long &cand, int &ncand, 
   else overflow = true;
 }
 
-template <int SCREEN>
+template <int SCREEN, int TMAX>
 __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned red_cnt[kTX * kTY / 32];
@@ -129,17 +142,20 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
   const int o1 = 1 + blockIdx.x * kTX - a.halo;  // grid coordinate of staged column 0
   const int o2 = 1 + blockIdx.y * kTY - a.halo;
   float xmax = 0.f;
-  for (int s = tid; s < S_; s += kTX * kTY) {
-    const int g1 = o1 + s % a.SW, g2 = o2 + s / a.SW;
-    double xv = 0.0;
-    if (g1 >= 0 && g1 < n && g2 >= 0 && g2 < n) xv = a.X[size_t(g2) * n + g1];
-    if (SCREEN) {
-      const float hi = float(xv);
-      hs[s] = hi;
-      ls[s] = float(xv - double(hi));
-      xmax = fmaxf(xmax, fabsf(hi));
-    } else {
-      xs64[s] = xv;
+  for (int r = threadIdx.y; r < a.SH; r += kTY) {
+    const int g2 = o2 + r;
+    for (int cc = threadIdx.x; cc < a.SW; cc += kTX) {
+      const int g1 = o1 + cc, s = r * a.SW + cc;
+      double xv = 0.0;
+      if (g1 >= 0 && g1 < n && g2 >= 0 && g2 < n) xv = a.X[size_t(g2) * n + g1];
+      if (SCREEN) {
+        const float hi = float(xv);
+        hs[s] = hi;
+        ls[s] = float(xv - double(hi));
+        xmax = fmaxf(xmax, fabsf(hi));
+      } else {
+        xs64[s] = xv;
+      }
     }
   }
   if (SCREEN) {
@@ -183,7 +199,7 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
       for (int k = 0; k < tab.K; ++k) {
         const int e = (k * tab.Q + q2) * tab.Q + q1;
         float S;
-        const float acc = eval_smem32(tab, a.slin, e, hs, ls, sidx, S);
+        const float acc = eval_smem32<TMAX>(tab, e, hs, ls, sidx, S);
         float f = 0.f;
         for (int mm = 0; mm < nf && mm < 4; ++mm) f = fmaf(__ldg(a.phi32 + k * nf + mm), Fv32[mm], f);
         const float v = acc + fmaf(tab.c32[k], xj32, f);
@@ -281,74 +297,176 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
   }
 }
 
+template <int SCREEN, int TMAX>
+cudaError_t argmin_launch(const ArgminArgs &a, dim3 grd, dim3 blk, size_t bytes, cudaStream_t s) {
+  cudaError_t err = cudaFuncSetAttribute(k_argmin<SCREEN, TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(bytes));
+  if (err != cudaSuccess) return err;
+  note_launch();
+  k_argmin<SCREEN, TMAX><<<grd, blk, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_argmin(const ArgminArgs &a, cudaStream_t s) {
   dim3 blk(kTX, kTY), grd((a.tab.m + kTX - 1) / kTX, (a.tab.m + kTY - 1) / kTY);
   const size_t bytes = size_t(a.SW) * a.SH * (a.screen ? 2 * sizeof(float) : sizeof(double));
-  cudaError_t err;
-  if (a.screen) {
-    err = cudaFuncSetAttribute(k_argmin<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    if (err != cudaSuccess) return err;
-    note_launch();
-    k_argmin<1><<<grd, blk, bytes, s>>>(a);
-  } else {
-    err = cudaFuncSetAttribute(k_argmin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    if (err != cudaSuccess) return err;
-    note_launch();
-    k_argmin<0><<<grd, blk, bytes, s>>>(a);
+  if (!a.screen) return argmin_launch<0, 0>(a, grd, blk, bytes, s);
+  switch (a.tab.tmax) {
+    case 8: return argmin_launch<1, 8>(a, grd, blk, bytes, s);
+    case 12: return argmin_launch<1, 12>(a, grd, blk, bytes, s);
+    case 16: return argmin_launch<1, 16>(a, grd, blk, bytes, s);
+    case 20: return argmin_launch<1, 20>(a, grd, blk, bytes, s);
+    default: return argmin_launch<1, 0>(a, grd, blk, bytes, s);
   }
-  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------- fine operator
 // (A x)_j = (1 + dt (W - c_k)) x_j - dt sum_t w_t x_{j+o_t}  (Eq. FullScheme, theta = 1; x has
 // zero boundary entries, so boundary taps drop out as they belong to the right-hand side).
 // Diagonal entry d_j = 1 + dt (W - c_k - w_self).
+//
+// Each block stages a 32 x 16 tile of x plus a halo of the longest tap in shared memory; each
+// thread computes two rows of one column (i2 = base + ty and base + ty + 8) independently (the
+// policy changes too often along a column for rows to share their taps).  Taps are packed
+// {tile offset, weight} and the loop runs over the padded table width TMAX (unused slots carry
+// weight 0 at offset 0), fully unrolled, so all table loads of a row are issued together.
+constexpr int kOpRowsY = 16;
+
 template <typename T, int OP>
-__global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__restrict__ policy, T dt,
-                                                 T omega, const T *__restrict__ x,
-                                                 const T *__restrict__ b, T *__restrict__ y) {
-  const int i1 = 1 + blockIdx.x * 32 + threadIdx.x;
-  const int i2 = 1 + blockIdx.y * 8 + threadIdx.y;
-  const int n = tab.n, m = tab.m;
-  if (i1 > m || i2 > m) return;
-  const int j = i2 * n + i1;
-  const int k = policy[(i2 - 1) * m + (i1 - 1)];
-  const int e = (k * tab.Q + class_q(i2, n, tab.B)) * tab.Q + class_q(i1, n, tab.B);
-  const T W = tab_W<T>(tab)[e], c = tab_c<T>(tab)[k];
-  const T d = T(1) + dt * (W - c - tab_ws<T>(tab)[e]);
-  if (OP == OP_JACOBI0) {
-    y[j] = omega * b[j] / d;
-    return;
-  }
-  const int nt = tab.nt[e];
-  const T *w = tab_w<T>(tab);
-  T acc = T(0);
-  for (int t = 0; t < nt; ++t) {
-    const int ix = e * tab.tmax + t;
-    acc = fma(__ldg(w + ix), __ldg(x + j + __ldg(tab.lin + ix)), acc);
-  }
-  const T xj = x[j];
-  const T ax = (T(1) + dt * (W - c)) * xj - dt * acc;
+__device__ __forceinline__ void fine_finish(T *y, const T *b, int j, T xj, T ax, T od) {
   if (OP == OP_APPLY) y[j] = ax;
   else if (OP == OP_RESID) y[j] = b[j] - ax;
-  else y[j] = xj + omega * (b[j] - ax) / d;
+  else y[j] = xj + od * (b[j] - ax);
+}
+
+// Stages rows [o2, o2 + SH) x columns [o1, o1 + SW) of a full-grid vector into shared memory,
+// with zeros outside the grid; tiles whose halo lies inside the grid skip the bounds checks.
+template <typename T>
+__device__ __forceinline__ void stage_tile(T *xs, const T *__restrict__ x, int n, int o1, int o2, int SW,
+                                           int SH, int tx, int ty) {
+  if (o1 >= 0 && o2 >= 0 && o1 + SW <= n && o2 + SH <= n) {
+    const T *src = x + size_t(o2) * n + o1;
+    for (int r = ty; r < SH; r += 8)
+      for (int c = tx; c < SW; c += 32) xs[r * SW + c] = src[size_t(r) * n + c];
+  } else {
+    for (int r = ty; r < SH; r += 8) {
+      const int g2 = o2 + r;
+      const bool rowin = g2 >= 0 && g2 < n;
+      for (int c = tx; c < SW; c += 32) {
+        const int g1 = o1 + c;
+        xs[r * SW + c] = (rowin && g1 >= 0 && g1 < n) ? x[size_t(g2) * n + g1] : T(0);
+      }
+    }
+  }
+}
+
+template <typename T, int OP, int TMAX>
+__global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__restrict__ policy, T dt, T omega,
+                                                 const T *__restrict__ x, const T *__restrict__ b,
+                                                 T *__restrict__ y, int halo, int SW) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  const int n = tab.n, m = tab.m;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  if (OP != OP_JACOBI0) {
+    stage_tile<T>(xs, x, n, 1 + blockIdx.x * 32 - halo, 1 + blockIdx.y * kOpRowsY - halo, SW,
+                  kOpRowsY + 2 * halo, tx, ty);
+    __syncthreads();
+  }
+  const int i1 = 1 + blockIdx.x * 32 + tx;
+  if (i1 > m) return;
+  const int q1 = class_q(i1, n, tab.B);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int i2 = 1 + blockIdx.y * kOpRowsY + ty + 8 * r;
+    if (i2 > m) continue;
+    const int k = policy[(i2 - 1) * m + (i1 - 1)];
+    const int e = (k * tab.Q + class_q(i2, n, tab.B)) * tab.Q + q1;
+    const int j = i2 * n + i1;
+    if (OP == OP_JACOBI0) {
+      y[j] = tab_od<T>(tab)[e] * b[j];
+      continue;
+    }
+    const int sidx = (ty + 8 * r + halo) * SW + tx + halo;
+    T acc = T(0);
+    if (TMAX > 0) {
+#pragma unroll
+      for (int t = 0; t < TMAX; ++t) {
+        int off;
+        T w;
+        PackedTap<T>::get(tab, e * TMAX + t, off, w);
+        acc = fma(w, xs[sidx + off], acc);
+      }
+    } else {
+      const int nt = tab.nt[e];
+      for (int t = 0; t < nt; ++t) {
+        int off;
+        T w;
+        PackedTap<T>::get(tab, e * tab.tmax + t, off, w);
+        acc = fma(w, xs[sidx + off], acc);
+      }
+    }
+    const T xj = xs[sidx];
+    const T diag = T(1) + dt * (tab_W<T>(tab)[e] - tab_c<T>(tab)[k]);
+    fine_finish<T, OP>(y, b, j, xj, diag * xj - dt * acc, OP == OP_JACOBI ? tab_od<T>(tab)[e] : T(0));
+  }
+}
+
+template <typename T, int OP>
+void fine_op_dispatch(const FineTab &tab, const uint8_t *policy, T dt, T omega, const T *x, const T *b,
+                      T *y, int halo, int SW, cudaStream_t s) {
+  dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + kOpRowsY - 1) / kOpRowsY);
+  const size_t bytes = OP == OP_JACOBI0 ? 0 : size_t(SW) * (kOpRowsY + 2 * halo) * sizeof(T);
+  if (bytes > 48 * 1024) {  // wide stencils: opt in to more dynamic shared memory
+    cudaFuncSetAttribute(k_fine_op<T, OP, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    cudaFuncSetAttribute(k_fine_op<T, OP, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    cudaFuncSetAttribute(k_fine_op<T, OP, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    cudaFuncSetAttribute(k_fine_op<T, OP, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    cudaFuncSetAttribute(k_fine_op<T, OP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  }
+  note_launch();
+  switch (tab.tmax) {
+    case 8: k_fine_op<T, OP, 8><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
+    case 12: k_fine_op<T, OP, 12><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
+    case 16: k_fine_op<T, OP, 16><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
+    case 20: k_fine_op<T, OP, 20><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
+    default: k_fine_op<T, OP, 0><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
+  }
 }
 
 template <typename T>
-void launch_fine_op(int op, const FineTab &tab, const uint8_t *policy, T dt, T omega, const T *x,
-                    const T *b, T *y, cudaStream_t s) {
-  dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + 7) / 8);
+void launch_fine_op(int op, const FineTab &tab, const int32_t *slin, const uint8_t *policy, T dt,
+                    T omega, const T *x, const T *b, T *y, int halo, int SW, cudaStream_t s) {
+  (void)slin;
   switch (op) {
-    case OP_APPLY: note_launch(); k_fine_op<T, OP_APPLY><<<grd, blk, 0, s>>>(tab, policy, dt, omega, x, b, y); break;
-    case OP_RESID: note_launch(); k_fine_op<T, OP_RESID><<<grd, blk, 0, s>>>(tab, policy, dt, omega, x, b, y); break;
-    case OP_JACOBI: note_launch(); k_fine_op<T, OP_JACOBI><<<grd, blk, 0, s>>>(tab, policy, dt, omega, x, b, y); break;
-    default: note_launch(); k_fine_op<T, OP_JACOBI0><<<grd, blk, 0, s>>>(tab, policy, dt, omega, x, b, y); break;
+    case OP_APPLY: fine_op_dispatch<T, OP_APPLY>(tab, policy, dt, omega, x, b, y, halo, SW, s); break;
+    case OP_RESID: fine_op_dispatch<T, OP_RESID>(tab, policy, dt, omega, x, b, y, halo, SW, s); break;
+    case OP_JACOBI: fine_op_dispatch<T, OP_JACOBI>(tab, policy, dt, omega, x, b, y, halo, SW, s); break;
+    default: fine_op_dispatch<T, OP_JACOBI0>(tab, policy, dt, omega, x, b, y, halo, SW, s); break;
   }
 }
-template void launch_fine_op<double>(int, const FineTab &, const uint8_t *, double, double,
-                                     const double *, const double *, double *, cudaStream_t);
-template void launch_fine_op<float>(int, const FineTab &, const uint8_t *, float, float,
-                                    const float *, const float *, float *, cudaStream_t);
+template void launch_fine_op<double>(int, const FineTab &, const int32_t *, const uint8_t *, double,
+                                     double, const double *, const double *, double *, int, int,
+                                     cudaStream_t);
+template void launch_fine_op<float>(int, const FineTab &, const int32_t *, const uint8_t *, float,
+                                    float, const float *, const float *, float *, int, int,
+                                    cudaStream_t);
+
+// omega / d_e for every fine table entry, d_e = 1 + dt (W_e - c_k - w_self,e) (the Jacobi scale).
+__global__ void k_fine_od(FineTab tab, double dt, double omega, int E, double *od64, float *od32) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const int k = e / (tab.Q * tab.Q);
+    const double d64 = 1.0 + dt * (tab.W64[e] - tab.c64[k] - tab.ws64[e]);
+    const float d32 = 1.0f + float(dt) * (tab.W32[e] - tab.c32[k] - tab.ws32[e]);
+    od64[e] = omega / d64;
+    od32[e] = float(omega) / d32;
+  }
+}
+void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, float *od32, cudaStream_t s) {
+  const int E = tab.K * tab.Q * tab.Q;
+  note_launch();
+  k_fine_od<<<(E + 255) / 256, 256, 0, s>>>(tab, dt, omega, E, od64, od32);
+}
 
 // ----------------------------------------------------------------------------- HJB residual
 // r_j = F_j - (A X)_j = U^{n-1}_j - X_j + dt (sum_t w_t (X_{j+o_t} - X_j) + c_k X_j + f_k(j)),

@@ -135,6 +135,25 @@ FineTabHost build_fine_tables(int n, double h, int K, int P, const double *sigma
       }
     }
   }
+  // Shrink the table stride to the longest actual tap list (rounded up to a multiple of 4), so
+  // that kernels looping over the padded width do no work on slots that are always empty.
+  int maxnt = 1;
+  for (uint8_t v : t.nt) maxnt = std::max(maxnt, int(v));
+  const int stride = (maxnt + 3) / 4 * 4;
+  if (stride < t.tmax) {
+    std::vector<int32_t> dx(size_t(E) * stride, 0), dy(size_t(E) * stride, 0);
+    std::vector<double> w(size_t(E) * stride, 0.0);
+    for (int e = 0; e < E; ++e)
+      for (int s = 0; s < t.nt[e]; ++s) {
+        dx[size_t(e) * stride + s] = t.dx[size_t(e) * t.tmax + s];
+        dy[size_t(e) * stride + s] = t.dy[size_t(e) * t.tmax + s];
+        w[size_t(e) * stride + s] = t.w[size_t(e) * t.tmax + s];
+      }
+    t.dx.swap(dx);
+    t.dy.swap(dy);
+    t.w.swap(w);
+    t.tmax = stride;
+  }
   return t;
 }
 

@@ -268,6 +268,21 @@ void launch_convert(const Tin *x, Tout *y, size_t N, cudaStream_t s) {
   k_convert<Tin, Tout><<<kRedBlocks, kVecThreads, 0, s>>>(x, y, N);
 }
 
+// X = 2 U - V on interior nodes (boundary of X untouched).
+__global__ void k_extrapolate(double *__restrict__ X, const double *__restrict__ U,
+                              const double *__restrict__ V, int n) {
+  const size_t N = size_t(n) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
+    const int i1 = int(i % n), i2 = int(i / n);
+    if (i1 == 0 || i2 == 0 || i1 == n - 1 || i2 == n - 1) continue;
+    X[i] = 2.0 * U[i] - V[i];
+  }
+}
+void launch_extrapolate(double *X, const double *U, const double *V, int n, cudaStream_t s) {
+  note_launch();
+  k_extrapolate<<<kRedBlocks, kVecThreads, 0, s>>>(X, U, V, n);
+}
+
 __global__ void k_add_f32(double *__restrict__ x, const float *__restrict__ e, size_t N) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x)
     x[i] += double(e[i]);

@@ -40,9 +40,13 @@ void launch_coef(const double *G, int nf, int nq, const double *tau, const doubl
                  cudaStream_t s);
 cudaError_t launch_argmin(const ArgminArgs &a, cudaStream_t s);
 
+// slin: staged-tile tap offsets (pitch SW = 32 + 2 halo), the same table as the argmin's.
 template <typename T>
-void launch_fine_op(int op, const FineTab &tab, const uint8_t *policy, T dt, T omega,
-                    const T *x, const T *b, T *y, cudaStream_t s);
+void launch_fine_op(int op, const FineTab &tab, const int32_t *slin, const uint8_t *policy, T dt,
+                    T omega, const T *x, const T *b, T *y, int halo, int SW, cudaStream_t s);
+
+// Jacobi scale omega / d_e of every fine table entry for step size dt (into od64 / od32).
+void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, float *od32, cudaStream_t s);
 
 // r = U_prev - X + dt (L X + c X + f) for the current policy (interior), FP64.
 void launch_hjb_resid(const FineTab &tab, const uint8_t *policy, const double *X,
@@ -91,6 +95,7 @@ template <typename T>
 void launch_fill(T *x, size_t N, T v, cudaStream_t s);
 template <typename Tin, typename Tout>
 void launch_convert(const Tin *x, Tout *y, size_t N, cudaStream_t s);
+void launch_extrapolate(double *X, const double *U, const double *V, int n, cudaStream_t s);
 void launch_add_f32_to_f64(double *x, const float *e, size_t N, cudaStream_t s);
 
 enum Post { POST_RHO_INIT = 0, POST_ALPHA = 1, POST_SS = 2, POST_OMEGA = 3, POST_RHO = 4,
