@@ -350,6 +350,7 @@ class StepResult:
     pi_iters: int
     iterates: List[np.ndarray]
     converged: bool
+    solve_policy: Optional[np.ndarray] = None   # policy of the last linear solve (defines A_n)
 
 
 def howard_step(prob, U_prev: np.ndarray, t: float, dt: float, policy0=None,
@@ -382,11 +383,12 @@ def howard_step(prob, U_prev: np.ndarray, t: float, dt: float, policy0=None,
         new_policy = improve(control_values(prob, X_full, t, f_full))
         same = bool(np.all(new_policy == policy))
         small = np.max(np.abs(X - X_prev)) <= pi_tol * max(1.0, np.max(np.abs(X)))
+        used = policy
         policy = new_policy
         X_prev = X
         if same or small:
-            return StepResult(X_full, policy, it, iterates, True)
-    return StepResult(X_full, policy, pi_max, iterates, False)
+            return StepResult(X_full, policy, it, iterates, True, used)
+    return StepResult(X_full, policy, pi_max, iterates, False, used)
 
 
 @dataclasses.dataclass
