@@ -162,6 +162,47 @@ sl_status sl_hjb_step(sl_hjb *h, double *u_dev, double t_n, double dt, uint8_t *
 sl_status sl_hjb_solve(sl_hjb *h, double *u_dev, double t0, double T, int n_steps,
                        uint8_t *policy_out_dev, sl_stats *stats, void *stream);
 
+/* ---- Discrete adjoint: gradients of J = sum_x w(x) U^N(x) through the implicit march ----
+ *
+ * Each step of Eq. FullScheme (theta = 1) at its converged policy alpha_n is the linear system
+ * A_n U^n = U^{n-1} + dt f^{alpha_n}(t_n) + (boundary terms).  The paper solves these
+ * systems forwards; the adjoint differentiates the same discrete march backwards at fixed
+ * policies (valid wherever no policy switches under a small perturbation):
+ *   A_N^T mu_N = w,  A_n^T mu_n = mu_{n+1}  (the unknowns are the interior nodes),
+ *   dJ/dg                    = mu_1,
+ *   dJ/dG[m][q](x)          = sum_n dt tau_q(t_n) phi[alpha_n(x), m] mu_n(x),
+ *   dJ/dtheta                = sum_n dt mu_n^T (dL^{alpha_n}/dtheta U^n)
+ * for a scalar parameter theta of the diffusion coefficients, with dL/dtheta the derivative
+ * of the truncated Scheme-2 operator (Proposition 2.2, Eq. Lhat: endpoints, truncation
+ * factors mu, weights A_p, B_p and the bilinear taps) on the piece of its piecewise-smooth
+ * dependence on sigma that the current sigma lies in.  Each backward system is solved like a
+ * forward one (BiCGSTAB preconditioned by a V-cycle built from the transposed Galerkin levels
+ * A_l^T = R A_{l-1}^T P, or the mixed-precision refinement), to opts.krylov_tol. */
+
+/* sl_hjb_solve that also records, for sl_hjb_adjoint, the policy of every step's last linear
+ * solve (the policy that defines A_n; one byte per interior node and step) and U^n at every
+ * multiple of ckpt_every and at the last step (full grid, FP64).  ckpt_every = 1 keeps every
+ * U^n, so the backward pass solves nothing forward again; with ckpt_every = k > 1 the
+ * backward pass re-solves the steps between two checkpoints at their recorded policies
+ * (k - 1 extra fields of workspace).  The record lives in the handle until the next call;
+ * ckpt_every >= 1, otherwise SL_EINVAL.  Synchronises the stream. */
+sl_status sl_hjb_solve_record(sl_hjb *h, double *u_dev, double t0, double T, int n_steps,
+                              int ckpt_every, sl_stats *stats, void *stream);
+
+/* Backward pass over the last sl_hjb_solve_record.
+ *   w_dev        device, n*n: weights of J (boundary entries do not enter).
+ *   dJ_dg_dev    device, n*n out: dJ/dg (zero on the boundary, where g is not used).
+ *   dJ_dG_dev    device, nf*nq*n*n out (layout of sl_source.G_dev), or NULL to skip.
+ *   nparam       0 .. 8 scalar parameters theta_p of sigma.
+ *   dsigma       host, nparam*K*2*P: d sigma / d theta_p, laid out like sl_controls.sigma.
+ *   dJ_dtheta    host, nparam out.
+ * Returns SL_EINVAL without a preceding record or with bad arguments, and the status of a
+ * failing backward solve otherwise.  Leaves the handle's policy at the first step's;
+ * synchronises the stream. */
+sl_status sl_hjb_adjoint(sl_hjb *h, const double *w_dev, double *dJ_dg_dev, double *dJ_dG_dev,
+                         int nparam, const double *dsigma, double *dJ_dtheta, sl_stats *stats,
+                         void *stream);
+
 const char *sl_hjb_last_error(const sl_hjb *h);
 void sl_hjb_destroy(sl_hjb *h);
 

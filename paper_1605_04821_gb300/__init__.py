@@ -26,7 +26,7 @@ EXPORTED = ["sl_opts_default", "sl_hjb_create", "sl_hjb_step", "sl_hjb_solve",
             "sl_hjb_last_error", "sl_hjb_destroy", "sl_hjb_improve", "sl_hjb_set_policy",
             "sl_hjb_build_hierarchy", "sl_hjb_apply", "sl_hjb_vcycle", "sl_hjb_linear_solve",
             "sl_hjb_level_info", "sl_hjb_num_levels", "sl_launch_count",
-            "sl_hjb_vcycle_noalloc"]
+            "sl_hjb_vcycle_noalloc", "sl_hjb_solve_record", "sl_hjb_adjoint"]
 
 
 class SlGrid(ctypes.Structure):
@@ -99,6 +99,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "sl_hjb_num_levels": (i, [vp]),
         "sl_launch_count": (ll, []),
         "sl_hjb_vcycle_noalloc": (i, [vp, i, vp, vp, vp]),
+        "sl_hjb_solve_record": (i, [vp, vp, d, d, i, i, ctypes.POINTER(SlStats), vp]),
+        "sl_hjb_adjoint": (i, [vp, vp, vp, vp, i, vp, vp, ctypes.POINTER(SlStats), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -254,6 +256,34 @@ class Solver:
                                                   ctypes.byref(s), _stream(stream)))
         return s.as_dict()
 
+    def solve_record(self, u, t0: float, T: float, n_steps: int, ckpt_every: int = 1,
+                     stream=None) -> dict:
+        """sl_hjb_solve that records policies and checkpoints for a later adjoint()."""
+        s = SlStats()
+        self._check(self._lib.sl_hjb_solve_record(self.h, _ptr(u), t0, T, n_steps, ckpt_every,
+                                                  ctypes.byref(s), _stream(stream)))
+        return s.as_dict()
+
+    def adjoint(self, w, dJ_dg, dJ_dG=None, dsigma=None, stream=None):
+        """Backward pass of the last solve_record for J = sum w U^N.
+
+        Fills dJ_dg (n, n) and, if given, dJ_dG (nf, nq, n, n); dsigma (nparam, K, 2, P) host
+        array of d sigma / d theta_p.  Returns (dJ/dtheta as a numpy array, stats dict).
+        """
+        s = SlStats()
+        np_ = 0
+        ds_ptr = None
+        out = np.zeros(0)
+        if dsigma is not None:
+            dsigma = np.ascontiguousarray(dsigma, dtype=np.float64)
+            np_ = dsigma.shape[0]
+            out = np.zeros(np_)
+            ds_ptr = dsigma.ctypes.data_as(ctypes.c_void_p)
+        self._check(self._lib.sl_hjb_adjoint(
+            self.h, _ptr(w), _ptr(dJ_dg), _ptr(dJ_dG) if dJ_dG is not None else None, np_, ds_ptr,
+            out.ctypes.data_as(ctypes.c_void_p) if np_ else None, ctypes.byref(s), _stream(stream)))
+        return out, s.as_dict()
+
     def num_levels(self) -> int:
         return self._lib.sl_hjb_num_levels(self.h)
 
@@ -282,3 +312,38 @@ def solver_from_problem(prob, device=None, stream=None, **opt_kw) -> Solver:
     return Solver(prob.n, prob.lo, prob.hi, prob.sigma, prob.phi, G,
                   np.asarray(prob.tau_kind, dtype=np.int32), np.asarray(prob.tau_rate, dtype=np.float64),
                   b=prob.drift, c=prob.c, stream=stream, **kw, **opt_kw)
+
+
+def hjb_solve(solver: Solver, g, G, T: float, n_steps: int, ckpt_every: int = 1, theta=None,
+              dsigma=None):
+    """U(T) = implicit march of `solver` from g, differentiable in g, G and theta.
+
+    G must be the solver's own source tensor (the handle reads it in place).  theta (nparam,)
+    names scalar parameters of sigma whose directions d sigma / d theta are `dsigma`
+    (nparam, K, 2, P); its value is the point the solver was created at and is not read.
+    The backward pass is the library's discrete adjoint (sl_hjb_adjoint).
+    """
+    import torch
+
+    class _HJBSolve(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, g_, G_, theta_):
+            if G_.data_ptr() != solver._G.data_ptr():
+                raise ValueError("G must be the tensor the solver was created with")
+            u = g_.detach().clone().contiguous()
+            solver.solve_record(u, 0.0, T, n_steps, ckpt_every)
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            w = grad_u.detach().contiguous().to(torch.float64)
+            dg = torch.zeros_like(w)
+            dG = torch.zeros_like(solver._G) if ctx.needs_input_grad[1] else None
+            dth, _ = solver.adjoint(w, dg, dG, dsigma if theta is not None else None)
+            gth = None
+            if theta is not None:
+                gth = torch.as_tensor(dth, dtype=theta.dtype, device=theta.device)
+            return dg, dG, gth
+
+    th = theta if theta is not None else torch.zeros(0, dtype=torch.float64, device=g.device)
+    return _HJBSolve.apply(g, G, th)

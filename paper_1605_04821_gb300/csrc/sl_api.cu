@@ -27,6 +27,8 @@ struct CoarseBuf {
   longlong2 *cpk64 = nullptr;
   double *ewin64 = nullptr, *cw64 = nullptr, *cdiag64 = nullptr;
   float *ewin32 = nullptr, *cw32 = nullptr, *cdiag32 = nullptr;
+  double *cdense64 = nullptr, *WT64 = nullptr;  // class windows [k*win + e]; rows of A_l^T
+  float *cdense32 = nullptr, *WT32 = nullptr;
   long long class_nnz_sum = 0;  // sum over class rows of their table's non-zeros
   std::vector<int> cnt_host;
 };
@@ -59,7 +61,7 @@ struct sl_hjb {
   int n = 0, m = 0, K = 0, P = 0, nf = 0, nq = 0, npsi = 0;
   double h = 0;
   sl_opts o{};
-  std::vector<double> phi, phimax, tau_rate, psi_rate, cvec;
+  std::vector<double> phi, phimax, tau_rate, psi_rate, cvec, sigma;
   std::vector<int> tau_kind, psi_kind;
   const double *G = nullptr, *Psi = nullptr;
   FineTabHost ft;
@@ -101,9 +103,30 @@ struct sl_hjb {
   unsigned long long *d_changes = nullptr, *h_changes = nullptr;
   int *d_flags = nullptr, *h_flags = nullptr, *d_count = nullptr, *h_count = nullptr;
   IterGraph graph[2];           // [precision]
+  IterGraph graphT[2];          // [precision], transposed operators (adjoint solves)
+  bool transposed = false;      // level operators act as A_l^T (backward solves)
   int *chunk_scratch = nullptr; // classification counts / offsets
   int tail_l0 = 0;              // first level run by the single-block V-cycle tail (0: none)
   cudaStream_t cap_stream = nullptr;
+  // adjoint: fine A^T (CSR), gradient tables and the recorded forward march
+  int32_t *t_rowptr = nullptr, *t_col = nullptr;
+  int *t_cnt = nullptr, *t_scan = nullptr;
+  double *t_v64 = nullptr, *t_d64 = nullptr;
+  float *t_v32 = nullptr, *t_d32 = nullptr;
+  double *mu = nullptr, *lam = nullptr;        // full grid, zero boundary
+  double *d_dtheta = nullptr, *d_dpart = nullptr;
+  int32_t *dt_lin = nullptr;
+  double *dt_dw = nullptr, *dt_dW = nullptr;
+  uint8_t *dt_nt = nullptr;
+  size_t dt_cap[4] = {0, 0, 0, 0};            // capacities of dt_lin, dt_dw, dt_nt, dt_dW
+  uint8_t *rec_pol = nullptr;                  // [step][m*m] policy of each step's last solve
+  double *rec_U = nullptr;                     // checkpoints U^{c k} and U^N, full grid
+  double *rec_seg = nullptr;                   // recomputed U^s inside one segment
+  size_t rec_pol_cap = 0, rec_U_cap = 0, rec_seg_cap = 0;
+  uint8_t *rec_slot = nullptr;                 // where step_impl stores the solve policy
+  int rec_N = 0, rec_k = 0;
+  double rec_t0 = 0.0, rec_dt = 0.0;
+  bool rec_valid = false;
   std::vector<void *> allocs;
   std::string err;
   sl_status sticky = SL_OK;
@@ -319,6 +342,17 @@ sl_status build_class_tables(sl_hjb *h, double dt) {
       AL(c.cnt, size_t(h->K));
       AL(c.cdiag64, size_t(h->K));
       AL(c.cdiag32, size_t(h->K));
+      AL(c.cdense64, size_t(h->K) * c.win);
+      AL(c.cdense32, size_t(h->K) * c.win);
+    }
+    {
+      // dense class windows (read by the transposed coarse rows of the adjoint)
+      std::vector<double> dn(size_t(h->K) * c.win, 0.0);
+      for (int k = 0; k < h->K && interior_exists; ++k)
+        std::copy(cur[k].begin(), cur[k].end(), dn.begin() + size_t(k) * c.win);
+      std::vector<float> dn32(dn.begin(), dn.end());
+      CK(cudaMemcpy(c.cdense64, dn.data(), dn.size() * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c.cdense32, dn32.data(), dn32.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
     c.ctmax = ctmax;
     std::vector<float> w32(w.begin(), w.end()), d32(diag.begin(), diag.end());
@@ -378,7 +412,27 @@ sl_status build_hierarchy(sl_hjb *h, double dt, cudaStream_t s) {
 
 // ---------------------------------------------------------------------- V-cycle
 template <typename T>
+CsrTView<T> csrT_view(sl_hjb *h) {
+  CsrTView<T> A{};
+  A.n = h->n;
+  A.m = h->m;
+  A.rowptr = h->t_rowptr;
+  A.col = h->t_col;
+  A.v = pick<T>(h->t_v64, h->t_v32);
+  A.d = pick<T>(h->t_d64, h->t_d32);
+  return A;
+}
+
+template <typename T>
 void level_op(sl_hjb *h, int l, int op, double dt, const T *x, const T *b, T *y, cudaStream_t s) {
+  if (h->transposed) {
+    if (l == 0)
+      launch_fineT_op<T>(op, csrT_view<T>(h), T(h->o.omega), x, b, y, s);
+    else
+      launch_denseT_op<T>(op, h->cl[l].n, h->cl[l].R, pick<T>(h->cl[l].WT64, h->cl[l].WT32),
+                          T(h->o.omega), x, b, y, s);
+    return;
+  }
   if (l == 0)
     launch_fine_op<T>(op, h->tab, h->d_slin, h->policy, T(dt), T(h->o.omega), x, b, y, h->halo, h->SW, s);
   else
@@ -400,7 +454,7 @@ void vbufs<float>(VBuf &v, float **x, float **t, float **r, float **b) {
 template <typename T>
 sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) {
   const size_t N = NN(h, l);
-  if (l > 0 && l == h->tail_l0 && l < h->L - 1) {
+  if (l > 0 && l == h->tail_l0 && l < h->L - 1 && !h->transposed) {
     // coarse end of the cycle in one thread block; b and x are this level's own buffers
     TailArgs<T> a{};
     a.l0 = l;
@@ -419,7 +473,7 @@ sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) 
     return SL_OK;
   }
   if (l == h->L - 1) {
-    launch_coarsest_apply<T>(pick<T>(h->Ainv64, h->Ainv32), h->cl[l].n, b, x, s);
+    launch_coarsest_apply<T>(pick<T>(h->Ainv64, h->Ainv32), h->cl[l].n, b, x, s, h->transposed ? 1 : 0);
     return SL_OK;
   }
   T *bx, *bt, *br, *bb;
@@ -480,7 +534,7 @@ sl_status issue_iteration(sl_hjb *h, double dt, TX *x, T *r, T *rh, T *p, T *v, 
 template <typename T, typename TX>
 sl_status ensure_graph(sl_hjb *h, int prec, double dt, TX *x, T *r, T *rh, T *p, T *v, T *sv, T *t,
                        T *ph, T *sh, BicgScalars *S) {
-  IterGraph &g = h->graph[prec];
+  IterGraph &g = h->transposed ? h->graphT[prec] : h->graph[prec];
   if (g.exec && g.dt == dt) return SL_OK;
   if (g.exec) {
     cudaGraphExecDestroy(g.exec);
@@ -522,8 +576,9 @@ sl_status bicgstab(sl_hjb *h, double dt, TX *x, T *r, T *rh, T *p, T *v, T *sv, 
   *iters = 0;
   for (int it = 1; it <= maxit; ++it) {
     if (h->o.use_graphs) {
-      CK(cudaGraphLaunch(h->graph[prec].exec, s));
-      note_launch(int(h->graph[prec].kernels));
+      IterGraph &g = h->transposed ? h->graphT[prec] : h->graph[prec];
+      CK(cudaGraphLaunch(g.exec, s));
+      note_launch(int(g.kernels));
     } else {
       sl_status st = issue_iteration<T, TX>(h, dt, x, r, rh, p, v, sv, t, ph, sh, S, s);
       if (st != SL_OK) return st;
@@ -547,9 +602,12 @@ struct ResNorms {
 
 sl_status true_residual(sl_hjb *h, double dt, double tolk, double *r, ResNorms *nr, cudaStream_t s) {
   const size_t N = NN(h, 0);
-  launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r, s);
+  if (h->transposed)  // backward solve A^T mu = lambda
+    launch_fineT_op<double>(OP_RESID, csrT_view<double>(h), h->o.omega, h->mu, h->lam, r, s);
+  else
+    launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r, s);
   launch_init_scalars(h->S, tolk * tolk, s);
-  launch_norms(h->Fvec, N, 0, h->S, h->partials, h->counter, s);
+  launch_norms(h->transposed ? h->lam : h->Fvec, N, 0, h->S, h->partials, h->counter, s);
   launch_norms(r, N, 1, h->S, h->partials, h->counter, s);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(h->hS, h->S, sizeof(BicgScalars), cudaMemcpyDeviceToHost, s));
@@ -569,11 +627,16 @@ sl_status true_residual(sl_hjb *h, double dt, double tolk, double *r, ResNorms *
 // test bounds the error of the step: ||X - X*||_inf <= ||r||_inf.  When the Krylov recurrence
 // meets the 2-norm test but the true max-norm test fails, the inner threshold is tightened
 // tenfold and BiCGSTAB restarts from the true residual.
+//
+// With h->transposed set, the same loop solves the backward system A^T mu = lambda of the
+// adjoint (h->mu from its initial value, right-hand side h->lam).
 sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
   const size_t N = NN(h, 0);
   // ||F||: the residual at X = (0 inside, psi on the boundary) is F itself
-  launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, s);
+  if (!h->transposed)
+    launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, s);
   CK(cudaGetLastError());
+  double *X = h->transposed ? h->mu : h->X;
   KBuf &k = h->kb;
   const double tol = h->o.krylov_tol;
   double tolk = tol;   // threshold handed to BiCGSTAB's recurrence
@@ -595,7 +658,7 @@ sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
     int it = 0;
     if (fp64) {
       // BiCGSTAB on the true residual; S holds ||F||_2 and the threshold (tolk ||F||_2)^2
-      r = bicgstab<double, double>(h, dt, h->X, k.r64, k.rh64, k.p64, k.v64, k.s64, k.t64, k.ph64,
+      r = bicgstab<double, double>(h, dt, X, k.r64, k.rh64, k.p64, k.v64, k.s64, k.t64, k.ph64,
                                    k.sh64, h->S, h->o.kry_max - total, &it, s);
     } else {
       // refinement: FP32 inner solve of A e = fp32(r) from e = 0, then X += e in FP64
@@ -606,7 +669,7 @@ sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
       launch_dot2<float>(k.r32, k.r32, nullptr, nullptr, N, POST_BNORM, h->S32, h->partials, h->counter, s);
       r = bicgstab<float, float>(h, dt, k.e32, k.r32, k.rh32, k.p32, k.v32, k.s32, k.t32, k.ph32,
                                  k.sh32, h->S32, h->o.kry_max, &it, s);
-      launch_add_f32_to_f64(h->X, k.e32, N, s);
+      launch_add_f32_to_f64(X, k.e32, N, s);
       CK(cudaGetLastError());
     }
     total += it;
@@ -674,6 +737,8 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
     r = linear_solve(h, dt, st, s);
     if (st) st->t_solve_ms += now_ms() - ts;
     if (r != SL_OK) return r;
+    if (h->rec_slot)  // the policy that defines A_n for the adjoint
+      CK(cudaMemcpyAsync(h->rec_slot, h->policy, size_t(h->m) * h->m, cudaMemcpyDeviceToDevice, s));
     double ta = now_ms();
     long long ch = 0;
     r = improve(h, h->X, &ch, s);
@@ -700,6 +765,137 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
   }
   CK(cudaMemcpyAsync(u, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return fail(h, SL_ENOCONV_PI, "Howard iteration reached pi_max");
+}
+
+// ---------------------------------------------------------------------- adjoint
+// Grows a device buffer (contents are not kept).
+template <typename T>
+sl_status dgrow(sl_hjb *h, T **p, size_t *cap, size_t count) {
+  if (*p && *cap >= count) return SL_OK;
+  if (*p) {
+    CK(cudaDeviceSynchronize());
+    h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), static_cast<void *>(*p)));
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+  }
+  sl_status st = dalloc(h, p, count);
+  if (st != SL_OK) return st;
+  *cap = count;
+  return SL_OK;
+}
+
+sl_status ensure_adjoint_buffers(sl_hjb *h) {
+  if (h->t_rowptr) return SL_OK;
+  const size_t M = size_t(h->m) * h->m, N = size_t(h->n) * h->n;
+  const size_t nnz = M * size_t(h->ft.tmax);  // every tap of every row at most once
+  AL(h->t_rowptr, M + 1);
+  AL(h->t_cnt, M);
+  AL(h->t_scan, 2 * ((M + 1023) / 1024) + 2);
+  AL(h->t_col, nnz);
+  AL(h->t_v64, nnz);
+  AL(h->t_v32, nnz);
+  AL(h->t_d64, M);
+  AL(h->t_d32, M);
+  AL(h->mu, N);
+  AL(h->lam, N);
+  AL(h->d_dtheta, kMaxParams);
+  AL(h->d_dpart, size_t(kMaxParams) * kRedBlocks);
+  for (int l = 1; l < h->L; ++l) {
+    CoarseBuf &c = h->cl[l];
+    const size_t cnt = size_t(c.win) * c.m * c.m;
+    if (h->o.precision == 0) AL(c.WT64, cnt);
+    else AL(c.WT32, cnt);
+  }
+  return SL_OK;
+}
+
+// Transposed operators of the current policy and step size (after build_hierarchy).
+sl_status build_transposed(sl_hjb *h, double dt, cudaStream_t s) {
+  launch_csrT_build(h->tab, h->d_off, h->policy, dt, h->t_cnt, h->t_scan, h->t_rowptr, h->t_col,
+                    h->t_v64, h->t_v32, h->t_d64, h->t_d32, s);
+  for (int l = 1; l < h->L; ++l) {
+    CoarseBuf &c = h->cl[l];
+    if (h->o.precision == 0) launch_denseT_build<double>(lev_view<double>(h, l), c.cdense64, c.WT64, s);
+    else launch_denseT_build<float>(lev_view<float>(h, l), c.cdense32, c.WT32, s);
+  }
+  CK(cudaGetLastError());
+  return SL_OK;
+}
+
+size_t rec_checkpoints(int N, int k) { return size_t(N / k) + 1 + (N % k ? 1 : 0); }
+
+// U^s of the recorded march, if stored (nullptr inside a segment).
+double *rec_stored(sl_hjb *h, int s) {
+  const size_t NNf = size_t(h->n) * h->n;
+  if (s % h->rec_k == 0) return h->rec_U + size_t(s / h->rec_k) * NNf;
+  if (s == h->rec_N) return h->rec_U + (rec_checkpoints(h->rec_N, h->rec_k) - 1) * NNf;
+  return nullptr;
+}
+
+// Re-solves steps base+1 .. top-1 of segment c at their recorded policies into rec_seg.
+sl_status recompute_segment(sl_hjb *h, int c, sl_stats *st, cudaStream_t s) {
+  const size_t NNf = size_t(h->n) * h->n, M = size_t(h->m) * h->m;
+  const int base = c * h->rec_k, top = std::min(base + h->rec_k, h->rec_N);
+  const double dt = h->rec_dt;
+  for (int j = base + 1; j < top; ++j) {
+    const double *prev = (j - 1 == base) ? rec_stored(h, base) : h->rec_seg + size_t(j - 2 - base) * NNf;
+    CK(cudaMemcpyAsync(h->Uprev, prev, NNf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->X, prev, NNf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->policy, h->rec_pol + size_t(j - 1) * M, M, cudaMemcpyDeviceToDevice, s));
+    sl_status r = coef(h, h->rec_t0 + j * dt, h->X, s);
+    if (r != SL_OK) return r;
+    r = build_hierarchy(h, dt, s);
+    if (r != SL_OK) return r;
+    r = linear_solve(h, dt, st, s);
+    if (r != SL_OK) return r;
+    CK(cudaMemcpyAsync(h->rec_seg + size_t(j - 1 - base) * NNf, h->X, NNf * sizeof(double),
+                       cudaMemcpyDeviceToDevice, s));
+  }
+  return SL_OK;
+}
+
+sl_status upload_dtables(sl_hjb *h, int np, const double *dsigma, DTabView *dv) {
+  const int E = h->K * h->ft.Q * h->ft.Q;
+  const size_t per = size_t(h->K) * 2 * h->P;
+  std::vector<FineDTabHost> tabs;
+  int stride = 1;
+  for (int p = 0; p < np; ++p) {
+    tabs.push_back(build_fine_dtables(h->ft, h->h, h->P, h->sigma.data(), dsigma + p * per));
+    stride = std::max(stride, tabs.back().stride);
+  }
+  std::vector<int32_t> lin(size_t(np) * E * stride, 0);
+  std::vector<double> dw(lin.size(), 0.0), dW(size_t(np) * E, 0.0);
+  std::vector<uint8_t> nt(size_t(np) * E, 0);
+  for (int p = 0; p < np; ++p)
+    for (int e = 0; e < E; ++e) {
+      const FineDTabHost &d = tabs[p];
+      const size_t pe = size_t(p) * E + e;
+      nt[pe] = d.nt[e];
+      dW[pe] = d.dW[e];
+      for (int t = 0; t < d.nt[e]; ++t) {
+        const size_t src = size_t(e) * d.stride + t;
+        lin[pe * stride + t] = d.dy[src] * h->n + d.dx[src];
+        dw[pe * stride + t] = d.dw[src];
+      }
+    }
+  sl_status r = dgrow(h, &h->dt_lin, &h->dt_cap[0], lin.size());
+  if (r == SL_OK) r = dgrow(h, &h->dt_dw, &h->dt_cap[1], dw.size());
+  if (r == SL_OK) r = dgrow(h, &h->dt_nt, &h->dt_cap[2], nt.size());
+  if (r == SL_OK) r = dgrow(h, &h->dt_dW, &h->dt_cap[3], dW.size());
+  if (r != SL_OK) return r;
+  CK(cudaMemcpy(h->dt_lin, lin.data(), lin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->dt_dw, dw.data(), dw.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->dt_nt, nt.data(), nt.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->dt_dW, dW.data(), dW.size() * sizeof(double), cudaMemcpyHostToDevice));
+  dv->np = np;
+  dv->E = E;
+  dv->stride = stride;
+  dv->lin = h->dt_lin;
+  dv->dw = h->dt_dw;
+  dv->nt = h->dt_nt;
+  dv->dW = h->dt_dW;
+  return SL_OK;
 }
 
 }  // namespace
@@ -839,6 +1035,8 @@ void sl_hjb_destroy(sl_hjb *h) {
   cudaDeviceSynchronize();
   for (auto &g : h->graph)
     if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto &g : h->graphT)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void *p : h->allocs) cudaFree(p);
   if (h->hS) cudaFreeHost(h->hS);
@@ -884,6 +1082,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   }
   h->cvec.assign(c->K, 0.0);
   if (c->c) h->cvec.assign(c->c, c->c + c->K);
+  h->sigma.assign(c->sigma, c->sigma + size_t(c->K) * 2 * c->P);
   h->phimax.assign(h->nf, 0.0);
   for (int k = 0; k < h->K; ++k)
     for (int mm = 0; mm < h->nf; ++mm)
@@ -1165,6 +1364,99 @@ sl_status sl_hjb_linear_solve(sl_hjb *h, const double *u_prev, double *x_ext, do
   CK(cudaMemcpyAsync(x_ext, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   return r;
+}
+
+sl_status sl_hjb_solve_record(sl_hjb *h, double *u, double t0, double T, int n_steps, int ckpt_every,
+                              sl_stats *st, void *stream) {
+  if (!h || !u || n_steps < 1 || !(T > 0) || ckpt_every < 1) return SL_EINVAL;
+  if (st) std::memset(st, 0, sizeof(*st));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->rec_valid = false;
+  const size_t M = size_t(h->m) * h->m, NNf = size_t(h->n) * h->n;
+  const int k = std::min(ckpt_every, n_steps);
+  const double dt = T / n_steps;
+  sl_status r = dgrow(h, &h->rec_pol, &h->rec_pol_cap, size_t(n_steps) * M);
+  if (r == SL_OK) r = dgrow(h, &h->rec_U, &h->rec_U_cap, rec_checkpoints(n_steps, k) * NNf);
+  if (r == SL_OK && k > 1) r = dgrow(h, &h->rec_seg, &h->rec_seg_cap, size_t(k - 1) * NNf);
+  if (r != SL_OK) return r;
+  h->rec_N = n_steps;
+  h->rec_k = k;
+  CK(cudaMemcpyAsync(h->rec_U, u, NNf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  for (int i = 1; i <= n_steps; ++i) {
+    h->rec_slot = h->rec_pol + size_t(i - 1) * M;
+    r = step_impl(h, u, t0 + i * dt, dt, nullptr, st, s);
+    h->rec_slot = nullptr;
+    if (r != SL_OK) return r;
+    double *dst = rec_stored(h, i);
+    if (dst) CK(cudaMemcpyAsync(dst, u, NNf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  h->rec_t0 = t0;
+  h->rec_dt = dt;
+  h->rec_valid = true;
+  CK(cudaStreamSynchronize(s));
+  return SL_OK;
+}
+
+sl_status sl_hjb_adjoint(sl_hjb *h, const double *w, double *dJ_dg, double *dJ_dG, int nparam,
+                         const double *dsigma, double *dJ_dtheta, sl_stats *st, void *stream) {
+  if (!h || !w || !dJ_dg || nparam < 0 || nparam > kMaxParams) return SL_EINVAL;
+  if (nparam > 0 && (!dsigma || !dJ_dtheta)) return SL_EINVAL;
+  if (!h->rec_valid) return fail(h, SL_EINVAL, "sl_hjb_adjoint needs a preceding sl_hjb_solve_record");
+  if (st) std::memset(st, 0, sizeof(*st));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  sl_status r = ensure_adjoint_buffers(h);
+  if (r != SL_OK) return r;
+  DTabView dv{};
+  if (nparam > 0) {
+    r = upload_dtables(h, nparam, dsigma, &dv);
+    if (r != SL_OK) return r;
+  }
+  const size_t M = size_t(h->m) * h->m, NNf = size_t(h->n) * h->n;
+  const double dt = h->rec_dt;
+  CK(cudaMemsetAsync(h->d_dtheta, 0, kMaxParams * sizeof(double), s));
+  if (dJ_dG) CK(cudaMemsetAsync(dJ_dG, 0, size_t(h->nf) * h->nq * NNf * sizeof(double), s));
+  launch_interior_copy(h->n, w, h->lam, s);  // lambda_N = dJ/dU^N on the unknowns
+  int seg = -1;
+  for (int sn = h->rec_N; sn >= 1; --sn) {
+    const double t = h->rec_t0 + sn * dt;
+    const double *U = rec_stored(h, sn);
+    if (!U) {
+      const int c = sn / h->rec_k;
+      if (c != seg) {
+        r = recompute_segment(h, c, st, s);
+        if (r != SL_OK) return r;
+        seg = c;
+      }
+      U = h->rec_seg + size_t(sn - 1 - c * h->rec_k) * NNf;
+    }
+    CK(cudaMemcpyAsync(h->policy, h->rec_pol + size_t(sn - 1) * M, M, cudaMemcpyDeviceToDevice, s));
+    h->have_policy = true;
+    r = coef(h, t, h->X, s);  // tau_q(t_n) for the source gradient
+    if (r != SL_OK) return r;
+    r = build_hierarchy(h, dt, s);
+    if (r == SL_OK) r = build_transposed(h, dt, s);
+    if (r != SL_OK) return r;
+    // A_n^T mu_n = lambda_n, started from lambda_n (A_n = I + O(dt))
+    CK(cudaMemcpyAsync(h->mu, h->lam, NNf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    h->transposed = true;
+    r = linear_solve(h, dt, st, s);
+    h->transposed = false;
+    if (r != SL_OK) return r;
+    if (st) st->steps += 1;
+    if (dJ_dG) launch_adj_dG(h->n, h->nf, h->nq, h->policy, h->d_phi, h->d_tau, dt, h->mu, dJ_dG, s);
+    if (nparam > 0) launch_adj_dtheta(h->tab, dv, h->policy, h->mu, U, dt, h->d_dpart, h->d_dtheta, s);
+    // lambda_{n-1} = mu_n (U^{n-1} enters step n as -I)
+    CK(cudaMemcpyAsync(h->lam, h->mu, NNf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(dJ_dg, h->lam, NNf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (nparam > 0)
+    CK(cudaMemcpyAsync(dJ_dtheta, h->d_dtheta, nparam * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // the handle's policy and hierarchy now belong to step 1; the next march starts afresh
+  h->hier_valid = false;
+  h->have_prev2 = false;
+  return SL_OK;
 }
 
 sl_status sl_hjb_level_info(const sl_hjb *h, int level, int *n, long long *explicit_rows, long long *nnz) {

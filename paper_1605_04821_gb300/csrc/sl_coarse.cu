@@ -538,21 +538,22 @@ template void launch_coarsest_setup<float>(int, const FineTab &, const uint8_t *
 
 template <typename T>
 __global__ void k_coarsest_apply(const T *__restrict__ Ainv, int n, const T *__restrict__ b,
-                                 T *__restrict__ x) {
+                                 T *__restrict__ x, int trans) {
   const int m = n - 2, N = m * m;
+  const size_t rs = trans ? 1 : size_t(N), cs = trans ? size_t(N) : 1;
   for (int r = threadIdx.x; r < N; r += blockDim.x) {
     T acc = T(0);
-    for (int c = 0; c < N; ++c) acc = fma(Ainv[size_t(r) * N + c], b[(1 + c / m) * n + 1 + c % m], acc);
+    for (int c = 0; c < N; ++c) acc = fma(Ainv[r * rs + c * cs], b[(1 + c / m) * n + 1 + c % m], acc);
     x[(1 + r / m) * n + 1 + r % m] = acc;
   }
 }
 
 template <typename T>
-void launch_coarsest_apply(const T *Ainv, int n, const T *b, T *x, cudaStream_t s) {
+void launch_coarsest_apply(const T *Ainv, int n, const T *b, T *x, cudaStream_t s, int trans) {
   note_launch();
-  k_coarsest_apply<T><<<1, 256, 0, s>>>(Ainv, n, b, x);
+  k_coarsest_apply<T><<<1, 256, 0, s>>>(Ainv, n, b, x, trans);
 }
-template void launch_coarsest_apply<double>(const double *, int, const double *, double *, cudaStream_t);
-template void launch_coarsest_apply<float>(const float *, int, const float *, float *, cudaStream_t);
+template void launch_coarsest_apply<double>(const double *, int, const double *, double *, cudaStream_t, int);
+template void launch_coarsest_apply<float>(const float *, int, const float *, float *, cudaStream_t, int);
 
 }  // namespace sl

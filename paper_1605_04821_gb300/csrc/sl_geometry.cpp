@@ -157,6 +157,115 @@ FineTabHost build_fine_tables(int n, double h, int K, int P, const double *sigma
   return t;
 }
 
+// ---------------------------------------------------------------------- derivative tables
+// Forward-mode differentiation of the construction above: every quantity carries its value
+// and its derivative in theta.  Branches (which side truncates, which cell an endpoint falls
+// in) follow the values, so the result is the derivative of the piecewise-smooth map on the
+// piece the current sigma lies in.  A component placed exactly on the boundary by the
+// truncation has derivative zero.
+namespace {
+
+struct Dual {
+  double v, d;
+};
+Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+Dual operator/(Dual a, Dual b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
+Dual cst(double v) { return {v, 0.0}; }
+
+struct DEndpoint {
+  Dual mu, z1, z2;
+};
+
+DEndpoint dtruncate_endpoint(double i1, double i2, Dual s1, Dual s2, int n) {
+  const double top = double(n - 1);
+  const double inf = std::numeric_limits<double>::infinity();
+  Dual b1 = cst(inf), b2 = cst(inf);
+  if (s1.v > 0) b1 = cst(top - i1) / s1; else if (s1.v < 0) b1 = cst(0.0 - i1) / s1;
+  if (s2.v > 0) b2 = cst(top - i2) / s2; else if (s2.v < 0) b2 = cst(0.0 - i2) / s2;
+  const Dual bmin = (b2.v < b1.v) ? b2 : b1;
+  DEndpoint e;
+  e.mu = (bmin.v < 1.0) ? bmin : cst(1.0);
+  e.z1 = cst(i1) + e.mu * s1;
+  e.z2 = cst(i2) + e.mu * s2;
+  if (e.mu.v < 1.0) {
+    if (b1.v == e.mu.v) e.z1 = cst(s1.v > 0 ? top : 0.0);
+    if (b2.v == e.mu.v) e.z2 = cst(s2.v > 0 ? top : 0.0);
+  }
+  return e;
+}
+
+using DTapMap = std::map<std::pair<int, int>, Dual>;
+
+void dadd_bilinear(DTapMap &taps, int i1, int i2, Dual z1, Dual z2, int n, Dual scale) {
+  const double c1 = std::min(std::max(std::floor(z1.v), 0.0), double(n - 2));
+  const double c2 = std::min(std::max(std::floor(z2.v), 0.0), double(n - 2));
+  const Dual t1 = z1 - cst(c1), t2 = z2 - cst(c2);
+  const int a1 = int(c1) - i1, a2 = int(c2) - i2;
+  const Dual one = cst(1.0);
+  const Dual wts[4] = {(one - t1) * (one - t2), t1 * (one - t2), (one - t1) * t2, t1 * t2};
+  const int o1[4] = {0, 1, 0, 1}, o2[4] = {0, 0, 1, 1};
+  for (int c = 0; c < 4; ++c) {
+    const Dual w = wts[c] * scale;
+    Dual &acc = taps.emplace(std::make_pair(a2 + o2[c], a1 + o1[c]), cst(0.0)).first->second;
+    acc = acc + w;
+  }
+}
+
+}  // namespace
+
+FineDTabHost build_fine_dtables(const FineTabHost &t, double h, int P, const double *sigma,
+                                const double *dsig) {
+  const int n = t.n, K = t.K, E = K * t.Q * t.Q;
+  const double sqh = std::sqrt(h);
+  std::vector<std::vector<std::pair<std::pair<int, int>, double>>> rows(E);
+  std::vector<double> dW(E, 0.0);
+  int maxnt = 1;
+  for (int k = 0; k < K; ++k)
+    for (int q2 = 1; q2 < t.Q; ++q2)
+      for (int q1 = 1; q1 < t.Q; ++q1) {
+        const int i1 = class_rep(q1, n, t.B), i2 = class_rep(q2, n, t.B);
+        if (i1 < 1 || i1 > n - 2 || i2 < 1 || i2 > n - 2) continue;
+        DTapMap taps;
+        Dual W = cst(0.0);
+        for (int p = 0; p < P; ++p) {
+          const size_t r1 = size_t(k * 2 + 0) * P + p, r2 = size_t(k * 2 + 1) * P + p;
+          const Dual s1 = {sigma[r1] / sqh, dsig[r1] / sqh};
+          const Dual s2 = {sigma[r2] / sqh, dsig[r2] / sqh};
+          const DEndpoint ep = dtruncate_endpoint(i1, i2, s1, s2, n);
+          const DEndpoint em = dtruncate_endpoint(i1, i2, cst(0.0) - s1, cst(0.0) - s2, n);
+          const Dual A = cst(2.0) / (ep.mu * ep.mu + ep.mu * em.mu);
+          const Dual Bw = cst(2.0) / (em.mu * em.mu + em.mu * ep.mu);
+          dadd_bilinear(taps, i1, i2, ep.z1, ep.z2, n, A / cst(2.0 * h));
+          dadd_bilinear(taps, i1, i2, em.z1, em.z2, n, Bw / cst(2.0 * h));
+          W = W + (A + Bw) / cst(2.0 * h);
+        }
+        // the drift taps do not depend on sigma and have zero derivative
+        const int e = t.entry(k, q1, q2);
+        for (const auto &kv : taps)
+          if (kv.second.d != 0.0) rows[e].push_back({kv.first, kv.second.d});
+        dW[e] = W.d;
+        maxnt = std::max(maxnt, int(rows[e].size()));
+      }
+  FineDTabHost d;
+  d.stride = (maxnt + 3) / 4 * 4;
+  d.dx.assign(size_t(E) * d.stride, 0);
+  d.dy.assign(size_t(E) * d.stride, 0);
+  d.dw.assign(size_t(E) * d.stride, 0.0);
+  d.nt.assign(E, 0);
+  d.dW = dW;
+  for (int e = 0; e < E; ++e) {
+    d.nt[e] = uint8_t(rows[e].size());
+    for (size_t s = 0; s < rows[e].size(); ++s) {
+      d.dy[size_t(e) * d.stride + s] = rows[e][s].first.first;
+      d.dx[size_t(e) * d.stride + s] = rows[e][s].first.second;
+      d.dw[size_t(e) * d.stride + s] = rows[e][s].second;
+    }
+  }
+  return d;
+}
+
 std::vector<double> fine_interior_window(const FineTabHost &t, int k, double dt) {
   const int R = t.R0, Wd = 2 * R + 1;
   std::vector<double> win(size_t(Wd) * Wd, 0.0);

@@ -24,6 +24,21 @@ struct FineTabHost {
 FineTabHost build_fine_tables(int n, double h, int K, int P, const double *sigma,
                               const double *b, const double *c);
 
+// Derivative of every fine table entry with respect to a scalar parameter theta of the
+// diffusion coefficients (dsig = d sigma / d theta, laid out like sigma): taps (dy, dx, dw) of
+// d(L^k)/d theta with dw = d w_t / d theta, and dW = d W / d theta, so that
+//   (d L^k / d theta x)_j = sum_t dw_t x_{j + o_t} - dW x_j.
+// Entry numbering is that of FineTabHost (same B and Q); `stride` is the tap stride.
+struct FineDTabHost {
+  int stride = 0;
+  std::vector<int32_t> dx, dy;  // [e*stride + t]
+  std::vector<double> dw;       // [e*stride + t]
+  std::vector<uint8_t> nt;      // [e]
+  std::vector<double> dW;       // [e]
+};
+FineDTabHost build_fine_dtables(const FineTabHost &t, double h, int P, const double *sigma,
+                                const double *dsig);
+
 // Dense (2R+1)^2 window of the level-l class-k Galerkin stencil, built from the level-(l-1)
 // class-k row `prev` (dense window of reach Rprev; for level 1 the fine interior row).
 std::vector<double> rap_class_window(const std::vector<double> &prev, int Rprev, int R);

@@ -87,8 +87,50 @@ template <typename T>
 void launch_coarsest_setup(int level, const FineTab &tab, const uint8_t *policy, T dt,
                            const CoarseLev<T> &L, const int32_t *coff, double *work, T *Ainv,
                            cudaStream_t s);
+// x = A^{-1} b, or x = A^{-T} b when trans != 0.
 template <typename T>
-void launch_coarsest_apply(const T *Ainv, int n, const T *b, T *x, cudaStream_t s);
+void launch_coarsest_apply(const T *Ainv, int n, const T *b, T *x, cudaStream_t s, int trans = 0);
+
+// ------------------------------------------------------------------ adjoint (transposed solves)
+// Explicit A^T of the fine level: row J (interior index of column j of A) lists the sources i
+// with A[i, j] != 0, i != j, sorted by i; the diagonal is stored apart.
+template <typename T>
+struct CsrTView {
+  int n, m;
+  const int32_t *rowptr;  // [m*m + 1]
+  const int32_t *col;     // [nnz] full-grid index of the source row i
+  const T *v;             // [nnz] A[i, j]
+  const T *d;             // [m*m] A[j, j]
+};
+// cnt: m*m ints, scan_scratch: 2 * ceil(m*m / 1024) ints; col/v64/v32 sized for every tap.
+void launch_csrT_build(const FineTab &tab, const int32_t *off, const uint8_t *policy, double dt,
+                       int *cnt, int *scan_scratch, int32_t *rowptr, int32_t *col, double *v64,
+                       float *v32, double *d64, float *d32, cudaStream_t s);
+template <typename T>
+void launch_fineT_op(int op, const CsrTView<T> &A, T omega, const T *x, const T *b, T *y, cudaStream_t s);
+// Dense windows of the rows of A_l^T (level l >= 1) from the forward level; cdense holds the
+// class windows [k * win + e].
+template <typename T>
+void launch_denseT_build(const CoarseLev<T> &L, const T *cdense, T *WT, cudaStream_t s);
+template <typename T>
+void launch_denseT_op(int op, int n, int R, const T *WT, T omega, const T *x, const T *b, T *y,
+                      cudaStream_t s);
+
+// Derivative tables of the fine stencil for np parameters: entry (p, e) at p*E + e.
+constexpr int kMaxParams = 8;
+struct DTabView {
+  int np, E, stride;
+  const int32_t *lin;   // [(p*E + e)*stride + t] dy*n + dx
+  const double *dw;     // [(p*E + e)*stride + t]
+  const uint8_t *nt;    // [p*E + e]
+  const double *dW;     // [p*E + e]
+};
+void launch_interior_copy(int n, const double *x, double *y, cudaStream_t s);
+void launch_adj_dG(int n, int nf, int nq, const uint8_t *policy, const double *phi, const double *tau,
+                   double dt, const double *mu, double *dG, cudaStream_t s);
+// partials: kMaxParams * kRedBlocks doubles; out[p] += dt * mu^T (dL/dtheta_p U).
+void launch_adj_dtheta(const FineTab &tab, const DTabView &d, const uint8_t *policy, const double *mu,
+                       const double *U, double dt, double *partials, double *out, cudaStream_t s);
 
 // vectors and reductions
 template <typename T>

@@ -20,19 +20,6 @@ from oracle import adjoint as adj
 from oracle import lisl
 
 
-def _with_boundary(p):
-    """The same problem with a non-zero, time-independent Dirichlet boundary."""
-    q = copy.copy(p)
-    x = np.linspace(p.lo, p.hi, p.n)
-    X1, X2 = np.meshgrid(x, x, indexing="xy")
-    psi = 0.3 + 0.1 * X1 - 0.05 * X2 * X1
-    q.psi_fn = lambda t, psi=psi: psi.copy()
-    g = p.g.copy()
-    g[0, :], g[-1, :], g[:, 0], g[:, -1] = psi[0, :], psi[-1, :], psi[:, 0], psi[:, -1]
-    q.g = g
-    return q
-
-
 def _weights(n, seed):
     rng = np.random.default_rng(seed)
     w = np.zeros((n, n))
@@ -40,22 +27,12 @@ def _weights(n, seed):
     return w
 
 
-def _sigma_dirs(p):
-    """d sigma / d theta for theta = s1 (first column, first row) and theta = s2 (second row)."""
-    d1 = np.zeros_like(p.sigma)
-    d1[:, 0, 0] = 1.0
-    d2 = np.zeros_like(p.sigma)
-    d2[:, 1, 0] = p.rho
-    d2[:, 1, 1] = np.sqrt(1.0 - p.rho ** 2)
-    return [d1, d2]
-
-
 def _J(p, w, **kw):
     return adj.objective(p, w, **kw)
 
 
 def test_single_control_linear_in_g():
-    p = _with_boundary(W.manufactured(17, 1, 0.4, 0.4, 0.9, 0.7, T=0.25, n_steps=5))
+    p = W.with_dirichlet(W.manufactured(17, 1, 0.4, 0.4, 0.9, 0.7, T=0.25, n_steps=5))
     w = _weights(17, 1)
     r = adj.adjoint(p, w)
     rng = np.random.default_rng(3)
@@ -87,9 +64,9 @@ def test_single_control_affine_in_source_tables():
 def test_sigma_gradient_matches_central_differences(s1, s2, bnd):
     p = W.manufactured(17, 5, -0.6, 0.6, s1, s2, T=0.25, n_steps=4)
     if bnd:
-        p = _with_boundary(p)
+        p = W.with_dirichlet(p)
     w = _weights(17, 5)
-    dirs = _sigma_dirs(p)
+    dirs = list(W.sigma_directions(p))
     r = adj.adjoint(p, w, dirs)
     eps = 1e-5
     for i, ds in enumerate(dirs):
@@ -103,7 +80,7 @@ def test_sigma_gradient_matches_central_differences(s1, s2, bnd):
         assert abs(fd - r.dJ_dtheta[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, r.dJ_dtheta[i])
 
 
-def test_g_and_source_gradients_match_central_differences_with_switching_policies():
+def test_g_and_source_gradients_match_central_differences_with_several_controls():
     p = W.manufactured(17, 5, -0.6, 0.6, 0.9, 0.7, T=0.25, n_steps=4)
     w = _weights(17, 6)
     r = adj.adjoint(p, w)
@@ -134,7 +111,7 @@ def test_policies_recorded_are_those_of_the_final_solves():
     dt = p.T / p.n_steps
     for s, pol in enumerate(r.policies, start=1):
         A, F = lisl.assemble(p, pol, U, s * dt, dt)
-        X = lisl.spla.spsolve(A.tocsc(), F) if hasattr(lisl, "spla") else np.linalg.solve(A.toarray(), F)
+        X = np.linalg.solve(A.toarray(), F)
         U2 = U.copy()
         U2[1:-1, 1:-1] = np.asarray(X).reshape(15, 15)
         U2[0, :], U2[-1, :], U2[:, 0], U2[:, -1] = 0.0, 0.0, 0.0, 0.0

@@ -25,6 +25,7 @@ Arrays of grid values have shape (n, n) and are indexed [i2, i1]: x1 runs along 
 """
 from __future__ import annotations
 
+import copy
 import dataclasses
 import math
 from typing import Callable, Optional
@@ -196,6 +197,50 @@ def scaled(n: int, K: int, n_steps: int, seed: Optional[int] = None, s=(0.3, 0.2
         s = tuple(rng.uniform(0.15, 0.4, size=2))
     return manufactured(n, K, rho_range[0], rho_range[1], float(s[0]), float(s[1]),
                         T=T, n_steps=n_steps)
+
+
+def with_dirichlet(p: Problem) -> Problem:
+    """The same problem with a non-zero, time-independent Dirichlet boundary
+    psi = 0.3 + 0.1 x1 - 0.05 x1 x2 (g takes psi on the boundary)."""
+    q = copy.copy(p)
+    x = np.linspace(p.lo, p.hi, p.n)
+    X1, X2 = np.meshgrid(x, x, indexing="xy")
+    psi = 0.3 + 0.1 * X1 - 0.05 * X2 * X1
+    q.psi_fn = lambda t, psi=psi: psi.copy()
+    g = p.g.copy()
+    g[0, :], g[-1, :], g[:, 0], g[:, -1] = psi[0, :], psi[-1, :], psi[:, 0], psi[:, -1]
+    q.g = g
+    return q
+
+
+def gaussian_bump(n: int, lo: float, hi: float, seed: int = 0) -> np.ndarray:
+    """Weights of J = sum_x w(x) U(T, x): exp(-|x - c|^2 / (2 r^2)) with centre c ~ U[-1, 1]^2
+    and width r ~ U[0.2, 0.5] (seeded), zero on the boundary."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1.0, 1.0, size=2)
+    r = rng.uniform(0.2, 0.5)
+    x = np.linspace(lo, hi, n)
+    X1, X2 = np.meshgrid(x, x, indexing="xy")
+    w = np.exp(-((X1 - c[0]) ** 2 + (X2 - c[1]) ** 2) / (2.0 * r * r))
+    w[0, :] = w[-1, :] = w[:, 0] = w[:, -1] = 0.0
+    return w
+
+
+def sigma_directions(p: Problem) -> np.ndarray:
+    """d sigma / d theta for theta = (s1, s2) of the correlation family
+    sigma^rho = [[s1, 0], [s2 rho, s2 sqrt(1 - rho^2)]]: shape (2, K, 2, 2)."""
+    d = np.zeros((2,) + p.sigma.shape)
+    d[0, :, 0, 0] = 1.0
+    d[1, :, 1, 0] = p.rho
+    d[1, :, 1, 1] = np.sqrt(1.0 - p.rho ** 2)
+    return d
+
+
+def adjoint_1025(seed: int = 0):
+    """1025 x 1025 grid, 33 controls rho in [-0.9, 0.9], s1 = 0.3, s2 = 0.2, T = 1, 64 steps,
+    and Gaussian-bump weights w (centre and width drawn from `seed`).  Returns (problem, w)."""
+    p = manufactured(1025, 33, -0.9, 0.9, 0.3, 0.2, T=1.0, n_steps=64)
+    return p, gaussian_bump(p.n, p.lo, p.hi, seed)
 
 
 def unit_circle_controls(n_alpha: int) -> np.ndarray:
