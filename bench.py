@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--opt", action="append", default=[],
                    help="solver option override key=value (sl_opts field), repeatable")
     return p.parse_args()
@@ -356,6 +357,11 @@ def run_ours(args):
             err = float((u_cmp - u64).abs().max() / u64.abs().max())
         del s64
 
+    # ---- discrete adjoint: gradients of J = sum w U(T) on 1025^2, 33 controls, 64 steps
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_record(slp, W, dev, stream, extra)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_record()
@@ -383,10 +389,54 @@ def run_ours(args):
             "clocks": clocks,
             "fp64": fp64,
             "mixed_vs_fp64_rel_err": err,
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def adjoint_record(slp, W, dev, stream, extra):
+    """Forward march with recording, then the backward pass, each timed with CUDA events."""
+    import torch
+    pa, wa = W.adjoint_1025(seed=0)
+    dirs = W.sigma_directions(pa)
+    na, nt = pa.n, pa.n_steps
+    dta = pa.T / nt
+    wd = torch.as_tensor(wa, dtype=torch.float64, device=dev)
+    out = {"workload": f"uncertain-correlation HJB, {na}x{na} grid, 33 controls rho in "
+                       f"[-0.9,0.9], s1=0.3 s2=0.2, {nt} steps of 1/{nt}; J = sum w U(T) with a "
+                       "seeded Gaussian bump w; every U^n kept (ckpt_every 1)",
+           "unit": UNIT}
+    for prec, key in ((1, "mixed"), (0, "fp64")):
+        kw = dict(precision=prec, argmin_screen=prec)
+        kw.update(extra)
+        sa = slp.solver_from_problem(pa, device=dev, **kw)
+        ua = torch.as_tensor(pa.g, dtype=torch.float64, device=dev)
+        dg = torch.zeros_like(ua)
+        sa.solve_record(ua.clone(), 0.0, 3 * dta, 3, 1)   # warm-up: buffers and graphs
+        sa.adjoint(wd, dg, None, dirs)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        l0 = slp.launch_count()
+        ev[0].record(stream)
+        stf = sa.solve_record(ua, 0.0, pa.T, nt, 1)
+        ev[1].record(stream)
+        dth, stb = sa.adjoint(wd, dg, None, dirs)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        out[key] = {"value": na * na * nt / (bwd / 1e3), "backward_ms": bwd,
+                    "backward_ms_per_step": bwd / nt, "forward_record_ms": fwd,
+                    "forward_ms_per_step": fwd / nt, "backward_krylov_iters": stb["krylov_iters"],
+                    "forward_krylov_iters": stf["krylov_iters"],
+                    "gpu_launches": slp.launch_count() - l0,
+                    "dJ_dtheta": [float(v) for v in dth],
+                    "J": float((wd * ua).sum())}
+        del sa
+        torch.cuda.empty_cache()
+    out["value"] = out["mixed"]["value"]
+    return out
 
 
 def make_levels(n):

@@ -320,6 +320,30 @@ def control_values(prob, X_full: np.ndarray, t: float, f_full: Optional[np.ndarr
     return V
 
 
+def control_values_at(prob, X_full: np.ndarray, t: float, i1: np.ndarray, i2: np.ndarray) -> np.ndarray:
+    """v_k(j) of control_values at the interior nodes (i1, i2) only, shape (K, len(i1)).
+
+    The same formulas restricted to the listed rows; the source is evaluated at those nodes
+    only (f^k = sum_m phi[k, m] sum_q tau_q(t) G[m, q]), so grids too large for the full
+    (K, n, n) source table can be sampled.
+    """
+    n = prob.n
+    i1 = np.asarray(i1, dtype=np.float64)
+    i2 = np.asarray(i2, dtype=np.float64)
+    flat = (i2.astype(np.int64) * n + i1.astype(np.int64))
+    if prob.f_fn is not None:
+        f_at = prob.f_fn(t).reshape(prob.K, -1)[:, flat]
+    else:
+        Fm = np.einsum("q,mqs->ms", prob.tau(t), prob.G.reshape(prob.G.shape[0], prob.G.shape[1], -1)[:, :, flat])
+        f_at = prob.phi @ Fm
+    V = np.empty((prob.K, len(flat)))
+    x = X_full.ravel()
+    for k in range(prob.K):
+        tp = control_taps(prob, k, i1, i2)
+        V[k] = apply_lhat(tp, X_full, flat) + control_c(prob, k) * x[flat] + f_at[k]
+    return V
+
+
 def improve(V: np.ndarray) -> np.ndarray:
     """Row-wise linear search: lowest k with v_k <= v_min + 1e-12 max(1, |v_min|)."""
     vmin = V.min(axis=0)

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_csrT_fill(FineTab tab, const in
                                                             const uint8_t *__restrict__ policy, double dt,
                                                             const int32_t *__restrict__ rowptr,
                                                             int *__restrict__ fillc, int32_t *__restrict__ col,
-                                                            double *__restrict__ v64, float *__restrict__ v32,
+                                                            double *__restrict__ vtmp,
                                                             double *__restrict__ d64, float *__restrict__ d32) {
   const int m = tab.m, n = tab.n;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,40 +125,65 @@ __global__ void __launch_bounds__(kAdjThreads) k_csrT_fill(FineTab tab, const in
     if ((dx | dy) == 0 || j1 < 1 || j1 > m || j2 < 1 || j2 > m) continue;
     const int J = (j2 - 1) * m + (j1 - 1);
     const int pos = rowptr[J] + atomicAdd(fillc + J, 1);
-    const double v = -dt * tab.w64[ix];
     col[pos] = i2 * n + i1;
-    v64[pos] = v;
-    v32[pos] = float(v);
+    vtmp[pos] = -dt * tab.w64[ix];
   }
 }
 
-// Orders every row by source index (insertion sort; rows hold a few dozen entries).
-__global__ void __launch_bounds__(kAdjThreads) k_csrT_sort(int M, const int32_t *__restrict__ rowptr,
-                                                            int32_t *__restrict__ col, double *__restrict__ v64,
-                                                            float *__restrict__ v32) {
+// Orders every row by source index.  A row holds a few dozen entries whose sources lie
+// within the stencil reach of j, so each entry is keyed by (i - j + kOff) << 6 | slot in one
+// int; each thread sorts its row's keys in a local array (insertion sort) and writes the
+// sorted columns and the permuted values (from the staging array vtmp) once.  A row longer
+// than the local array is sorted in place in global memory.
+constexpr int kSortMax = 64;
+
+__global__ void __launch_bounds__(kAdjThreads) k_csrT_sort(int M, int m, int n, int koff,
+                                                            const int32_t *__restrict__ rowptr,
+                                                            int32_t *__restrict__ col,
+                                                            const double *__restrict__ vtmp,
+                                                            double *__restrict__ v64, float *__restrict__ v32) {
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= M) return;
-  const int lo = rowptr[J], hi = rowptr[J + 1];
+  const int j = (1 + J / m) * n + 1 + J % m;
+  const int lo = rowptr[J], hi = rowptr[J + 1], len = hi - lo;
+  if (len <= kSortMax) {
+    int key[kSortMax];
+    for (int a = 0; a < len; ++a) {
+      const int ka = ((col[lo + a] - j + koff) << 6) | a;
+      int b = a - 1;
+      while (b >= 0 && key[b] > ka) {
+        key[b + 1] = key[b];
+        --b;
+      }
+      key[b + 1] = ka;
+    }
+    for (int a = 0; a < len; ++a) {
+      const double v = vtmp[lo + (key[a] & 63)];
+      col[lo + a] = j + (key[a] >> 6) - koff;
+      v64[lo + a] = v;
+      v32[lo + a] = float(v);
+    }
+    return;
+  }
+  for (int a = lo; a < hi; ++a) v64[a] = vtmp[a];
   for (int a = lo + 1; a < hi; ++a) {
     const int c = col[a];
     const double w = v64[a];
-    const float w32 = v32[a];
     int b = a - 1;
     while (b >= lo && col[b] > c) {
       col[b + 1] = col[b];
       v64[b + 1] = v64[b];
-      v32[b + 1] = v32[b];
       --b;
     }
     col[b + 1] = c;
     v64[b + 1] = w;
-    v32[b + 1] = w32;
   }
+  for (int a = lo; a < hi; ++a) v32[a] = float(v64[a]);
 }
 
-void launch_csrT_build(const FineTab &tab, const int32_t *off, const uint8_t *policy, double dt,
-                       int *cnt, int *scan_scratch, int32_t *rowptr, int32_t *col, double *v64,
-                       float *v32, double *d64, float *d32, cudaStream_t s) {
+void launch_csrT_build(const FineTab &tab, const int32_t *off, const uint8_t *policy, double dt, int R0,
+                       int *cnt, int *scan_scratch, int32_t *rowptr, int32_t *col, double *vtmp,
+                       double *v64, float *v32, double *d64, float *d32, cudaStream_t s) {
   const int M = tab.m * tab.m;
   const int g = (M + kAdjThreads - 1) / kAdjThreads;
   const int nchunks = (M + kScanChunk - 1) / kScanChunk;
@@ -169,8 +194,9 @@ void launch_csrT_build(const FineTab &tab, const int32_t *off, const uint8_t *po
   k_scan_chunk_offsets<<<1, kScanChunk, 0, s>>>(scan_scratch, nchunks, scan_scratch + nchunks);
   k_scan_apply<<<nchunks, kScanChunk, 0, s>>>(cnt, M, scan_scratch + nchunks, rowptr);
   cudaMemsetAsync(cnt, 0, size_t(M) * sizeof(int), s);
-  k_csrT_fill<<<g, kAdjThreads, 0, s>>>(tab, off, policy, dt, rowptr, cnt, col, v64, v32, d64, d32);
-  k_csrT_sort<<<g, kAdjThreads, 0, s>>>(M, rowptr, col, v64, v32);
+  k_csrT_fill<<<g, kAdjThreads, 0, s>>>(tab, off, policy, dt, rowptr, cnt, col, vtmp, d64, d32);
+  // sources i of row j satisfy |i - j| <= R0 (n + 1)
+  k_csrT_sort<<<g, kAdjThreads, 0, s>>>(M, tab.m, tab.n, R0 * (tab.n + 1), rowptr, col, vtmp, v64, v32);
 }
 
 // ----------------------------------------------------------------------------- transposed ops

@@ -111,7 +111,7 @@ struct sl_hjb {
   // adjoint: fine A^T (CSR), gradient tables and the recorded forward march
   int32_t *t_rowptr = nullptr, *t_col = nullptr;
   int *t_cnt = nullptr, *t_scan = nullptr;
-  double *t_v64 = nullptr, *t_d64 = nullptr;
+  double *t_v64 = nullptr, *t_d64 = nullptr, *t_vtmp = nullptr;
   float *t_v32 = nullptr, *t_d32 = nullptr;
   double *mu = nullptr, *lam = nullptr;        // full grid, zero boundary
   double *d_dtheta = nullptr, *d_dpart = nullptr;
@@ -787,6 +787,8 @@ sl_status dgrow(sl_hjb *h, T **p, size_t *cap, size_t count) {
 
 sl_status ensure_adjoint_buffers(sl_hjb *h) {
   if (h->t_rowptr) return SL_OK;
+  if (double(h->ft.R0) * (h->n + 1) >= double(1 << 24))  // packed sort keys of the fine A^T
+    return fail(h, SL_EINVAL, "stencil reach too large for the transposed fine operator");
   const size_t M = size_t(h->m) * h->m, N = size_t(h->n) * h->n;
   const size_t nnz = M * size_t(h->ft.tmax);  // every tap of every row at most once
   AL(h->t_rowptr, M + 1);
@@ -794,6 +796,7 @@ sl_status ensure_adjoint_buffers(sl_hjb *h) {
   AL(h->t_scan, 2 * ((M + 1023) / 1024) + 2);
   AL(h->t_col, nnz);
   AL(h->t_v64, nnz);
+  AL(h->t_vtmp, nnz);
   AL(h->t_v32, nnz);
   AL(h->t_d64, M);
   AL(h->t_d32, M);
@@ -812,8 +815,8 @@ sl_status ensure_adjoint_buffers(sl_hjb *h) {
 
 // Transposed operators of the current policy and step size (after build_hierarchy).
 sl_status build_transposed(sl_hjb *h, double dt, cudaStream_t s) {
-  launch_csrT_build(h->tab, h->d_off, h->policy, dt, h->t_cnt, h->t_scan, h->t_rowptr, h->t_col,
-                    h->t_v64, h->t_v32, h->t_d64, h->t_d32, s);
+  launch_csrT_build(h->tab, h->d_off, h->policy, dt, h->ft.R0, h->t_cnt, h->t_scan, h->t_rowptr,
+                    h->t_col, h->t_vtmp, h->t_v64, h->t_v32, h->t_d64, h->t_d32, s);
   for (int l = 1; l < h->L; ++l) {
     CoarseBuf &c = h->cl[l];
     if (h->o.precision == 0) launch_denseT_build<double>(lev_view<double>(h, l), c.cdense64, c.WT64, s);

@@ -102,10 +102,11 @@ struct CsrTView {
   const T *v;             // [nnz] A[i, j]
   const T *d;             // [m*m] A[j, j]
 };
-// cnt: m*m ints, scan_scratch: 2 * ceil(m*m / 1024) ints; col/v64/v32 sized for every tap.
-void launch_csrT_build(const FineTab &tab, const int32_t *off, const uint8_t *policy, double dt,
-                       int *cnt, int *scan_scratch, int32_t *rowptr, int32_t *col, double *v64,
-                       float *v32, double *d64, float *d32, cudaStream_t s);
+// cnt: m*m ints, scan_scratch: 2 * ceil(m*m / 1024) ints; col/vtmp/v64/v32 sized for every
+// tap; R0: the largest |dx|, |dy| of any tap (at most (2^25 - 1) / (n + 1) / 2).
+void launch_csrT_build(const FineTab &tab, const int32_t *off, const uint8_t *policy, double dt, int R0,
+                       int *cnt, int *scan_scratch, int32_t *rowptr, int32_t *col, double *vtmp,
+                       double *v64, float *v32, double *d64, float *d32, cudaStream_t s);
 template <typename T>
 void launch_fineT_op(int op, const CsrTView<T> &A, T omega, const T *x, const T *b, T *y, cudaStream_t s);
 // Dense windows of the rows of A_l^T (level l >= 1) from the forward level; cdense holds the

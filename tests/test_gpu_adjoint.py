@@ -33,6 +33,10 @@ def _case(name):
         p = W.oracle_scale(True)
     elif name == "bnd33":
         p = W.with_dirichlet(W.oracle_scale(True))
+    elif name == "cb33":
+        p = W.with_dirichlet(W.oracle_scale(True))
+        p.c = np.linspace(-0.5, 0.3, p.K)
+        p.drift = np.stack([np.linspace(-2.0, 2.0, p.K), np.linspace(1.5, -1.0, p.K)], axis=1)
     elif name == "k1_33":
         p = W.manufactured(33, 1, 0.3, 0.3, 0.9, 0.7)
     else:
@@ -50,7 +54,7 @@ def _oracle(p, w, dirs):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name,ckpt", [("c33", 1), ("heavy33", 3), ("bnd33", 1), ("k1_33", 2),
-                                       ("s65", 1)])
+                                       ("s65", 1), ("cb33", 2)])
 def test_adjoint_matches_oracle(name, ckpt, precision):
     import torch
     S = _lib()

@@ -3,7 +3,9 @@
 Tolerances: 1e-10 relative max-norm for FP64 results, 1e-8 for the mixed path, bit-exact
 policies apart from near-ties within 1e-12 relative (lowest index wins on both sides).
 Sizes span several 32 x 8 tiles with ragged edges (interior 31, 63, 127, 255 per dimension)
-and include the truncation-heavy 33 x 33 case and the degenerate single-control case.
+and include the truncation-heavy 33 x 33 case, the degenerate single-control case, the
+smallest grid (5 x 5: one level, 9 unknowns), the largest control set (255, the limit of the
+one-byte policy), and a case with discount c^k, constant drift b^k and non-zero Dirichlet data.
 """
 import numpy as np
 import pytest
@@ -38,7 +40,18 @@ CASES = {
     "s65": lambda: W.scaled(65, 17, 8, seed=3),
     "s129": lambda: W.scaled(129, 33, 4, s=(0.6, 0.5)),
     "n9": lambda: W.manufactured(9, 3, -0.5, 0.5, 0.8, 0.6, T=0.25, n_steps=2),
+    "n5": lambda: W.manufactured(5, 3, -0.5, 0.5, 0.8, 0.6, T=0.25, n_steps=2),
+    "k255_33": lambda: W.manufactured(33, 255, -0.95, 0.95, 0.3, 0.2, T=0.25, n_steps=4),
+    "cb33": lambda: _discount_drift(W.with_dirichlet(W.manufactured(33, 9, -0.8, 0.8, 1.2, 1.2,
+                                                                    T=0.5, n_steps=6))),
 }
+
+
+def _discount_drift(p):
+    """Non-zero discount c^k and constant drift b^k (in cells per step) on every control."""
+    p.c = np.linspace(-0.5, 0.3, p.K)
+    p.drift = np.stack([np.linspace(-2.0, 2.0, p.K), np.linspace(1.5, -1.0, p.K)], axis=1)
+    return p
 
 
 def _perturbed_state(prob, seed=0, amp=0.02):
@@ -68,7 +81,7 @@ def _random_policy(prob, seed):
     return rng.integers(0, prob.K, size=(prob.n - 2) ** 2)
 
 
-@pytest.mark.parametrize("name", ["c33", "heavy33", "s65", "s129", "n9"])
+@pytest.mark.parametrize("name", ["c33", "heavy33", "s65", "s129", "n9", "n5", "k255_33", "cb33"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_operators_on_every_level(name, precision):
     prob = CASES[name]()
@@ -97,7 +110,7 @@ def test_operators_on_every_level(name, precision):
         assert rel_maxnorm(got, ref) <= tol, f"level {level}"
 
 
-@pytest.mark.parametrize("name", ["c33", "heavy33", "s65", "s129"])
+@pytest.mark.parametrize("name", ["c33", "heavy33", "s65", "s129", "cb33"])
 def test_vcycle_matches_oracle(name):
     prob = CASES[name]()
     s = _solver(prob, precision=0)
@@ -117,7 +130,7 @@ def test_vcycle_matches_oracle(name):
     assert rel_maxnorm(x.cpu().numpy()[1:-1, 1:-1].ravel(), ref) <= 1e-11
 
 
-@pytest.mark.parametrize("name", ["c33", "heavy33", "s65", "s129"])
+@pytest.mark.parametrize("name", ["c33", "heavy33", "s65", "s129", "cb33"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_linear_solve_matches_direct_solve(name, precision):
     prob = CASES[name]()
@@ -134,7 +147,8 @@ def test_linear_solve_matches_direct_solve(name, precision):
     assert rel_maxnorm(got, ref) <= (TOL_FP64 if precision == 0 else TOL_MIXED)
 
 
-@pytest.mark.parametrize("name", ["c33", "heavy33", "k1_33", "s65", "s129", "n9"])
+@pytest.mark.parametrize("name", ["c33", "heavy33", "k1_33", "s65", "s129", "n9", "n5", "k255_33",
+                                  "cb33"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_full_solve_matches_oracle(name, precision):
     prob = CASES[name]()

@@ -152,3 +152,23 @@ def test_bilinear_discrete_solution_with_boundary_data_and_discount(heavy):
     V = lisl.control_values(p, q, 0.0, f_full=np.zeros((p.K, p.n, p.n)))
     chosen = V[policy, np.arange(N)]
     assert np.max(np.abs(chosen - (Lq + cq))) <= 1e-10 * (1 + np.abs(q).max()) / p.h
+
+
+@pytest.mark.parametrize("heavy", [False, True])
+def test_sampled_control_values_equal_the_full_evaluation(heavy):
+    """control_values_at (used to check full-size GPU steps node by node) restricted to every
+    interior node, and to a shuffled subset, reproduces control_values, including a non-zero
+    boundary, a discount and a drift."""
+    p = W.with_dirichlet(W.oracle_scale(heavy))
+    p.c = np.linspace(-0.5, 0.3, p.K)
+    p.drift = np.stack([np.linspace(-2.0, 2.0, p.K), np.linspace(1.5, -1.0, p.K)], axis=1)
+    rng = np.random.default_rng(0)
+    X = p.g + rng.uniform(-0.1, 0.1, p.g.shape)
+    t = 0.37
+    V = lisl.control_values(p, X, t)
+    i1, i2, _ = lisl.interior_flat(p.n)
+    Va = lisl.control_values_at(p, X, t, i1, i2)
+    assert np.max(np.abs(Va - V)) <= 1e-13 * max(1.0, np.abs(V).max())
+    sel = rng.permutation(len(i1))[:50]
+    Vs = lisl.control_values_at(p, X, t, i1[sel], i2[sel])
+    assert np.max(np.abs(Vs - V[:, sel])) <= 1e-13 * max(1.0, np.abs(V).max())
