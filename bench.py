@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--adjoint-steps", type=int, default=64,
+                   help="steps of 1/64 in the adjoint workload's march (64: T = 1)")
     p.add_argument("--opt", action="append", default=[],
                    help="solver option override key=value (sl_opts field), repeatable")
     return p.parse_args()
@@ -360,7 +362,9 @@ def run_ours(args):
     # ---- discrete adjoint: gradients of J = sum w U(T) on 1025^2, 33 controls, 64 steps
     adjoint = None
     if not args.no_adjoint:
-        adjoint = adjoint_record(slp, W, dev, stream, extra)
+        torch.cuda.nvtx.range_push("adjoint")  # lets a profiler select this part alone
+        adjoint = adjoint_record(slp, W, dev, stream, extra, args.adjoint_steps)
+        torch.cuda.nvtx.range_pop()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -396,16 +400,22 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def adjoint_record(slp, W, dev, stream, extra):
+def adjoint_record(slp, W, dev, stream, extra, steps=64):
     """Forward march with recording, then the backward pass, each timed with CUDA events."""
+    import copy
+
     import torch
     pa, wa = W.adjoint_1025(seed=0)
+    if steps != pa.n_steps:
+        pa = copy.copy(pa)
+        pa.T = pa.T * steps / pa.n_steps
+        pa.n_steps = steps
     dirs = W.sigma_directions(pa)
     na, nt = pa.n, pa.n_steps
     dta = pa.T / nt
     wd = torch.as_tensor(wa, dtype=torch.float64, device=dev)
     out = {"workload": f"uncertain-correlation HJB, {na}x{na} grid, 33 controls rho in "
-                       f"[-0.9,0.9], s1=0.3 s2=0.2, {nt} steps of 1/{nt}; J = sum w U(T) with a "
+                       f"[-0.9,0.9], s1=0.3 s2=0.2, {nt} steps of {dta:g}; J = sum w U(T) with a "
                        "seeded Gaussian bump w; every U^n kept (ckpt_every 1)",
            "unit": UNIT}
     for prec, key in ((1, "mixed"), (0, "fp64")):
