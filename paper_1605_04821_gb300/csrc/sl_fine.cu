@@ -46,15 +46,17 @@ void launch_coef(const double *G, int nf, int nq, const double *tau, const doubl
 // alpha_j = lowest k with v_k <= v_min + tie_rel max(1, |v_min|), decided in FP64.
 //
 // Pass 1 screens all controls from a shared-memory tile of X (tile 32 x 8 nodes plus a halo of
-// the longest tap).  With screen = 0 it is FP64.  With screen = 1 it is FP32 on the split
-// X = hi + lo (hi = fp32(X), lo = fp32(X - hi)), and each screened value carries a rigorous
-// bound E_k on its distance from the exact value; pass 2 decides in FP64 among the controls
-// that the bounds cannot exclude, and with a single survivor that survivor is the FP64 answer.
+// the longest tap).  With screen = 0 it is FP64.  With screen = 1 it is FP32 on the centred
+// tile x'_s = fp32(X_s - c), c = X at the tile's centre node (the subtraction in FP64), and
+// each screened value carries a rigorous bound E_k on its distance from the exact value;
+// pass 2 decides in FP64 among the controls that the bounds cannot exclude, and with a single
+// survivor that survivor is the FP64 answer.
 //
-// Bound of the FP32 screen (unit roundoff u = 2^-24, n_t taps, d_t = X_{j+o_t} - X_j):
-//   X = hi + lo + eta, |eta| <= u^2 |X|;  the staged difference dd_t = (hi_nb - hi_j) + (lo_nb - lo_j)
-//   satisfies |dd_t - d_t| <= 2 u |d_t| + 6 u^2 |X|max;
-//   |sum_t w32_t dd_t - sum_t w_t d_t| <= (n_t + 4) u S + 6 u^2 W |X|max,  S = sum_t w_t |d_t|;
+// Bound of the FP32 screen (unit roundoff u = 2^-24, n_t taps, d_t = X_{j+o_t} - X_j,
+// D = max |X_s - c| over the staged nodes inside the grid):
+//   |x'_s - (X_s - c)| <= u |X_s - c|, so the difference dd_t = fp32(x'_nb - x'_j) satisfies
+//   |dd_t - d_t| <= u |d_t| + 2 u (1 + u) D;
+//   |sum_t w32_t dd_t - sum_t w_t d_t| <= (n_t + 4) u S + 2 u (1 + u) D W,  S = sum_t w_t |d_t|;
 //   |f32_k - f_k| <= (nf + 3) u sum_m |phi_km| |F_m|;  |c32 x32 - c x| <= 3 u |c| |X_j|;
 //   the two final additions <= 2 u |v~_k|.
 // E_k doubles the sum of these terms (S taken from its FP32 evaluation), which also absorbs
@@ -89,12 +91,12 @@ __device__ __forceinline__ double eval_smem64(const FineTab &tab, const int32_t 
   return acc;
 }
 
-// FP32 screen of one control: returns sum_t w (dd_t) and S = sum_t w |dd_t|.  Taps are packed
-// {tile offset, weight}; with TMAX > 0 the loop runs over the padded width, fully unrolled.
+// FP32 screen of one control: returns sum_t w (dd_t) and S = sum_t w |dd_t| on the centred
+// tile xs.  Taps are packed {tile offset, weight}; with TMAX > 0 the loop runs over the padded
+// width, fully unrolled.
 template <int TMAX>
-__device__ __forceinline__ float eval_smem32(const FineTab &tab, int e, const float *__restrict__ hs,
-                                             const float *__restrict__ ls, int sidx, float &S) {
-  const float h0 = hs[sidx], l0 = ls[sidx];
+__device__ __forceinline__ float eval_smem32(const FineTab &tab, int e, const float *__restrict__ xs,
+                                             int sidx, float x0, float &S) {
   float acc = 0.f, sa = 0.f;
   if (TMAX > 0) {
 #pragma unroll
@@ -102,7 +104,7 @@ __device__ __forceinline__ float eval_smem32(const FineTab &tab, int e, const fl
       int o;
       float w;
       PackedTap<float>::get(tab, e * TMAX + t, o, w);
-      const float dd = (hs[sidx + o] - h0) + (ls[sidx + o] - l0);
+      const float dd = xs[sidx + o] - x0;
       acc = fmaf(w, dd, acc);
       sa = fmaf(w, fabsf(dd), sa);
     }
@@ -112,7 +114,7 @@ __device__ __forceinline__ float eval_smem32(const FineTab &tab, int e, const fl
       int o;
       float w;
       PackedTap<float>::get(tab, e * tab.tmax + t, o, w);
-      const float dd = (hs[sidx + o] - h0) + (ls[sidx + o] - l0);
+      const float dd = xs[sidx + o] - x0;
       acc = fmaf(w, dd, acc);
       sa = fmaf(w, fabsf(dd), sa);
     }
@@ -131,41 +133,44 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned red_cnt[kTX * kTY / 32];
   __shared__ float red_max[kTX * kTY / 32];
-  const int S_ = a.SW * a.SH;
   double *xs64 = reinterpret_cast<double *>(smem_raw);
-  float *hs = reinterpret_cast<float *>(smem_raw);
-  float *ls = hs + S_;
+  float *xs32 = reinterpret_cast<float *>(smem_raw);
 
   const FineTab &tab = a.tab;
   const int n = tab.n, m = tab.m;
   const int tid = threadIdx.y * kTX + threadIdx.x;
   const int o1 = 1 + blockIdx.x * kTX - a.halo;  // grid coordinate of staged column 0
   const int o2 = 1 + blockIdx.y * kTY - a.halo;
-  float xmax = 0.f;
+  // centre of the FP32 tile: X at the tile's middle node (inside the grid)
+  double xc = 0.0;
+  if (SCREEN) {
+    const int c1 = min(1 + blockIdx.x * kTX + kTX / 2, n - 2), c2 = min(1 + blockIdx.y * kTY + kTY / 2, n - 2);
+    xc = a.X[size_t(c2) * n + c1];
+  }
+  float dmax = 0.f;
   for (int r = threadIdx.y; r < a.SH; r += kTY) {
     const int g2 = o2 + r;
     for (int cc = threadIdx.x; cc < a.SW; cc += kTX) {
       const int g1 = o1 + cc, s = r * a.SW + cc;
-      double xv = 0.0;
-      if (g1 >= 0 && g1 < n && g2 >= 0 && g2 < n) xv = a.X[size_t(g2) * n + g1];
+      const bool in = g1 >= 0 && g1 < n && g2 >= 0 && g2 < n;
+      const double xv = in ? a.X[size_t(g2) * n + g1] : 0.0;
       if (SCREEN) {
-        const float hi = float(xv);
-        hs[s] = hi;
-        ls[s] = float(xv - double(hi));
-        xmax = fmaxf(xmax, fabsf(hi));
+        const float xd = float(xv - xc);  // taps never leave the grid: outside values are unused
+        xs32[s] = xd;
+        if (in) dmax = fmaxf(dmax, fabsf(xd));
       } else {
         xs64[s] = xv;
       }
     }
   }
   if (SCREEN) {
-    for (int o = 16; o > 0; o >>= 1) xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-    if ((tid & 31) == 0) red_max[tid >> 5] = xmax;
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((tid & 31) == 0) red_max[tid >> 5] = dmax;
   }
   __syncthreads();
-  float Xmax = 0.f;
+  float Dmax = 0.f;
   if (SCREEN)
-    for (int w = 0; w < kTX * kTY / 32; ++w) Xmax = fmaxf(Xmax, red_max[w]);
+    for (int w = 0; w < kTX * kTY / 32; ++w) Dmax = fmaxf(Dmax, red_max[w]);
 
   const int i1 = 1 + blockIdx.x * kTX + threadIdx.x;
   const int i2 = 1 + blockIdx.y * kTY + threadIdx.y;
@@ -191,15 +196,17 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
     if (SCREEN) {
       const float u = 5.9604645e-8f;
       const float xj32 = float(Xj);
-      // node-constant part of E_k: f-term, c-term and the u^2 term (Xmax * 1.001 covers |X|)
+      // node-constant part of E_k: f-term, c-term and the centring term 2 u (1 + u) D
+      // (Dmax * 1.001 covers D: the staged |x'| are within a factor 1 + u of |X - c|)
       const float Ef = u * ((nf + 3.0f) * Fabs * 1.001f + 3.0f * float(a.cmax) * fabsf(xj32) * 1.001f);
-      const float eta = 6.0f * u * u * Xmax * 1.001f + 1e-30f;
+      const float eta = 2.0f * u * Dmax * 1.001f + 1e-30f;
+      const float x0 = xs32[sidx];
       const float tw_rel = float(a.tie_rel) * 2.0f;
       float Umin = INFINITY, Lmin = INFINITY;
       for (int k = 0; k < tab.K; ++k) {
         const int e = (k * tab.Q + q2) * tab.Q + q1;
         float S;
-        const float acc = eval_smem32<TMAX>(tab, e, hs, ls, sidx, S);
+        const float acc = eval_smem32<TMAX>(tab, e, xs32, sidx, x0, S);
         float f = 0.f;
         for (int mm = 0; mm < nf && mm < 4; ++mm) f = fmaf(__ldg(a.phi32 + k * nf + mm), Fv32[mm], f);
         const float v = acc + fmaf(tab.c32[k], xj32, f);
@@ -309,7 +316,7 @@ cudaError_t argmin_launch(const ArgminArgs &a, dim3 grd, dim3 blk, size_t bytes,
 
 cudaError_t launch_argmin(const ArgminArgs &a, cudaStream_t s) {
   dim3 blk(kTX, kTY), grd((a.tab.m + kTX - 1) / kTX, (a.tab.m + kTY - 1) / kTY);
-  const size_t bytes = size_t(a.SW) * a.SH * (a.screen ? 2 * sizeof(float) : sizeof(double));
+  const size_t bytes = size_t(a.SW) * a.SH * (a.screen ? sizeof(float) : sizeof(double));
   if (!a.screen) return argmin_launch<0, 0>(a, grd, blk, bytes, s);
   switch (a.tab.tmax) {
     case 8: return argmin_launch<1, 8>(a, grd, blk, bytes, s);
