@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batched-instances", type=int, default=256)
+    p.add_argument("--batched-workers", type=int, default=16)
     p.add_argument("--adjoint-steps", type=int, default=64,
                    help="steps of 1/64 in the adjoint workload's march (64: T = 1)")
     p.add_argument("--opt", action="append", default=[],
@@ -366,6 +369,13 @@ def run_ours(args):
         adjoint = adjoint_record(slp, W, dev, stream, extra, args.adjoint_steps)
         torch.cuda.nvtx.range_pop()
 
+    # ---- batched: many independent instances, LPT-sharded over the ranks
+    batched = None
+    if not args.no_batched:
+        torch.cuda.nvtx.range_push("batched")
+        batched = batched_record(slp, W, dev, args, extra, rank, world, barrier, dist)
+        torch.cuda.nvtx.range_pop()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_record()
@@ -394,6 +404,7 @@ def run_ours(args):
             "fp64": fp64,
             "mixed_vs_fp64_rel_err": err,
             "adjoint": adjoint,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -446,6 +457,59 @@ def adjoint_record(slp, W, dev, stream, extra, steps=64):
         del sa
         torch.cuda.empty_cache()
     out["value"] = out["mixed"]["value"]
+    return out
+
+
+def batched_record(slp, W, dev, args, extra, rank, world, barrier, dist):
+    """The batched workload (independent instances of the same PDE family) with W worker
+    threads and, for comparison, with one; each run is timed on the host around
+    sl_batch_run, which returns when every instance's stream is idle."""
+    import torch
+    probs = W.batched(n_inst=args.batched_instances, seed=0)
+    mine = slp.shard(probs, world, rank)
+    sub = [probs[i] for i in mine]
+    us = [torch.as_tensor(p.g, dtype=torch.float64, device=dev) for p in sub]
+    kw = dict(precision=1, argmin_screen=1)
+    kw.update(extra)
+    out = {"workload": f"{len(probs)} instances of the uncertain-correlation family: n uniform in "
+                       "{65,129,257,513}, (s1,s2) ~ U[0.15,0.4]^2, K ~ U{17..65}, rho in "
+                       "[-0.9,0.9], 32 steps of 1/32 (seed 0); mixed precision",
+           "unit": UNIT, "instances": len(probs), "scaling": "weak" if world > 1 else None,
+           "sharding": "LPT over ranks by n^2 * steps * (K + 32), no collective" if world > 1 else None}
+    gp = sum(p.n * p.n * p.n_steps for p in sub)
+    for workers, key in ((args.batched_workers, "concurrent"), (1, "one_worker")):
+        b = slp.Batch(sub, us, workers=workers, device=dev, **kw)
+        for u, p in zip(us, sub):
+            u.copy_(torch.as_tensor(p.g, device=dev))
+        b.run()   # warm-up: graphs and class tables of every handle
+        for u, p in zip(us, sub):
+            u.copy_(torch.as_tensor(p.g, device=dev))
+        torch.cuda.synchronize()
+        barrier()
+        l0 = slp.launch_count()
+        t0 = time.perf_counter()
+        st, stats = b.run()
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        launches = slp.launch_count() - l0
+        if dist is not None:
+            t = torch.tensor([sec], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+            g = torch.tensor([gp], device=dev, dtype=torch.float64)
+            dist.all_reduce(g)
+            total = float(g.item())
+        else:
+            total = float(gp)
+        out[key] = {"workers": workers, "value": total / sec, "seconds": sec,
+                    "failed": int(sum(1 for x in st if x != 0)), "gpu_launches": launches,
+                    "pi_iters": int(sum(s["pi_iters"] for s in stats)),
+                    "krylov_iters": int(sum(s["krylov_iters"] for s in stats))}
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+    out["value"] = out["concurrent"]["value"]
+    out["speedup_vs_one_worker"] = out["concurrent"]["value"] / out["one_worker"]["value"]
     return out
 
 

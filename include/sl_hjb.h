@@ -206,6 +206,55 @@ sl_status sl_hjb_adjoint(sl_hjb *h, const double *w_dev, double *dJ_dg_dev, doub
 const char *sl_hjb_last_error(const sl_hjb *h);
 void sl_hjb_destroy(sl_hjb *h);
 
+/* Forgets the march state of the handle: the current policy (the next step starts from an
+ * improvement on its U^{n-1}, as the first step of a new handle does), the previous step used
+ * for extrapolation and the Galerkin hierarchy.  A solve after a reset gives the same result
+ * as the same solve on a new handle. */
+sl_status sl_hjb_reset(sl_hjb *h);
+
+/* ---- Batched solves: many independent instances on one GPU ----
+ *
+ * The paper solves one problem at a time; a batch runs many independent instances (each its
+ * own grid, control set and source, as for sl_hjb_create) concurrently on one device.  The
+ * library assigns instances to n_workers host threads by the longest-processing-time-first
+ * rule on the estimated cost nx*ny*n_steps*(K + 32); each worker owns one CUDA stream and
+ * solves its instances in decreasing cost, so kernels of different instances overlap on the
+ * device.  Every instance runs exactly the launch sequence of sl_hjb_solve on a new handle,
+ * so its result equals that solve bit for bit. */
+typedef struct {
+  sl_grid grid;
+  sl_controls ctrl;    /* host arrays are copied by sl_batch_create */
+  sl_source src;       /* G_dev / Psi_dev must outlive the batch */
+  double *u_dev;       /* device, nx*ny: in g, out U(t0 + T); owned by the caller */
+  double t0, T;
+  int n_steps;
+} sl_instance;
+
+typedef struct sl_batch sl_batch;
+
+/* Creates one handle per instance (all with opts) and the workers' streams.  Returns
+ * SL_EINVAL for bad arguments or the status of the first failing sl_hjb_create (then *b is
+ * NULL). */
+sl_status sl_batch_create(sl_batch **b, int n_inst, const sl_instance *inst, const sl_opts *opts,
+                          int n_workers);
+
+/* Solves every instance from its u_dev (reset first, see sl_hjb_reset) and returns when all
+ * are done.  status_out / stats_out (host, n_inst entries, may be NULL) receive each
+ * instance's status and statistics; a failing instance does not stop the others.  Returns
+ * SL_OK or the status of the lowest-numbered failing instance. */
+sl_status sl_batch_run(sl_batch *b, sl_status *status_out, sl_stats *stats_out);
+
+/* Worker (0 .. n_workers-1) that runs instance i, or -1. */
+int sl_batch_worker_of(const sl_batch *b, int i);
+
+/* LPT plan used by the batch (pure host function): bin_of[i] = bin of item i for n_bins bins,
+ * items taken in decreasing cost (ties by index) and each placed in the least-loaded bin
+ * (ties by the lowest bin).  Returns SL_OK or SL_EINVAL. */
+int sl_batch_plan(int n_items, const double *cost, int n_bins, int *bin_of);
+
+const char *sl_batch_last_error(const sl_batch *b);
+void sl_batch_destroy(sl_batch *b);
+
 /* ---- Stage entry points: single phases of a step, for parity checks and diagnostics ---- */
 
 /* Policy improvement (row-wise linear search of Eq. nonlinear_sys) on x_ext_dev (n*n FP64,

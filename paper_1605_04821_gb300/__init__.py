@@ -26,7 +26,9 @@ EXPORTED = ["sl_opts_default", "sl_hjb_create", "sl_hjb_step", "sl_hjb_solve",
             "sl_hjb_last_error", "sl_hjb_destroy", "sl_hjb_improve", "sl_hjb_set_policy",
             "sl_hjb_build_hierarchy", "sl_hjb_apply", "sl_hjb_vcycle", "sl_hjb_linear_solve",
             "sl_hjb_level_info", "sl_hjb_num_levels", "sl_launch_count",
-            "sl_hjb_vcycle_noalloc", "sl_hjb_solve_record", "sl_hjb_adjoint"]
+            "sl_hjb_vcycle_noalloc", "sl_hjb_solve_record", "sl_hjb_adjoint", "sl_hjb_reset",
+            "sl_batch_create", "sl_batch_run", "sl_batch_worker_of", "sl_batch_plan",
+            "sl_batch_last_error", "sl_batch_destroy"]
 
 
 class SlGrid(ctypes.Structure):
@@ -54,6 +56,12 @@ class SlOpts(ctypes.Structure):
                 ("argmin_screen", ctypes.c_int), ("rebuild_frac", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("coarse_tail_rows", ctypes.c_int),
                 ("extrapolate", ctypes.c_int)]
+
+
+class SlInstance(ctypes.Structure):
+    _fields_ = [("grid", SlGrid), ("ctrl", SlControls), ("src", SlSource),
+                ("u_dev", ctypes.c_void_p), ("t0", ctypes.c_double), ("T", ctypes.c_double),
+                ("n_steps", ctypes.c_int)]
 
 
 class SlStats(ctypes.Structure):
@@ -101,6 +109,14 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "sl_hjb_vcycle_noalloc": (i, [vp, i, vp, vp, vp]),
         "sl_hjb_solve_record": (i, [vp, vp, d, d, i, i, ctypes.POINTER(SlStats), vp]),
         "sl_hjb_adjoint": (i, [vp, vp, vp, vp, i, vp, vp, ctypes.POINTER(SlStats), vp]),
+        "sl_hjb_reset": (i, [vp]),
+        "sl_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(SlInstance),
+                                ctypes.POINTER(SlOpts), i]),
+        "sl_batch_run": (i, [vp, vp, ctypes.POINTER(SlStats)]),
+        "sl_batch_worker_of": (i, [vp, i]),
+        "sl_batch_plan": (i, [i, vp, i, vp]),
+        "sl_batch_last_error": (ctypes.c_char_p, [vp]),
+        "sl_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -141,6 +157,42 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _describe(keep: list, n, lo, hi, sigma, phi, G, tau_kind, tau_rate, Psi=None, psi_kind=None,
+              psi_rate=None, b=None, c=None):
+    """sl_grid / sl_controls / sl_source for one problem.  Host arrays and the device tensors
+    are appended to `keep` (which must outlive the structs); the last two entries are G and
+    Psi (or None)."""
+    import torch
+
+    def host(a, dtype):
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        keep.append(arr)
+        return arr.ctypes.data_as(ctypes.c_void_p)
+
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    K, _, P = sigma.shape
+    grid = SlGrid(n, n, lo, hi, lo, hi)
+    ctrl = SlControls(K, P, host(sigma, np.float64),
+                      host(b, np.float64) if b is not None else None,
+                      host(c, np.float64) if c is not None else None)
+    G = G.contiguous()
+    assert G.is_cuda and G.dtype == torch.float64 and G.shape[2:] == (n, n)
+    nf, nq = G.shape[0], G.shape[1]
+    npsi = 0
+    psi_ptr = None
+    if Psi is not None:
+        Psi = Psi.contiguous()
+        npsi = Psi.shape[0]
+        psi_ptr = _ptr(Psi)
+    src = SlSource(nf, nq, host(phi, np.float64), _ptr(G), host(tau_kind, np.int32),
+                   host(tau_rate, np.float64), npsi, psi_ptr,
+                   host(psi_kind, np.int32) if npsi else None,
+                   host(psi_rate, np.float64) if npsi else None)
+    keep.append(G)
+    keep.append(Psi)
+    return grid, ctrl, src
+
+
 class Solver:
     """Owns one library handle.  All tensors are CUDA tensors on the current device.
 
@@ -151,38 +203,14 @@ class Solver:
     def __init__(self, n: int, lo: float, hi: float, sigma: np.ndarray, phi: np.ndarray, G,
                  tau_kind, tau_rate, Psi=None, psi_kind=None, psi_rate=None, b=None, c=None,
                  opts: Optional[SlOpts] = None, stream=None, **opt_kw):
-        import torch
         lib = load()
         self._lib = lib
-        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
-        K, _, P = sigma.shape
-        self.n, self.K, self.P = n, K, P
         self._keep = []
-
-        def host(a, dtype):
-            arr = np.ascontiguousarray(a, dtype=dtype)
-            self._keep.append(arr)
-            return arr.ctypes.data_as(ctypes.c_void_p)
-
-        grid = SlGrid(n, n, lo, hi, lo, hi)
-        ctrl = SlControls(K, P, host(sigma, np.float64),
-                          host(b, np.float64) if b is not None else None,
-                          host(c, np.float64) if c is not None else None)
-        G = G.contiguous()
-        assert G.is_cuda and G.dtype == torch.float64 and G.shape[2:] == (n, n)
-        nf, nq = G.shape[0], G.shape[1]
-        self._G = G
-        npsi = 0
-        psi_ptr = None
-        if Psi is not None:
-            Psi = Psi.contiguous()
-            self._Psi = Psi
-            npsi = Psi.shape[0]
-            psi_ptr = _ptr(Psi)
-        src = SlSource(nf, nq, host(phi, np.float64), _ptr(G), host(tau_kind, np.int32),
-                       host(tau_rate, np.float64), npsi, psi_ptr,
-                       host(psi_kind, np.int32) if npsi else None,
-                       host(psi_rate, np.float64) if npsi else None)
+        grid, ctrl, src = _describe(self._keep, n, lo, hi, sigma, phi, G, tau_kind, tau_rate, Psi,
+                                    psi_kind, psi_rate, b, c)
+        self.n, self.K, self.P = n, ctrl.K, ctrl.P
+        self._G = self._keep[-2]
+        self._Psi = self._keep[-1]
         self.opts = opts if opts is not None else default_opts(**opt_kw)
         h = ctypes.c_void_p()
         st = lib.sl_hjb_create(ctypes.byref(h), ctypes.byref(grid), ctypes.byref(ctrl),
@@ -191,6 +219,10 @@ class Solver:
             raise SLError(st, "sl_hjb_create failed (see stderr)")
         self.h = h
         self.m = n - 2
+
+    def reset(self):
+        """sl_hjb_reset: the next step starts like the first step of a new handle."""
+        self._check(self._lib.sl_hjb_reset(self.h))
 
     def close(self):
         if getattr(self, "h", None):
@@ -296,22 +328,104 @@ class Solver:
         return n.value, ex.value
 
 
-def solver_from_problem(prob, device=None, stream=None, **opt_kw) -> Solver:
-    """Marshals a `workloads.Problem` with a separable source into a Solver."""
+def _problem_args(prob, dev):
+    """Positional and keyword arguments of Solver / _describe for a `workloads.Problem`."""
     import torch
     if prob.G is None:
         raise ValueError("the library needs the separable source form (phi, G, tau)")
-    dev = device or torch.device("cuda")
     G = torch.as_tensor(prob.G, dtype=torch.float64, device=dev)
     psi = prob.psi_fn(0.0)
-    Psi = None
     kw = {}
     if np.any(psi != 0.0):
         Psi = torch.as_tensor(psi[None], dtype=torch.float64, device=dev)
         kw = dict(Psi=Psi, psi_kind=np.array([0], dtype=np.int32), psi_rate=np.array([0.0]))
-    return Solver(prob.n, prob.lo, prob.hi, prob.sigma, prob.phi, G,
-                  np.asarray(prob.tau_kind, dtype=np.int32), np.asarray(prob.tau_rate, dtype=np.float64),
-                  b=prob.drift, c=prob.c, stream=stream, **kw, **opt_kw)
+    args = (prob.n, prob.lo, prob.hi, prob.sigma, prob.phi, G,
+            np.asarray(prob.tau_kind, dtype=np.int32), np.asarray(prob.tau_rate, dtype=np.float64))
+    kw.update(b=prob.drift, c=prob.c)
+    return args, kw
+
+
+def solver_from_problem(prob, device=None, stream=None, **opt_kw) -> Solver:
+    """Marshals a `workloads.Problem` with a separable source into a Solver."""
+    import torch
+    args, kw = _problem_args(prob, device or torch.device("cuda"))
+    return Solver(*args, stream=stream, **kw, **opt_kw)
+
+
+class Batch:
+    """sl_batch: independent instances solved concurrently by `workers` host threads, each
+    with its own stream.  `problems` are `workloads.Problem`s; `us` are their state tensors
+    (n x n float64 on the device: in g, out U(t0 + T)), kept by the batch."""
+
+    def __init__(self, problems, us, workers: int = 8, t0: float = 0.0, device=None, **opt_kw):
+        import torch
+        lib = load()
+        self._lib = lib
+        self._keep = []
+        dev = device or torch.device("cuda")
+        n = len(problems)
+        arr = (SlInstance * n)()
+        for i, (p, u) in enumerate(zip(problems, us)):
+            args, kw = _problem_args(p, dev)
+            grid, ctrl, src = _describe(self._keep, *args, **kw)
+            assert u.is_cuda and u.dtype == torch.float64 and u.is_contiguous()
+            self._keep.append(u)
+            arr[i] = SlInstance(grid, ctrl, src, _ptr(u), t0, p.T, p.n_steps)
+        self._arr = arr
+        self.n = n
+        self.opts = default_opts(**opt_kw)
+        b = ctypes.c_void_p()
+        st = lib.sl_batch_create(ctypes.byref(b), n, arr, ctypes.byref(self.opts), workers)
+        if st != SL_OK:
+            raise SLError(st, "sl_batch_create failed (see stderr)")
+        self.b = b
+
+    def run(self):
+        """Solves every instance; returns (statuses, per-instance stats dicts)."""
+        st = (ctypes.c_int * self.n)()
+        stats = (SlStats * self.n)()
+        self._lib.sl_batch_run(self.b, st, stats)
+        return [int(x) for x in st], [s.as_dict() for s in stats]
+
+    def worker_of(self, i: int) -> int:
+        return int(self._lib.sl_batch_worker_of(self.b, i))
+
+    def last_error(self) -> str:
+        return self._lib.sl_batch_last_error(self.b).decode()
+
+    def close(self):
+        if getattr(self, "b", None):
+            self._lib.sl_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lpt_plan(costs, bins: int):
+    """sl_batch_plan: the LPT assignment (bin of each item) the batch uses."""
+    costs = np.ascontiguousarray(costs, dtype=np.float64)
+    out = np.zeros(len(costs), dtype=np.int32)
+    st = load().sl_batch_plan(len(costs), costs.ctypes.data_as(ctypes.c_void_p), bins,
+                              out.ctypes.data_as(ctypes.c_void_p))
+    if st != SL_OK:
+        raise SLError(st, "sl_batch_plan: bad arguments")
+    return out
+
+
+def instance_cost(prob) -> float:
+    """The batch's cost estimate of one instance: nodes x steps x (K + 32)."""
+    return float(prob.n) * prob.n * prob.n_steps * (prob.K + 32)
+
+
+def shard(problems, world: int, rank: int):
+    """Indices of the instances that rank `rank` of `world` solves: the LPT plan over ranks
+    (instances are independent, so no collective is needed on the data path)."""
+    plan = lpt_plan([instance_cost(p) for p in problems], world)
+    return [i for i in range(len(problems)) if plan[i] == rank]
 
 
 def hjb_solve(solver: Solver, g, G, T: float, n_steps: int, ckpt_every: int = 1, theta=None,

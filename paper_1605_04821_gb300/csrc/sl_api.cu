@@ -541,14 +541,14 @@ sl_status ensure_graph(sl_hjb *h, int prec, double dt, TX *x, T *r, T *rh, T *p,
     g.exec = nullptr;
   }
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-  const long long before = launch_count();
+  const long long before = thread_launch_count();  // other threads may launch meanwhile
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   sl_status st = issue_iteration<T, TX>(h, dt, x, r, rh, p, v, sv, t, ph, sh, S, h->cap_stream);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
   if (st != SL_OK) return st;
   CK(e);
-  g.kernels = launch_count() - before;
+  g.kernels = thread_launch_count() - before;
   note_launch(int(-g.kernels));  // captured, not executed
   e = cudaGraphInstantiate(&g.exec, graph, 0);
   cudaGraphDestroy(graph);
@@ -1108,6 +1108,9 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
     const int mc = h->cl[h->L - 1].m;
     if (mc * mc > kCoarsestMax) return fail(h, SL_EINVAL, "coarsest level too large for the dense solve: use more levels");
   }
+  // kernels that may take more than 48 KB of dynamic shared memory (once per device)
+  CK(prepare_fine_kernels());
+  CK(prepare_coarse_kernels());
   // stencil tables
   try {
     h->ft = build_fine_tables(h->n, h->h, h->K, h->P, c->sigma, c->b, c->c);
@@ -1269,6 +1272,15 @@ sl_status sl_hjb_solve(sl_hjb *h, double *u, double t0, double T, int n_steps, u
     sl_status r = step_impl(h, u, t0 + i * dt, dt, pol_out, st, static_cast<cudaStream_t>(stream));
     if (r != SL_OK) return r;
   }
+  return SL_OK;
+}
+
+sl_status sl_hjb_reset(sl_hjb *h) {
+  if (!h) return SL_EINVAL;
+  h->have_policy = false;
+  h->have_prev2 = false;
+  h->hier_valid = false;
+  h->changes_since_build = 0;
   return SL_OK;
 }
 

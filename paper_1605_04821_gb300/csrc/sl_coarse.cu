@@ -180,9 +180,6 @@ cudaError_t launch_rap_explicit(int level, const FineTab &tab, const int32_t *fi
   threads = threads > 128 ? 128 : threads;
   if (threads < 1) return cudaErrorInvalidValue;
   const size_t bytes = per * threads;
-  cudaError_t err = cudaFuncSetAttribute(k_rap_explicit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(bytes));
-  if (err != cudaSuccess) return err;
   note_launch();
   k_rap_explicit<T><<<(count + threads - 1) / threads, threads, bytes, s>>>(
       level, tab, fine_off, policy, dt, prev, prev_coff, cur, count, ewin_out);
@@ -318,11 +315,6 @@ void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T ome
   const int eg = std::max(1, std::min(kRedBlocks, (L.cap + 255) / 256));
   const int grid = tiles + eg;
   const size_t bytes = op == OP_JACOBI0 ? 0 : size_t(32 + 2 * L.R) * (kCRowsY + 2 * L.R) * sizeof(T);
-  if (bytes > 48 * 1024) {
-    cudaFuncSetAttribute(k_coarse_op<T, OP_APPLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    cudaFuncSetAttribute(k_coarse_op<T, OP_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    cudaFuncSetAttribute(k_coarse_op<T, OP_JACOBI>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-  }
   note_launch();
   switch (op) {
     case OP_APPLY: k_coarse_op<T, OP_APPLY><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
@@ -555,5 +547,25 @@ void launch_coarsest_apply(const T *Ainv, int n, const T *b, T *x, cudaStream_t 
 }
 template void launch_coarsest_apply<double>(const double *, int, const double *, double *, cudaStream_t, int);
 template void launch_coarsest_apply<float>(const float *, int, const float *, float *, cudaStream_t, int);
+
+// ----------------------------------------------------------------------------- attributes
+template <typename T>
+static cudaError_t prepare_coarse_T() {
+  const void *fs[] = {reinterpret_cast<const void *>(k_rap_explicit<T>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_APPLY>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_RESID>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI0>)};
+  for (const void *f : fs) {
+    cudaError_t e = allow_dynamic_smem(f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t prepare_coarse_kernels() {
+  cudaError_t e = prepare_coarse_T<double>();
+  return e != cudaSuccess ? e : prepare_coarse_T<float>();
+}
 
 }  // namespace sl

@@ -306,9 +306,6 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
 
 template <int SCREEN, int TMAX>
 cudaError_t argmin_launch(const ArgminArgs &a, dim3 grd, dim3 blk, size_t bytes, cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(k_argmin<SCREEN, TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(bytes));
-  if (err != cudaSuccess) return err;
   note_launch();
   k_argmin<SCREEN, TMAX><<<grd, blk, bytes, s>>>(a);
   return cudaGetLastError();
@@ -424,13 +421,6 @@ void fine_op_dispatch(const FineTab &tab, const uint8_t *policy, T dt, T omega, 
                       T *y, int halo, int SW, cudaStream_t s) {
   dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + kOpRowsY - 1) / kOpRowsY);
   const size_t bytes = OP == OP_JACOBI0 ? 0 : size_t(SW) * (kOpRowsY + 2 * halo) * sizeof(T);
-  if (bytes > 48 * 1024) {  // wide stencils: opt in to more dynamic shared memory
-    cudaFuncSetAttribute(k_fine_op<T, OP, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    cudaFuncSetAttribute(k_fine_op<T, OP, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    cudaFuncSetAttribute(k_fine_op<T, OP, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    cudaFuncSetAttribute(k_fine_op<T, OP, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    cudaFuncSetAttribute(k_fine_op<T, OP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-  }
   note_launch();
   switch (tab.tmax) {
     case 8: k_fine_op<T, OP, 8><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
@@ -541,5 +531,42 @@ template void launch_restrict<double>(const double *, int, double *, int, cudaSt
 template void launch_restrict<float>(const float *, int, float *, int, cudaStream_t);
 template void launch_prolong_add<double>(const double *, int, double *, int, cudaStream_t);
 template void launch_prolong_add<float>(const float *, int, float *, int, cudaStream_t);
+
+// ----------------------------------------------------------------------------- attributes
+template <typename T, int OP>
+static cudaError_t prepare_fine_op() {
+  const void *fs[] = {reinterpret_cast<const void *>(k_fine_op<T, OP, 8>),
+                      reinterpret_cast<const void *>(k_fine_op<T, OP, 12>),
+                      reinterpret_cast<const void *>(k_fine_op<T, OP, 16>),
+                      reinterpret_cast<const void *>(k_fine_op<T, OP, 20>),
+                      reinterpret_cast<const void *>(k_fine_op<T, OP, 0>)};
+  for (const void *f : fs) {
+    cudaError_t e = allow_dynamic_smem(f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t prepare_fine_kernels() {
+  const void *fs[] = {reinterpret_cast<const void *>(k_argmin<0, 0>),
+                      reinterpret_cast<const void *>(k_argmin<1, 8>),
+                      reinterpret_cast<const void *>(k_argmin<1, 12>),
+                      reinterpret_cast<const void *>(k_argmin<1, 16>),
+                      reinterpret_cast<const void *>(k_argmin<1, 20>),
+                      reinterpret_cast<const void *>(k_argmin<1, 0>)};
+  for (const void *f : fs) {
+    cudaError_t e = allow_dynamic_smem(f);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t (*ops[])() = {prepare_fine_op<double, OP_APPLY>, prepare_fine_op<double, OP_RESID>,
+                            prepare_fine_op<double, OP_JACOBI>, prepare_fine_op<double, OP_JACOBI0>,
+                            prepare_fine_op<float, OP_APPLY>, prepare_fine_op<float, OP_RESID>,
+                            prepare_fine_op<float, OP_JACOBI>, prepare_fine_op<float, OP_JACOBI0>};
+  for (auto op : ops) {
+    cudaError_t e = op();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 }  // namespace sl

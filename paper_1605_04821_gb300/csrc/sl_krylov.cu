@@ -7,6 +7,9 @@
 // only the residual norm once per iteration.
 #include <atomic>
 #include <cmath>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "sl_launch.h"
 
@@ -15,8 +18,33 @@ namespace sl {
 constexpr int kVecThreads = 256;
 
 static std::atomic<long long> g_launches{0};
-void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;  // this host thread's launches (graph captures)
+void note_launch(int n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+long long thread_launch_count() { return t_launches; }
+
+cudaError_t allow_dynamic_smem(const void *func) {
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({func, dev})) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - int(fa.sharedSizeBytes));
+  if (e == cudaSuccess) done.insert({func, dev});
+  return e;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

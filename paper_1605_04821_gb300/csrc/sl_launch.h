@@ -8,9 +8,20 @@
 
 namespace sl {
 
-// Host-side count of kernel launches issued by the library (all handles).
+// Host-side count of kernel launches issued by the library (all handles, all threads), and
+// the part issued by the calling host thread.
 void note_launch(int n = 1);
 long long launch_count();
+long long thread_launch_count();
+
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum, once per
+// kernel and device (thread-safe).  The limit is process-wide state of the kernel: setting it
+// to each launch's own size would race between host threads that launch the same kernel with
+// different sizes.  prepare_*_kernels apply it to every kernel of a file that may need more
+// than 48 KB; sl_hjb_create calls them, so no solve or graph capture changes the attribute.
+cudaError_t allow_dynamic_smem(const void *func);
+cudaError_t prepare_fine_kernels();
+cudaError_t prepare_coarse_kernels();
 
 enum FineOp { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_JACOBI0 = 3 };
 

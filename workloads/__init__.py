@@ -243,6 +243,20 @@ def adjoint_1025(seed: int = 0):
     return p, gaussian_bump(p.n, p.lo, p.hi, seed)
 
 
+def batched(n_inst: int = 256, seed: int = 0, sizes=(65, 129, 257, 513), k_range=(17, 65),
+            n_steps: int = 32, T: float = 1.0):
+    """Independent instances of the uncertain-correlation family: grid size uniform over
+    `sizes`, (s1, s2) ~ U[0.15, 0.4]^2, K ~ U{k_range}, rho in [-0.9, 0.9], n_steps steps."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_inst):
+        n = int(rng.choice(sizes))
+        s1, s2 = rng.uniform(0.15, 0.4, size=2)
+        K = int(rng.integers(k_range[0], k_range[1] + 1))
+        out.append(manufactured(n, K, -0.9, 0.9, float(s1), float(s2), T=T, n_steps=n_steps))
+    return out
+
+
 def unit_circle_controls(n_alpha: int) -> np.ndarray:
     """N_alpha equally spaced points on the unit circle, angles 2 pi k / N_alpha."""
     ang = 2.0 * math.pi * np.arange(n_alpha) / n_alpha
