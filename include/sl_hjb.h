@@ -67,9 +67,14 @@ typedef struct {
 typedef struct {
   int K;                /* 1 .. 255 */
   int P;                /* 1 .. 4 */
-  const double *sigma;  /* host, K*2*P */
+  const double *sigma;  /* host, K*2*P, or NULL when sigma_field is given */
   const double *b;      /* host, K*2 drift, or NULL for b = 0 */
   const double *c;      /* host, K discount, or NULL for c = 0 */
+  const double *sigma_field;  /* host, n*n*2*P, or NULL: an x-dependent diffusion shared by all
+                                 controls (Section 2.4, Problem A), sigma_field[((i2*n + i1)*2 + d)*P + p]
+                                 = component d of column p at node (i1, i2); sigma is then ignored.
+                                 The controls differ through b and c; the policy improvement is FP64
+                                 (argmin_screen ignored) and sl_hjb_adjoint gives no dJ/dtheta. */
 } sl_controls;
 
 /* Time factors tau(t) of the separable source and boundary data. */

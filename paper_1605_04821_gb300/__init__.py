@@ -38,7 +38,7 @@ class SlGrid(ctypes.Structure):
 
 class SlControls(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("P", ctypes.c_int), ("sigma", ctypes.c_void_p),
-                ("b", ctypes.c_void_p), ("c", ctypes.c_void_p)]
+                ("b", ctypes.c_void_p), ("c", ctypes.c_void_p), ("sigma_field", ctypes.c_void_p)]
 
 
 class SlSource(ctypes.Structure):
@@ -158,7 +158,7 @@ def _stream(stream):
 
 
 def _describe(keep: list, n, lo, hi, sigma, phi, G, tau_kind, tau_rate, Psi=None, psi_kind=None,
-              psi_rate=None, b=None, c=None):
+              psi_rate=None, b=None, c=None, sigma_field=None):
     """sl_grid / sl_controls / sl_source for one problem.  Host arrays and the device tensors
     are appended to `keep` (which must outlive the structs); the last two entries are G and
     Psi (or None)."""
@@ -169,12 +169,19 @@ def _describe(keep: list, n, lo, hi, sigma, phi, G, tau_kind, tau_rate, Psi=None
         keep.append(arr)
         return arr.ctypes.data_as(ctypes.c_void_p)
 
-    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
-    K, _, P = sigma.shape
+    if sigma_field is not None:   # x-dependent diffusion shared by all controls
+        sigma_field = np.ascontiguousarray(sigma_field, dtype=np.float64)
+        assert sigma_field.shape[:3] == (n, n, 2)
+        K, P = len(np.atleast_2d(phi)), sigma_field.shape[3]
+        sig_ptr, fld_ptr = None, host(sigma_field, np.float64)
+    else:
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        K, _, P = sigma.shape
+        sig_ptr, fld_ptr = host(sigma, np.float64), None
     grid = SlGrid(n, n, lo, hi, lo, hi)
-    ctrl = SlControls(K, P, host(sigma, np.float64),
+    ctrl = SlControls(K, P, sig_ptr,
                       host(b, np.float64) if b is not None else None,
-                      host(c, np.float64) if c is not None else None)
+                      host(c, np.float64) if c is not None else None, fld_ptr)
     G = G.contiguous()
     assert G.is_cuda and G.dtype == torch.float64 and G.shape[2:] == (n, n)
     nf, nq = G.shape[0], G.shape[1]
@@ -202,13 +209,14 @@ class Solver:
 
     def __init__(self, n: int, lo: float, hi: float, sigma: np.ndarray, phi: np.ndarray, G,
                  tau_kind, tau_rate, Psi=None, psi_kind=None, psi_rate=None, b=None, c=None,
-                 opts: Optional[SlOpts] = None, stream=None, **opt_kw):
+                 sigma_field=None, opts: Optional[SlOpts] = None, stream=None, **opt_kw):
         lib = load()
         self._lib = lib
         self._keep = []
         grid, ctrl, src = _describe(self._keep, n, lo, hi, sigma, phi, G, tau_kind, tau_rate, Psi,
-                                    psi_kind, psi_rate, b, c)
+                                    psi_kind, psi_rate, b, c, sigma_field)
         self.n, self.K, self.P = n, ctrl.K, ctrl.P
+        self.general = ctrl.sigma_field is not None
         self._G = self._keep[-2]
         self._Psi = self._keep[-1]
         self.opts = opts if opts is not None else default_opts(**opt_kw)
@@ -342,6 +350,22 @@ def _problem_args(prob, dev):
     args = (prob.n, prob.lo, prob.hi, prob.sigma, prob.phi, G,
             np.asarray(prob.tau_kind, dtype=np.int32), np.asarray(prob.tau_rate, dtype=np.float64))
     kw.update(b=prob.drift, c=prob.c)
+    if prob.sigma_fn is not None:
+        # x-dependent sigma: the library takes one field shared by all controls, and constant
+        # per-control drifts
+        x = prob.lo + prob.h * np.arange(prob.n, dtype=np.float64)
+        X1, X2 = np.meshgrid(x, x, indexing="xy")
+        field = prob.sigma_fn(0, X1, X2)
+        for k in range(1, prob.K):
+            if not np.array_equal(prob.sigma_fn(k, X1, X2), field):
+                raise ValueError("the library needs sigma(x) shared by all controls")
+        kw["sigma_field"] = field
+        if prob.drift_fn is not None:
+            b = np.stack([prob.drift_fn(k, X1, X2)[0, 0] for k in range(prob.K)])
+            for k in range(prob.K):
+                if not np.all(prob.drift_fn(k, X1, X2) == b[k]):
+                    raise ValueError("the library needs a constant drift per control")
+            kw["b"] = b
     return args, kw
 
 

@@ -20,7 +20,7 @@ constexpr int kAdjThreads = 256;
 constexpr int kScanChunk = 1024;
 
 __device__ __forceinline__ int fine_entry(const FineTab &tab, int k, int i1, int i2) {
-  return (k * tab.Q + class_q(i2, tab.n, tab.B)) * tab.Q + class_q(i1, tab.n, tab.B);
+  return fine_row_entry(tab, k, i1, i2);
 }
 
 // ----------------------------------------------------------------------------- CSR transpose

@@ -76,6 +76,13 @@ struct sl_hjb {
   double *d_phi = nullptr, *d_phimax = nullptr, *d_tau = nullptr, *d_tpsi = nullptr;
   double *d_od64 = nullptr;
   float *d_od32 = nullptr;
+  // general fine level (x-dependent diffusion): drift tables, per-row diffusion taps, and the
+  // per-row table assembled for the current policy (h->tab then describes the latter)
+  bool general = false;
+  FineTab dtab{};
+  GeneralArgs gen{};
+  GeneralOut gout{};
+  NodeTabHost nd;
   float *d_phi32 = nullptr;
   int halo = 0, SW = 0, SH = 0;
   // step state (full-grid FP64 vectors)
@@ -209,6 +216,20 @@ sl_status coef(sl_hjb *h, double t, double *Xext, cudaStream_t s) {
 
 // ---------------------------------------------------------------------- argmin
 sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_t s) {
+  if (h->general) {
+    CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+    launch_argmin_general(h->gen, h->dtab, h->dtab.c64, Xext, h->F, h->d_phi, h->nf, h->o.tie_rel,
+                          h->policy, h->d_changes, h->d_flags, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_changes, h->d_changes, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*h->h_flags & 1) return fail(h, SL_ENAN, "non-finite control value in the policy improvement");
+    if (changes) *changes = (long long)*h->h_changes;
+    h->have_policy = true;
+    return SL_OK;
+  }
   ArgminArgs a{};
   a.tab = h->tab;
   a.slin = h->d_slin;
@@ -269,7 +290,7 @@ CoarseLev<T> lev_view(sl_hjb *h, int l) {
 
 // Translation-invariant class stencils S_k^l (host, FP64), rebuilt when dt changes.
 sl_status build_class_tables(sl_hjb *h, double dt) {
-  const bool interior_exists = (h->n - 1 >= 2 * h->ft.B);
+  const bool interior_exists = !h->general && (h->n - 1 >= 2 * h->ft.B);
   std::vector<std::vector<double>> prev(h->K);
   int Rprev = h->ft.R0;
   if (interior_exists)
@@ -395,10 +416,14 @@ sl_status build_hierarchy_T(sl_hjb *h, double dt, cudaStream_t s) {
 }
 
 sl_status build_hierarchy(sl_hjb *h, double dt, cudaStream_t s) {
+  if (h->general) {  // the fine rows of the current policy and step size
+    launch_assemble_general(h->gen, h->dtab, h->policy, h->dtab.c64, dt, h->o.omega, h->SW, h->gout, s);
+    CK(cudaGetLastError());
+  }
   if (!h->class_valid || h->class_dt != dt) {
     sl_status st = build_class_tables(h, dt);
     if (st != SL_OK) return st;
-    launch_fine_od(h->tab, dt, h->o.omega, h->d_od64, h->d_od32, s);
+    if (!h->general) launch_fine_od(h->tab, dt, h->o.omega, h->d_od64, h->d_od32, s);
     CK(cudaGetLastError());
   }
   sl_status st = (h->o.precision == 0) ? build_hierarchy_T<double>(h, dt, s)
@@ -719,7 +744,8 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
   h->prev_dt = dt;
   if (st) st->steps += 1;
   for (int it = 1; it <= h->o.pi_max; ++it) {
-    const long long thresh = (long long)(h->o.rebuild_frac * double(h->m) * h->m);
+    // a general fine level re-assembles its rows on every policy change
+    const long long thresh = h->general ? 0 : (long long)(h->o.rebuild_frac * double(h->m) * h->m);
     if (!h->hier_valid || h->hier_dt != dt || h->changes_since_build > thresh) {
       double tb = now_ms();
       r = build_hierarchy(h, dt, s);
@@ -787,10 +813,12 @@ sl_status dgrow(sl_hjb *h, T **p, size_t *cap, size_t count) {
 
 sl_status ensure_adjoint_buffers(sl_hjb *h) {
   if (h->t_rowptr) return SL_OK;
-  if (double(h->ft.R0) * (h->n + 1) >= double(1 << 24))  // packed sort keys of the fine A^T
+  // the fine table in use: the class tables, or the per-row tables of a general level (whose
+  // rows hold diffusion and drift taps and reach farther than the drift tables alone)
+  if (double(h->cl[0].R) * (h->n + 1) >= double(1 << 24))  // packed sort keys of the fine A^T
     return fail(h, SL_EINVAL, "stencil reach too large for the transposed fine operator");
   const size_t M = size_t(h->m) * h->m, N = size_t(h->n) * h->n;
-  const size_t nnz = M * size_t(h->ft.tmax);  // every tap of every row at most once
+  const size_t nnz = M * size_t(h->tab.tmax);  // every tap of every row at most once
   AL(h->t_rowptr, M + 1);
   AL(h->t_cnt, M);
   AL(h->t_scan, 2 * ((M + 1023) / 1024) + 2);
@@ -815,7 +843,7 @@ sl_status ensure_adjoint_buffers(sl_hjb *h) {
 
 // Transposed operators of the current policy and step size (after build_hierarchy).
 sl_status build_transposed(sl_hjb *h, double dt, cudaStream_t s) {
-  launch_csrT_build(h->tab, h->d_off, h->policy, dt, h->ft.R0, h->t_cnt, h->t_scan, h->t_rowptr,
+  launch_csrT_build(h->tab, h->d_off, h->policy, dt, h->cl[0].R, h->t_cnt, h->t_scan, h->t_rowptr,
                     h->t_col, h->t_vtmp, h->t_v64, h->t_v32, h->t_d64, h->t_d32, s);
   for (int l = 1; l < h->L; ++l) {
     CoarseBuf &c = h->cl[l];
@@ -1057,7 +1085,8 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   const double hx = (g->x_hi - g->x_lo) / (g->nx - 1), hy = (g->y_hi - g->y_lo) / (g->ny - 1);
   if (!(hx > 0) || std::fabs(hx - hy) > 1e-12 * hx) return fail(h, SL_EINVAL, "cells must be square");
   if (c->K < 1 || c->K > 255) return fail(h, SL_EINVAL, "K must be in 1..255");
-  if (c->P < 1 || c->P > 4 || !c->sigma) return fail(h, SL_EINVAL, "P must be in 1..4 with sigma given");
+  if (c->P < 1 || c->P > 4 || (!c->sigma && !c->sigma_field))
+    return fail(h, SL_EINVAL, "P must be in 1..4 with sigma or sigma_field given");
   if (src->nf < 1 || src->nf > 4 || src->nq < 1 || !src->phi || !src->G_dev || !src->tau_kind || !src->tau_rate)
     return fail(h, SL_EINVAL, "source: need 1 <= nf <= 4, nq >= 1, phi, G, tau");
   if (src->npsi < 0 || (src->npsi > 0 && (!src->Psi_dev || !src->psi_kind || !src->psi_rate)))
@@ -1085,7 +1114,8 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   }
   h->cvec.assign(c->K, 0.0);
   if (c->c) h->cvec.assign(c->c, c->c + c->K);
-  h->sigma.assign(c->sigma, c->sigma + size_t(c->K) * 2 * c->P);
+  if (c->sigma) h->sigma.assign(c->sigma, c->sigma + size_t(c->K) * 2 * c->P);
+  h->general = c->sigma_field != nullptr;
   h->phimax.assign(h->nf, 0.0);
   for (int k = 0; k < h->K; ++k)
     for (int mm = 0; mm < h->nf; ++mm)
@@ -1113,12 +1143,19 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   CK(prepare_coarse_kernels());
   // stencil tables
   try {
-    h->ft = build_fine_tables(h->n, h->h, h->K, h->P, c->sigma, c->b, c->c);
+    if (h->general) {
+      // drift taps per (control, boundary class), diffusion taps per row
+      h->ft = build_fine_tables(h->n, h->h, h->K, 0, nullptr, c->b, c->c);
+      h->nd = build_node_tables(h->n, h->h, h->P, c->sigma_field);
+    } else {
+      h->ft = build_fine_tables(h->n, h->h, h->K, h->P, c->sigma, c->b, c->c);
+    }
   } catch (const std::exception &e) {
     return fail(h, SL_EINVAL, e.what());
   }
   const FineTabHost &ft = h->ft;
-  h->halo = std::max(1, ft.R0);
+  const int R0 = h->general ? std::max(ft.R0, h->nd.R0) : ft.R0;
+  h->halo = std::max(1, R0);
   h->SW = 32 + 2 * h->halo;
   h->SH = 8 + 2 * h->halo;
   if (size_t(h->SW) * (32 + 2 * h->halo) * sizeof(double) > 200 * 1024)
@@ -1170,6 +1207,37 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   AL(h->d_od64, size_t(h->K) * ft.Q * ft.Q);
   AL(h->d_od32, size_t(h->K) * ft.Q * ft.Q);
   t.od64 = h->d_od64; t.od32 = h->d_od32;
+  t.general = 0;
+  if (h->general) {
+    // the tables above hold the drift part; the fine level reads per-row entries
+    h->dtab = t;
+    const NodeTabHost &nd = h->nd;
+    const size_t M = size_t(h->m) * h->m;
+    std::vector<int32_t> ndoff(nd.dx.size());
+    for (size_t i = 0; i < ndoff.size(); ++i) ndoff[i] = (nd.dy[i] << 16) | (nd.dx[i] & 0xffff);
+    GeneralArgs &g = h->gen;
+    g.n = h->n;
+    g.nd_stride = nd.stride;
+    int32_t *p_off = nullptr;
+    double *p_w = nullptr, *p_W = nullptr;
+    uint8_t *p_nt = nullptr;
+    UP(p_off, ndoff);
+    UP(p_w, nd.w);
+    UP(p_nt, nd.nt);
+    UP(p_W, nd.W);
+    g.nd_off = p_off; g.nd_w = p_w; g.nd_nt = p_nt; g.nd_W = p_W;
+    g.dr_off = h->d_off;
+    GeneralOut &o = h->gout;
+    o.stride = nd.stride + ft.tmax;
+    const size_t ES = M * o.stride;
+    AL(o.off, ES); AL(o.lin, ES); AL(o.w64, ES); AL(o.w32, ES); AL(o.pk32, ES); AL(o.pk64, ES);
+    AL(o.nt, M); AL(o.W64, M); AL(o.W32, M); AL(o.ws64, M); AL(o.ws32, M); AL(o.od64, M); AL(o.od32, M);
+    t.general = 1;
+    t.tmax = o.stride;
+    t.lin = o.lin; t.w64 = o.w64; t.w32 = o.w32; t.nt = o.nt; t.W64 = o.W64; t.W32 = o.W32;
+    t.ws64 = o.ws64; t.ws32 = o.ws32; t.od64 = o.od64; t.od32 = o.od32; t.pk32 = o.pk32; t.pk64 = o.pk64;
+    h->d_off = o.off;  // Galerkin, coarsest and transposed builds read the assembled rows
+  }
   // vectors
   const size_t N = size_t(h->n) * h->n;
   AL(h->X, N);
@@ -1192,7 +1260,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
     AL(k.ph32, N); AL(k.sh32, N); AL(k.e32, N);
   }
   // multigrid levels
-  h->cl[0].R = ft.R0;
+  h->cl[0].R = R0;
   for (int l = 0; l < h->L; ++l) {
     CoarseBuf &cb = h->cl[l];
     const size_t Nl = size_t(cb.n) * cb.n;
@@ -1417,6 +1485,8 @@ sl_status sl_hjb_adjoint(sl_hjb *h, const double *w, double *dJ_dg, double *dJ_d
   if (!h || !w || !dJ_dg || nparam < 0 || nparam > kMaxParams) return SL_EINVAL;
   if (nparam > 0 && (!dsigma || !dJ_dtheta)) return SL_EINVAL;
   if (!h->rec_valid) return fail(h, SL_EINVAL, "sl_hjb_adjoint needs a preceding sl_hjb_solve_record");
+  if (nparam > 0 && h->general)
+    return fail(h, SL_EINVAL, "dJ/dtheta needs an x-independent sigma (sl_controls.sigma)");
   if (st) std::memset(st, 0, sizeof(*st));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   sl_status r = ensure_adjoint_buffers(h);

@@ -23,8 +23,9 @@ __device__ __forceinline__ int coarse_class_of(int level, const FineTab &tab, co
       const int i1 = 2 * I1 + a1, i2 = 2 * I2 + a2;
       int k;
       if (level == 1) {
-        const bool interior = (tab.n - 1 >= 2 * tab.B) && class_q(i1, tab.n, tab.B) == tab.B &&
-                              class_q(i2, tab.n, tab.B) == tab.B;
+        // rows of a general fine level (x-dependent diffusion) are all different
+        const bool interior = !tab.general && (tab.n - 1 >= 2 * tab.B) &&
+                              class_q(i1, tab.n, tab.B) == tab.B && class_q(i2, tab.n, tab.B) == tab.B;
         k = interior ? int(policy[(i2 - 1) * tab.m + (i1 - 1)]) : -1;
       } else {
         k = cls_prev[(i2 - 1) * (n_prev - 2) + (i1 - 1)];
@@ -136,7 +137,7 @@ __global__ void k_rap_explicit(int level, FineTab tab, const int32_t *__restrict
       const int i1 = 2 * I1 + a1, i2 = 2 * I2 + a2;
       if (level == 1) {
         const int k = policy[(i2 - 1) * tab.m + (i1 - 1)];
-        const int e = (k * tab.Q + class_q(i2, tab.n, tab.B)) * tab.Q + class_q(i1, tab.n, tab.B);
+        const int e = fine_row_entry(tab, k, i1, i2);
         const T W = tab_W<T>(tab)[e], c = tab_c<T>(tab)[k];
         rap_scatter<T>(win, R, I1, I2, i1, i2, ra * (T(1) + dt * (W - c)));
         const T *w = tab_w<T>(tab);
@@ -451,7 +452,7 @@ __global__ void k_coarsest_setup(int level, FineTab tab, const uint8_t *__restri
     };
     if (level == 0) {
       const int k = policy[r];
-      const int e = (k * tab.Q + class_q(i2, n, tab.B)) * tab.Q + class_q(i1, n, tab.B);
+      const int e = fine_row_entry(tab, k, i1, i2);
       put(0, 0, 1.0 + double(dt) * (double(tab_W<T>(tab)[e]) - double(tab_c<T>(tab)[k])));
       for (int t = 0; t < tab.nt[e]; ++t) {
         const int ix = e * tab.tmax + t;

@@ -67,7 +67,16 @@ struct FineTab {
   const float *od32;
   const int2 *pk32;       // [e*tmax + t] {staged-tile offset, fp32 weight bits}
   const longlong2 *pk64;  // [e*tmax + t] {staged-tile offset, fp64 weight bits}
+  int general;            // 1: x-dependent sigma; entry e = interior row, assembled per policy
 };
+
+// Table entry of row (i1, i2) whose control is k: the (control, boundary class) entry, or, on
+// a general fine level (x-dependent diffusion), the row's own entry, which holds the taps of
+// the row's current control.
+SL_HD int fine_row_entry(const FineTab &t, int k, int i1, int i2) {
+  if (t.general) return (i2 - 1) * t.m + (i1 - 1);
+  return (k * t.Q + class_q(i2, t.n, t.B)) * t.Q + class_q(i1, t.n, t.B);
+}
 
 
 

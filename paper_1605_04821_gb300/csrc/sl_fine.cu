@@ -379,13 +379,12 @@ __global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__r
   }
   const int i1 = 1 + blockIdx.x * 32 + tx;
   if (i1 > m) return;
-  const int q1 = class_q(i1, n, tab.B);
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int i2 = 1 + blockIdx.y * kOpRowsY + ty + 8 * r;
     if (i2 > m) continue;
     const int k = policy[(i2 - 1) * m + (i1 - 1)];
-    const int e = (k * tab.Q + class_q(i2, n, tab.B)) * tab.Q + q1;
+    const int e = fine_row_entry(tab, k, i1, i2);
     const int j = i2 * n + i1;
     if (OP == OP_JACOBI0) {
       y[j] = tab_od<T>(tab)[e] * b[j];
@@ -480,7 +479,7 @@ __global__ void __launch_bounds__(256) k_hjb_resid(FineTab tab, const uint8_t *_
   if (i1 > m || i2 > m) return;
   const int j = i2 * n + i1;
   const int k = policy[(i2 - 1) * m + (i1 - 1)];
-  const int e = (k * tab.Q + class_q(i2, n, tab.B)) * tab.Q + class_q(i1, n, tab.B);
+  const int e = fine_row_entry(tab, k, i1, i2);
   const size_t N = size_t(n) * n;
   double f = 0.0;
   for (int mm = 0; mm < nf; ++mm) f = fma(__ldg(phi + k * nf + mm), F[mm * N + j], f);

@@ -266,6 +266,47 @@ FineDTabHost build_fine_dtables(const FineTabHost &t, double h, int P, const dou
   return d;
 }
 
+NodeTabHost build_node_tables(int n, double h, int P, const double *field) {
+  NodeTabHost t;
+  const int m = n - 2;
+  const double sqh = std::sqrt(h);
+  t.stride = 4 * 2 * P;
+  t.dx.assign(size_t(m) * m * t.stride, 0);
+  t.dy.assign(t.dx.size(), 0);
+  t.w.assign(t.dx.size(), 0.0);
+  t.nt.assign(size_t(m) * m, 0);
+  t.W.assign(size_t(m) * m, 0.0);
+  for (int i2 = 1; i2 <= m; ++i2)
+    for (int i1 = 1; i1 <= m; ++i1) {
+      const size_t I = size_t(i2 - 1) * m + (i1 - 1);
+      const double *sg = field + (size_t(i2) * n + i1) * 2 * P;
+      TapMap taps;
+      double W = 0.0;
+      for (int p = 0; p < P; ++p) {
+        const double s1 = sg[0 * P + p] / sqh, s2 = sg[1 * P + p] / sqh;
+        Endpoint ep = truncate_endpoint(i1, i2, s1, s2, n);
+        Endpoint em = truncate_endpoint(i1, i2, -s1, -s2, n);
+        const double A = 2.0 / (ep.mu * ep.mu + ep.mu * em.mu);
+        const double Bw = 2.0 / (em.mu * em.mu + em.mu * ep.mu);
+        add_bilinear(taps, i1, i2, ep.z1, ep.z2, n, A / (2.0 * h));
+        add_bilinear(taps, i1, i2, em.z1, em.z2, n, Bw / (2.0 * h));
+        W += (A + Bw) / (2.0 * h);
+      }
+      if (int(taps.size()) > t.stride) throw std::runtime_error("node stencil table overflow");
+      int slot = 0;
+      for (const auto &kv : taps) {
+        t.dy[I * t.stride + slot] = kv.first.first;
+        t.dx[I * t.stride + slot] = kv.first.second;
+        t.w[I * t.stride + slot] = kv.second;
+        t.R0 = std::max(t.R0, std::max(std::abs(kv.first.first), std::abs(kv.first.second)));
+        ++slot;
+      }
+      t.nt[I] = uint8_t(slot);
+      t.W[I] = W;
+    }
+  return t;
+}
+
 std::vector<double> fine_interior_window(const FineTabHost &t, int k, double dt) {
   const int R = t.R0, Wd = 2 * R + 1;
   std::vector<double> win(size_t(Wd) * Wd, 0.0);

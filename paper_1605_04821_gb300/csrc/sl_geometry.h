@@ -24,6 +24,19 @@ struct FineTabHost {
 FineTabHost build_fine_tables(int n, double h, int K, int P, const double *sigma,
                               const double *b, const double *c);
 
+// Diffusion taps of every interior row for an x-dependent sigma shared by all controls:
+// field[((i2*n + i1)*2 + d)*P + p] is component d of column p at node (i1, i2).  Row
+// I = (i2-1)(n-2) + (i1-1) has nt[I] taps (dy, dx, w) at [I*stride + t] and the weight sum
+// W[I] = sum_p (A_p + B_p)/(2h) (Proposition 2.2, Eq. Lhat); R0 is the longest tap.
+struct NodeTabHost {
+  int stride = 0, R0 = 0;
+  std::vector<int32_t> dx, dy;
+  std::vector<double> w;
+  std::vector<uint8_t> nt;
+  std::vector<double> W;
+};
+NodeTabHost build_node_tables(int n, double h, int P, const double *field);
+
 // Derivative of every fine table entry with respect to a scalar parameter theta of the
 // diffusion coefficients (dsig = d sigma / d theta, laid out like sigma): taps (dy, dx, dw) of
 // d(L^k)/d theta with dw = d w_t / d theta, and dW = d W / d theta, so that

@@ -102,6 +102,35 @@ void launch_coarsest_setup(int level, const FineTab &tab, const uint8_t *policy,
 template <typename T>
 void launch_coarsest_apply(const T *Ainv, int n, const T *b, T *x, cudaStream_t s, int trans = 0);
 
+// ------------------------------------------------------------------ general fine level
+// x-dependent diffusion shared by all controls (per-row taps) plus per-control drift taps
+// from (control, boundary class) tables; see sl_general.cu.
+struct GeneralArgs {
+  int n, nd_stride;
+  const int32_t *nd_off;   // [I*nd_stride + t] packed (dy << 16) | (dx & 0xffff) of row I's diffusion taps
+  const double *nd_w;      // [I*nd_stride + t]
+  const uint8_t *nd_nt;    // [I]
+  const double *nd_W;      // [I] sum_p (A_p + B_p)/(2h) of the diffusion part
+  const int32_t *dr_off;   // drift tables: [ed*tmax + t] packed offsets (weights in the FineTab)
+};
+struct GeneralOut {        // the assembled fine table (entry = interior row)
+  int stride;
+  int32_t *off, *lin;
+  double *w64;
+  float *w32;
+  int2 *pk32;
+  longlong2 *pk64;
+  uint8_t *nt;
+  double *W64, *ws64, *od64;
+  float *W32, *ws32, *od32;
+};
+void launch_assemble_general(const GeneralArgs &g, const FineTab &dtab, const uint8_t *policy,
+                             const double *c64, double dt, double omega, int SW, const GeneralOut &o,
+                             cudaStream_t s);
+void launch_argmin_general(const GeneralArgs &g, const FineTab &dtab, const double *c64, const double *X,
+                           const double *F, const double *phi, int nf, double tie_rel, uint8_t *policy,
+                           unsigned long long *changes, int *flags, cudaStream_t s);
+
 // ------------------------------------------------------------------ adjoint (transposed solves)
 // Explicit A^T of the fine level: row J (interior index of column j of A) lists the sources i
 // with A[i, j] != 0, i != j, sorted by i; the diagonal is stored apart.

@@ -303,8 +303,15 @@ def problem_A(n: int, n_alpha: int = 40, n_steps: int = 1) -> Problem:
         return u
 
     g = exact(0.0)
+    # The same source in the separable form (phi = 1, tau = (1, t)): with
+    # Q = sqrt(C1^2 S2^2 + S1^2 C2^2) - 2 sin(x1+x2) cos(x1+x2) C1 C2,
+    # f = (0.5 S1 S2 + 1.5 Q) * 1 - (S1 S2 + Q) * t.  The oracle evaluates f_fn.
+    Q = np.sqrt(C1 ** 2 * S2 ** 2 + S1 ** 2 * C2 ** 2) - 2.0 * sp * cp * C1 * C2
+    G = np.zeros((1, 2, n, n))
+    G[0, 0] = 0.5 * S1 * S2 + 1.5 * Q
+    G[0, 1] = -(S1 * S2 + Q)
     p = Problem(name=f"problemA{n}", n=n, lo=lo, hi=hi, T=0.5, n_steps=n_steps, sigma=None,
-                phi=None, G=None, tau_kind=None, tau_rate=None, g=g,
+                phi=np.ones((K, 1)), G=G, tau_kind=[TAU_ONE, TAU_LINEAR], tau_rate=[0.0, 0.0], g=g,
                 psi_fn=lambda t: np.zeros((n, n)), exact=exact, sigma_fn=sigma_fn,
                 drift_fn=drift_fn, f_fn=f_fn)
     p._K = K
@@ -336,6 +343,14 @@ def problem_B(n: int, n_alpha: int = 40, n_steps: int = 1) -> Problem:
         u[0, :] = u[-1, :] = u[:, 0] = u[:, -1] = 0.0
         return u
 
+    # The same source in the separable form f^k = sum_m phi[k, m] sum_q tau_q(t) G[m, q] with
+    # phi[k] = (1, alpha_1 alpha_2) and tau = (1, t):
+    #   (1 - t) S1 S2 = S1 S2 * 1 - S1 S2 * t,  -2 (2 - t) C1 C2 = -4 C1 C2 * 1 + 2 C1 C2 * t.
+    # The oracle evaluates f_fn (the printed form); the library reads G.
+    phi = np.stack([np.ones(K), alphas[:, 0] * alphas[:, 1]], axis=1)
+    G = np.zeros((2, 2, n, n))
+    G[0, 0], G[0, 1] = S1 * S2, -S1 * S2
+    G[1, 0], G[1, 1] = -4.0 * C1 * C2, 2.0 * C1 * C2
     return Problem(name=f"problemB{n}", n=n, lo=lo, hi=hi, T=0.5, n_steps=n_steps, sigma=sig,
-                   phi=None, G=None, tau_kind=None, tau_rate=None, g=exact(0.0),
-                   psi_fn=lambda t: np.zeros((n, n)), exact=exact, f_fn=f_fn)
+                   phi=phi, G=G, tau_kind=[TAU_ONE, TAU_LINEAR], tau_rate=[0.0, 0.0],
+                   g=exact(0.0), psi_fn=lambda t: np.zeros((n, n)), exact=exact, f_fn=f_fn)
