@@ -25,14 +25,19 @@ Coarsening (one level = two pairwise passes, aggregates of at most four unknowns
     piecewise constant (P_iI = 1 for i in aggregate I), the coarse matrix is the Galerkin
     product P^T A P.  The second pass repeats the matching on that coarse matrix, and the
     level's aggregates are the unions.
-Cycle (K-cycle, damped Jacobi, GCR acceleration on every coarse level):
+Cycle (K-cycle, damped Jacobi, GCR acceleration of the coarse corrections):
   kcycle(l, b): x = omega D^-1 b, nu1 - 1 further sweeps x += omega D^-1 (b - A x);
-                r = b - A x; e = gcr2(l + 1, P^T r) (an exact solve on the coarsest level);
+                r = b - A x; e = gcr(l + 1, P^T r) (an exact solve on the coarsest level);
                 x += P e; nu2 sweeps; return x.
-  gcr2(l, r):  v1 = kcycle(l, r); w1 = A v1; a1 = (w1.r)/(w1.w1); e = a1 v1; r2 = r - a1 w1;
-               if ||r2|| <= t ||r|| (t = 0.25) return e;   (a zero denominator gives a zero step)
+  gcr(l, r):   v1 = kcycle(l, r); w1 = A v1; a1 = (w1.r)/(w1.w1); e = a1 v1;
+               on levels l <= k_levels a second step follows: r2 = r - a1 w1;
                v2 = kcycle(l, r2); w2 = A v2; g = (w2.w1)/(w1.w1); w2 -= g w1; v2 -= g v1;
-               a2 = (w2.r2)/(w2.w2); return e + a2 v2.
+               a2 = (w2.r2)/(w2.w2); e += a2 v2.   (a zero denominator gives a zero step)
+The number of GCR steps per level is fixed (two on the first k_levels coarse levels, one
+below) instead of being decided by the size of the first step's residual: a data-dependent
+exit would have to be decided on the device before launching the second step's subtree, and
+with two steps on every level the launches grow as 2^l.  With k_levels = 2 the levels below
+the second are visited four times per cycle.
 """
 from __future__ import annotations
 
@@ -45,7 +50,7 @@ import scipy.linalg as sla
 
 BETA = 0.25
 ROUNDS = 8
-GCR_T = 0.25
+K_LEVELS = 2
 
 
 def strength(A: sp.csr_matrix) -> sp.csr_matrix:
@@ -165,7 +170,7 @@ def build(A: sp.csr_matrix, coarsest: int = 256, max_levels: int = 16) -> AmgHie
 
 
 def kcycle(H: AmgHierarchy, l: int, b: np.ndarray, nu1: int = 1, nu2: int = 1,
-           omega: float = 0.8) -> np.ndarray:
+           omega: float = 0.8, k_levels: int = K_LEVELS) -> np.ndarray:
     A = H.A[l]
     if l == len(H.A) - 1:
         return sla.solve(A.toarray(), b)
@@ -174,26 +179,27 @@ def kcycle(H: AmgHierarchy, l: int, b: np.ndarray, nu1: int = 1, nu2: int = 1,
     for _ in range(nu1 - 1):
         x = x + omega * (b - A @ x) / d
     r = b - A @ x
-    e = gcr2(H, l + 1, H.P[l].T @ r, nu1, nu2, omega)
+    e = gcr(H, l + 1, H.P[l].T @ r, nu1, nu2, omega, k_levels)
     x = x + H.P[l] @ e
     for _ in range(nu2):
         x = x + omega * (b - A @ x) / d
     return x
 
 
-def gcr2(H: AmgHierarchy, l: int, r: np.ndarray, nu1: int, nu2: int, omega: float) -> np.ndarray:
+def gcr(H: AmgHierarchy, l: int, r: np.ndarray, nu1: int, nu2: int, omega: float,
+        k_levels: int = K_LEVELS) -> np.ndarray:
     A = H.A[l]
     if l == len(H.A) - 1:
         return sla.solve(A.toarray(), r)
-    v1 = kcycle(H, l, r, nu1, nu2, omega)
+    v1 = kcycle(H, l, r, nu1, nu2, omega, k_levels)
     w1 = A @ v1
     ww = w1 @ w1
     a1 = (w1 @ r) / ww if ww > 0.0 else 0.0     # r = 0 gives e = 0
     e = a1 * v1
-    r2 = r - a1 * w1
-    if np.linalg.norm(r2) <= GCR_T * np.linalg.norm(r):
+    if l > k_levels:
         return e
-    v2 = kcycle(H, l, r2, nu1, nu2, omega)
+    r2 = r - a1 * w1
+    v2 = kcycle(H, l, r2, nu1, nu2, omega, k_levels)
     w2 = A @ v2
     g = (w2 @ w1) / ww if ww > 0.0 else 0.0
     w2 = w2 - g * w1

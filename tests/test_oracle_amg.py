@@ -8,8 +8,9 @@
 * Galerkin: row sums of P^T A P are the aggregated row sums of A (P 1 = 1), and a symmetric A
   gives a symmetric coarse matrix.
 * Cycle: on a two-level hierarchy the K-cycle equals the explicit two-grid operator
-  (pre-smoothing, exact coarse correction, post-smoothing) written with dense matrices; the
-  coarse GCR(2) step leaves a residual orthogonal to both search directions; as a BiCGSTAB
+  (pre-smoothing, exact coarse correction, post-smoothing) written with dense matrices; a
+  two-step coarse GCR leaves a residual orthogonal to both search directions, a one-step GCR
+  (levels below k_levels) is the minimal-residual scaling of one cycle; as a BiCGSTAB
   preconditioner it converges in a mesh-independent number of iterations on the 2-D
   Laplacian.
 """
@@ -158,17 +159,16 @@ def test_edge_hash_is_symmetric():
         assert amg.edge_hash(i, j) == amg.edge_hash(j, i)
 
 
-def test_coarse_gcr_two_steps_minimise_over_both_directions(monkeypatch):
-    """With the early exit disabled, GCR(2) leaves a residual orthogonal to A v1 and to the
+def test_coarse_gcr_two_steps_minimise_over_both_directions():
+    """On a level with two steps, GCR leaves a residual orthogonal to A v1 and to the
     orthogonalised A v2 (the minimal residual over span{v1, v2})."""
-    monkeypatch.setattr(amg, "GCR_T", 0.0)
     A = _lap2d(40)
     H = amg.build(A)
     assert len(H.A) >= 3
     l = 1
     Al = H.A[l]
     r = np.random.default_rng(2).standard_normal(Al.shape[0])
-    e = amg.gcr2(H, l, r, 1, 1, 0.8)
+    e = amg.gcr(H, l, r, 1, 1, 0.8)
     v1 = amg.kcycle(H, l, r)
     w1 = Al @ v1
     a1 = (w1 @ r) / (w1 @ w1)
@@ -181,18 +181,27 @@ def test_coarse_gcr_two_steps_minimise_over_both_directions(monkeypatch):
     assert np.linalg.norm(res) < np.linalg.norm(r2)
 
 
-def test_coarse_gcr_stops_after_one_step_when_it_suffices():
-    A = _lap2d(40)
-    H = amg.build(A)
-    l = len(H.A) - 2            # its K-cycle ends in an exact solve: one step reduces a lot
+def test_coarse_gcr_below_k_levels_takes_one_step():
+    A = _lap2d(64)
+    H = amg.build(A, coarsest=16)
+    assert len(H.A) >= amg.K_LEVELS + 3
+    l = amg.K_LEVELS + 1
     Al = H.A[l]
     r = np.random.default_rng(4).standard_normal(Al.shape[0])
     v1 = amg.kcycle(H, l, r)
     w1 = Al @ v1
-    a1 = (w1 @ r) / (w1 @ w1)
-    assert np.linalg.norm(r - a1 * w1) <= amg.GCR_T * np.linalg.norm(r)
-    e = amg.gcr2(H, l, r, 1, 1, 0.8)
-    assert np.array_equal(e, a1 * v1)
+    e = amg.gcr(H, l, r, 1, 1, 0.8)
+    assert np.array_equal(e, (w1 @ r) / (w1 @ w1) * v1)
+    # and the residual after one step is orthogonal to A v1
+    res = r - Al @ e
+    assert abs(res @ w1) <= 1e-10 * np.linalg.norm(res) * np.linalg.norm(w1)
+    # level k_levels itself still takes two steps
+    lk = amg.K_LEVELS
+    rk = np.random.default_rng(6).standard_normal(H.A[lk].shape[0])
+    vk = amg.kcycle(H, lk, rk)
+    wk = H.A[lk] @ vk
+    ek = amg.gcr(H, lk, rk, 1, 1, 0.8)
+    assert np.max(np.abs(ek - (wk @ rk) / (wk @ wk) * vk)) > 1e-6 * np.abs(ek).max()
 
 
 def test_mesh_independent_iterations_on_the_laplacian():
