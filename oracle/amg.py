@@ -9,9 +9,13 @@ Notay's aggregation papers that it cites).  The paper gives no algorithm listing
 restates the published scheme in the following form, which the GPU path implements exactly:
 
 Coarsening (one level = two pairwise passes, aggregates of at most four unknowns):
-  * strength of the coupling i-j: s_ij = -(a_ij + a_ji) / 2 over the off-diagonal entries of
-    row i (a_ji = 0 when row j has no entry in column i); j is a strong neighbour of i when
-    s_ij > 0 and s_ij >= beta * max_k s_ik, beta = 0.25;
+  * strength of the coupling i-j: the off-diagonal entries of the symmetric part,
+    s_ij = -(a_ij + a_ji) / 2, on the union of the patterns of A and A^T (zero entries
+    dropped).  The paper points to A + A^T as the matrix that carries the aggregation
+    theory's assumptions for non-symmetric M-matrices (Section 3.4), and the union pattern
+    matters: with far-reaching stencils whose direction depends on x (Problem A) a_ij != 0
+    rarely comes with a_ji != 0, and a row-only pattern leaves almost nothing to pair.
+    j is a strong neighbour of i when s_ij > 0 and s_ij >= beta * max_k s_ik, beta = 0.25;
   * pairwise matching in rounds: every unmatched unknown proposes its strong unmatched
     neighbour that is largest in the order of the edge keys (s_ij, h(i, j), -j), where
     h(i, j) = fmix32(min(i, j) XOR fmix32(max(i, j))) and fmix32 is the 32-bit finalizer of
@@ -54,21 +58,13 @@ K_LEVELS = 2
 
 
 def strength(A: sp.csr_matrix) -> sp.csr_matrix:
-    """s_ij = -(a_ij + a_ji) / 2 on the off-diagonal pattern of A (row i's entries only)."""
+    """Off-diagonal part of -(A + A^T) / 2 on the union pattern, zero entries dropped."""
     A = A.tocsr()
-    At = A.T.tocsr()
-    rows, cols = [], []
-    vals = []
-    for i in range(A.shape[0]):
-        for p in range(A.indptr[i], A.indptr[i + 1]):
-            j = A.indices[p]
-            if j == i:
-                continue
-            aji = At[i, j]  # (A^T)_{ij} = a_ji, 0 when row j has no entry in column i
-            rows.append(i)
-            cols.append(j)
-            vals.append(-(A.data[p] + aji) / 2.0)
-    return sp.csr_matrix((vals, (rows, cols)), shape=A.shape)
+    S = (-(A + A.T) / 2.0).tocsr()
+    S.setdiag(0.0)
+    S.eliminate_zeros()
+    S.sort_indices()
+    return S
 
 
 def fmix32(x: int) -> int:

@@ -35,6 +35,19 @@ def _lisl(heavy, seed=0):
     return A.tocsr()
 
 
+def test_union_pattern_coarsens_far_reaching_directional_stencils():
+    """Problem A (x-dependent diffusion direction, offsets of about 3.6 cells at 41 nodes):
+    couplings are rarely mutual, yet the symmetric part pairs most unknowns, so every level
+    has at most half the unknowns of the one above."""
+    p = W.problem_A(41)
+    r = lisl.howard_step(p, p.g, p.T, p.T)
+    A, _ = lisl.assemble(p, r.policy, p.g, p.T, p.T)
+    H = amg.build(A.tocsr())
+    sizes = [a.shape[0] for a in H.A]
+    assert sizes[-1] <= 256
+    assert all(b <= a // 2 for a, b in zip(sizes, sizes[1:])), sizes
+
+
 def test_fmix32_is_murmur3_finalizer():
     assert amg.fmix32(0) == 0
     assert amg.fmix32(1) == 0x514E28B7
