@@ -124,6 +124,14 @@ typedef struct {
   int extrapolate;      /* 1: when a step continues the previous one (same dt, t = t_prev + dt)
                            its first linear solve starts from 2 U^{n-1} - U^{n-2}; Howard's stop
                            test still measures against U^{n-1}.  0: start from U^{n-1}. */
+  int precond;          /* BiCGSTAB preconditioner.  0: the geometric V-cycle (Section 3.3).
+                           1: aggregation AMG with a K-cycle (the aggregation multigrid the paper
+                           recommends in Section 3.4): two pairwise-matching passes per level
+                           (aggregates of at most four unknowns, Galerkin P^T A P), damped Jacobi
+                           (nu1, nu2, omega), GCR-accelerated coarse corrections, dense coarsest
+                           solve.  The V-cycle entry points and sl_hjb_adjoint need precond 0. */
+  int amg_k_levels;     /* precond 1: coarse levels 1..amg_k_levels take two GCR steps, deeper
+                           levels one */
 } sl_opts;
 
 typedef struct {
@@ -141,7 +149,7 @@ typedef struct {
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
  * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0, use_graphs 1, coarse_tail_rows -1,
- * extrapolate 1. */
+ * extrapolate 1, precond 0, amg_k_levels 2. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every
@@ -210,6 +218,27 @@ sl_status sl_hjb_adjoint(sl_hjb *h, const double *w_dev, double *dJ_dg_dev, doub
 
 const char *sl_hjb_last_error(const sl_hjb *h);
 void sl_hjb_destroy(sl_hjb *h);
+
+/* ---- Aggregation AMG on a given matrix (the preconditioner of precond = 1, standalone) ----
+ * Builds the aggregation hierarchy of an n x n matrix given in CSR form (host arrays:
+ * rowptr[n+1], col[nnz] sorted ascending within each row, no repeated column, a diagonal entry
+ * in every row; val[nnz] FP64) with opts->nu1, nu2, omega and amg_k_levels, exactly as the
+ * solver does for its step matrices.  SL_EINVAL for a malformed matrix or when the coarsening
+ * stops above 256 unknowns. */
+typedef struct sl_amg sl_amg;
+sl_status sl_amg_create(sl_amg **a, int n, const int *rowptr, const int *col, const double *val,
+                        const sl_opts *opts);
+int sl_amg_num_levels(const sl_amg *a);
+/* Level `level` (0 = the given matrix): unknowns *n, entries *nnz, and, for non-NULL host
+ * arrays, agg[n] = the level-(level+1) unknown of each unknown (levels below the coarsest), and
+ * the level's matrix (rowptr[n+1], col[nnz], val[nnz]).  Synchronises. */
+sl_status sl_amg_level(const sl_amg *a, int level, int *n, long long *nnz, int *agg, int *rowptr,
+                       int *col, double *val);
+/* x = one K-cycle applied to b (device vectors of n entries, FP64 for precision 0, FP32 for
+ * precision 1).  Stream-ordered; no host synchronisation. */
+sl_status sl_amg_apply(sl_amg *a, int precision, const void *b_dev, void *x_dev, void *stream);
+const char *sl_amg_last_error(const sl_amg *a);
+void sl_amg_destroy(sl_amg *a);
 
 /* Forgets the march state of the handle: the current policy (the next step starts from an
  * improvement on its U^{n-1}, as the first step of a new handle does), the previous step used

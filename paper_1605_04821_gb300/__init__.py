@@ -28,7 +28,8 @@ EXPORTED = ["sl_opts_default", "sl_hjb_create", "sl_hjb_step", "sl_hjb_solve",
             "sl_hjb_level_info", "sl_hjb_num_levels", "sl_launch_count",
             "sl_hjb_vcycle_noalloc", "sl_hjb_solve_record", "sl_hjb_adjoint", "sl_hjb_reset",
             "sl_batch_create", "sl_batch_run", "sl_batch_worker_of", "sl_batch_plan",
-            "sl_batch_last_error", "sl_batch_destroy"]
+            "sl_batch_last_error", "sl_batch_destroy", "sl_amg_create", "sl_amg_num_levels",
+            "sl_amg_level", "sl_amg_apply", "sl_amg_last_error", "sl_amg_destroy"]
 
 
 class SlGrid(ctypes.Structure):
@@ -55,7 +56,7 @@ class SlOpts(ctypes.Structure):
                 ("pi_tol", ctypes.c_double), ("pi_max", ctypes.c_int), ("tie_rel", ctypes.c_double),
                 ("argmin_screen", ctypes.c_int), ("rebuild_frac", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("coarse_tail_rows", ctypes.c_int),
-                ("extrapolate", ctypes.c_int)]
+                ("extrapolate", ctypes.c_int), ("precond", ctypes.c_int), ("amg_k_levels", ctypes.c_int)]
 
 
 class SlInstance(ctypes.Structure):
@@ -117,6 +118,12 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "sl_batch_plan": (i, [i, vp, i, vp]),
         "sl_batch_last_error": (ctypes.c_char_p, [vp]),
         "sl_batch_destroy": (None, [vp]),
+        "sl_amg_create": (i, [ctypes.POINTER(vp), i, vp, vp, vp, ctypes.POINTER(SlOpts)]),
+        "sl_amg_num_levels": (i, [vp]),
+        "sl_amg_level": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ll), vp, vp, vp, vp]),
+        "sl_amg_apply": (i, [vp, i, vp, vp, vp]),
+        "sl_amg_last_error": (ctypes.c_char_p, [vp]),
+        "sl_amg_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -438,6 +445,69 @@ def lpt_plan(costs, bins: int):
     if st != SL_OK:
         raise SLError(st, "sl_batch_plan: bad arguments")
     return out
+
+
+class Amg:
+    """sl_amg: the aggregation hierarchy of a given CSR matrix (scipy.sparse) and its K-cycle."""
+
+    def __init__(self, A, **opt_kw):
+        import scipy.sparse as sp
+        lib = load()
+        self._lib = lib
+        A = sp.csr_matrix(A)
+        A.sort_indices()
+        A.sum_duplicates()
+        self.n = A.shape[0]
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
+        ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+        va = np.ascontiguousarray(A.data, dtype=np.float64)
+        opts = default_opts(**opt_kw)
+        a = ctypes.c_void_p()
+        st = lib.sl_amg_create(ctypes.byref(a), self.n, rp.ctypes.data_as(ctypes.c_void_p),
+                               ci.ctypes.data_as(ctypes.c_void_p), va.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.byref(opts))
+        if st != SL_OK:
+            raise SLError(st, "sl_amg_create failed (see stderr)")
+        self.a = a
+
+    def num_levels(self) -> int:
+        return int(self._lib.sl_amg_num_levels(self.a))
+
+    def level(self, l: int):
+        """(agg or None, scipy CSR matrix) of level l."""
+        import scipy.sparse as sp
+        n = ctypes.c_int(0)
+        nnz = ctypes.c_longlong(0)
+        self._lib.sl_amg_level(self.a, l, ctypes.byref(n), ctypes.byref(nnz), None, None, None, None)
+        agg = np.zeros(n.value, dtype=np.int32) if l < self.num_levels() - 1 else None
+        rp = np.zeros(n.value + 1, dtype=np.int32)
+        ci = np.zeros(nnz.value, dtype=np.int32)
+        va = np.zeros(nnz.value, dtype=np.float64)
+        st = self._lib.sl_amg_level(self.a, l, ctypes.byref(n), ctypes.byref(nnz),
+                                    agg.ctypes.data_as(ctypes.c_void_p) if agg is not None else None,
+                                    rp.ctypes.data_as(ctypes.c_void_p), ci.ctypes.data_as(ctypes.c_void_p),
+                                    va.ctypes.data_as(ctypes.c_void_p))
+        if st != SL_OK:
+            raise SLError(st, "sl_amg_level failed")
+        return agg, sp.csr_matrix((va, ci, rp), shape=(n.value, n.value))
+
+    def apply(self, b, x, stream=None):
+        import torch
+        prec = 0 if b.dtype == torch.float64 else 1
+        st = self._lib.sl_amg_apply(self.a, prec, _ptr(b), _ptr(x), _stream(stream))
+        if st != SL_OK:
+            raise SLError(st, self._lib.sl_amg_last_error(self.a).decode())
+
+    def close(self):
+        if getattr(self, "a", None):
+            self._lib.sl_amg_destroy(self.a)
+            self.a = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def instance_cost(prob) -> float:

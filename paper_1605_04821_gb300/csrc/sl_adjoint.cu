@@ -101,6 +101,15 @@ __global__ void __launch_bounds__(kScanChunk) k_scan_apply(const int *__restrict
   if (i == M - 1) rowptr[M] = chunk_off[blockIdx.x] + ex + v;
 }
 
+// out[0..n] = exclusive prefix sums of in[0..n-1] (out[n] = total); scratch: 2 ceil(n/1024) ints.
+void launch_exclusive_scan(const int *in, int n, int32_t *out, int *scratch, cudaStream_t s) {
+  const int nchunks = (n + kScanChunk - 1) / kScanChunk;
+  note_launch(3);
+  k_scan_chunk_sums<<<nchunks, kScanChunk, 0, s>>>(in, n, scratch);
+  k_scan_chunk_offsets<<<1, kScanChunk, 0, s>>>(scratch, nchunks, scratch + nchunks);
+  k_scan_apply<<<nchunks, kScanChunk, 0, s>>>(in, n, scratch + nchunks, out);
+}
+
 // Scatters the entries A[i, j] (i = source row) into row j of A^T and writes the diagonal.
 __global__ void __launch_bounds__(kAdjThreads) k_csrT_fill(FineTab tab, const int32_t *__restrict__ off,
                                                             const uint8_t *__restrict__ policy, double dt,

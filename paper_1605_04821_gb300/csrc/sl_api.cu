@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/sl_hjb.h"
+#include "sl_amg.h"
 #include "sl_geometry.h"
 #include "sl_launch.h"
 
@@ -46,6 +47,7 @@ struct IterGraph {  // one captured BiCGSTAB iteration
   cudaGraphExec_t exec = nullptr;
   double dt = -1.0;
   long long kernels = 0;
+  long long gen = -1;  // AMG hierarchy generation it was captured with
 };
 
 struct KBuf {  // BiCGSTAB vectors on the finest level
@@ -134,6 +136,8 @@ struct sl_hjb {
   int rec_N = 0, rec_k = 0;
   double rec_t0 = 0.0, rec_dt = 0.0;
   bool rec_valid = false;
+  AmgEngine amg;                               // precond 1
+  long long amg_gen = 0;                       // bumped by every AMG setup (its sizes change)
   std::vector<void *> allocs;
   std::string err;
   sl_status sticky = SL_OK;
@@ -420,6 +424,19 @@ sl_status build_hierarchy(sl_hjb *h, double dt, cudaStream_t s) {
     launch_assemble_general(h->gen, h->dtab, h->policy, h->dtab.c64, dt, h->o.omega, h->SW, h->gout, s);
     CK(cudaGetLastError());
   }
+  if (h->o.precond == 1) {  // aggregation AMG on the assembled step matrix
+    cudaError_t e = amg_level0_from_tables(h->amg, h->tab, h->d_off, h->policy, dt, s);
+    if (e == cudaSuccess) e = amg_setup(h->amg, s);
+    if (e != cudaSuccess)
+      return fail(h, e == cudaErrorInvalidValue && !h->amg.err_msg.empty() ? SL_EINVAL : SL_ECUDA,
+                  h->amg.err_msg.empty() ? std::string("AMG setup: ") + cudaGetErrorString(e) : h->amg.err_msg);
+    h->hier_valid = true;
+    h->hier_dt = dt;
+    h->changes_since_build = 0;
+    // level sizes and buffers may have changed: captured iterations must be captured again
+    ++h->amg_gen;
+    return SL_OK;
+  }
   if (!h->class_valid || h->class_dt != dt) {
     sl_status st = build_class_tables(h, dt);
     if (st != SL_OK) return st;
@@ -529,6 +546,22 @@ sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) 
   return SL_OK;
 }
 
+// x = M^{-1} b on the finest level: the V-cycle, or the aggregation K-cycle (precond 1) on the
+// interior unknowns gathered from b and scattered back into x.
+template <typename T>
+sl_status precond(sl_hjb *h, double dt, const T *b, T *x, cudaStream_t s) {
+  if (h->o.precond == 1) {
+    AmgLevel &L0 = h->amg.lev[0];
+    T *cb = pick<T>(L0.vec64[AV_B], L0.vec32[AV_B]), *cx = pick<T>(L0.vec64[AV_X], L0.vec32[AV_X]);
+    amg_full_to_compact<T>(h->n, b, cb, s);
+    amg_cycle<T>(h->amg, cb, cx, s);
+    amg_compact_to_full<T>(h->n, cx, x, s);
+    CK(cudaGetLastError());
+    return SL_OK;
+  }
+  return vcycle<T>(h, 0, dt, b, x, s);
+}
+
 // ---------------------------------------------------------------------- BiCGSTAB
 // Right-preconditioned BiCGSTAB for A e = r0 with x += e accumulated in place (x may be FP64
 // while the Krylov vectors are FP32: TX / T).  On entry r holds the initial residual and S
@@ -540,12 +573,12 @@ sl_status issue_iteration(sl_hjb *h, double dt, TX *x, T *r, T *rh, T *p, T *v, 
                           T *sh, BicgScalars *S, cudaStream_t s) {
   const size_t N = NN(h, 0);
   launch_bicg_p<T>(p, r, v, N, 0, S, s);
-  sl_status st = vcycle<T>(h, 0, dt, p, ph, s);
+  sl_status st = precond<T>(h, dt, p, ph, s);
   if (st != SL_OK) return st;
   level_op<T>(h, 0, OP_APPLY, dt, ph, nullptr, v, s);
   launch_dot2<T>(rh, v, nullptr, nullptr, N, POST_ALPHA, S, h->partials, h->counter, s);
   launch_bicg_s<T>(sv, r, v, N, S, h->partials, h->counter, s);
-  st = vcycle<T>(h, 0, dt, sv, sh, s);
+  st = precond<T>(h, dt, sv, sh, s);
   if (st != SL_OK) return st;
   level_op<T>(h, 0, OP_APPLY, dt, sh, nullptr, t, s);
   launch_dot2<T>(t, sv, t, t, N, POST_OMEGA, S, h->partials, h->counter, s);
@@ -560,7 +593,8 @@ template <typename T, typename TX>
 sl_status ensure_graph(sl_hjb *h, int prec, double dt, TX *x, T *r, T *rh, T *p, T *v, T *sv, T *t,
                        T *ph, T *sh, BicgScalars *S) {
   IterGraph &g = h->transposed ? h->graphT[prec] : h->graph[prec];
-  if (g.exec && g.dt == dt) return SL_OK;
+  // the V-cycle's buffers and launch shapes are fixed at create; the AMG ones are not
+  if (g.exec && g.dt == dt && (h->o.precond == 0 || g.gen == h->amg_gen)) return SL_OK;
   if (g.exec) {
     cudaGraphExecDestroy(g.exec);
     g.exec = nullptr;
@@ -579,6 +613,7 @@ sl_status ensure_graph(sl_hjb *h, int prec, double dt, TX *x, T *r, T *rh, T *p,
   cudaGraphDestroy(graph);
   CK(e);
   g.dt = dt;
+  g.gen = h->amg_gen;
   return SL_OK;
 }
 
@@ -1057,6 +1092,8 @@ void sl_opts_default(sl_opts *o) {
   o->use_graphs = 1;
   o->coarse_tail_rows = -1;
   o->extrapolate = 1;
+  o->precond = 0;
+  o->amg_k_levels = 2;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -1069,6 +1106,7 @@ void sl_hjb_destroy(sl_hjb *h) {
   for (auto &g : h->graphT)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  amg_free(h->amg);
   for (void *p : h->allocs) cudaFree(p);
   if (h->hS) cudaFreeHost(h->hS);
   if (h->h_maxd) cudaFreeHost(h->h_maxd);
@@ -1095,6 +1133,13 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   if (h->o.precision != 0 && h->o.precision != 1) return fail(h, SL_EINVAL, "precision must be 0 or 1");
   if (h->o.nu1 < 0 || h->o.nu2 < 0 || h->o.kry_max < 1 || h->o.pi_max < 1 || !(h->o.omega > 0))
     return fail(h, SL_EINVAL, "bad iteration options");
+  if (h->o.precond != 0 && h->o.precond != 1) return fail(h, SL_EINVAL, "precond must be 0 or 1");
+  if (h->o.precond == 1 && (h->o.nu1 < 1 || h->o.amg_k_levels < 0))
+    return fail(h, SL_EINVAL, "the aggregation K-cycle needs nu1 >= 1 and amg_k_levels >= 0");
+  h->amg.nu1 = h->o.nu1;
+  h->amg.nu2 = h->o.nu2;
+  h->amg.omega = h->o.omega;
+  h->amg.k_levels = h->o.amg_k_levels;
   h->n = g->nx;
   h->m = g->nx - 2;
   h->h = hx;
@@ -1391,8 +1436,8 @@ sl_status sl_hjb_build_hierarchy(sl_hjb *h, double dt, void *stream) {
 sl_status sl_hjb_apply(sl_hjb *h, int level, int precision, const void *x, void *y, void *stream) {
   if (!h || !x || !y || level < 0 || level >= h->L) return SL_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (level > 0 && (!h->hier_valid || precision != h->o.precision))
-    return fail(h, SL_EINVAL, "coarse levels need a built hierarchy in the handle's precision");
+  if (level > 0 && (!h->hier_valid || precision != h->o.precision || h->o.precond != 0))
+    return fail(h, SL_EINVAL, "coarse levels need a built V-cycle hierarchy in the handle's precision");
   const double dt = h->hier_valid ? h->hier_dt : (h->class_valid ? h->class_dt : -1.0);
   if (level == 0 && !(dt > 0)) return fail(h, SL_EINVAL, "build the hierarchy first (it fixes dt)");
   if (precision == 0)
@@ -1407,6 +1452,7 @@ sl_status sl_hjb_apply(sl_hjb *h, int level, int precision, const void *x, void 
 
 sl_status sl_hjb_vcycle(sl_hjb *h, int precision, const void *b, void *x, void *stream) {
   if (!h || !b || !x) return SL_EINVAL;
+  if (h->o.precond != 0) return fail(h, SL_EINVAL, "the V-cycle needs precond 0");
   if (!h->hier_valid || precision != h->o.precision)
     return fail(h, SL_EINVAL, "V-cycle needs a built hierarchy in the handle's precision");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1420,6 +1466,7 @@ sl_status sl_hjb_vcycle(sl_hjb *h, int precision, const void *b, void *x, void *
 
 sl_status sl_hjb_vcycle_noalloc(sl_hjb *h, int precision, const void *b, void *x, void *stream) {
   if (!h || !b || !x) return SL_EINVAL;
+  if (h->o.precond != 0) return fail(h, SL_EINVAL, "the V-cycle needs precond 0");
   if (!h->hier_valid || precision != h->o.precision)
     return fail(h, SL_EINVAL, "V-cycle needs a built hierarchy in the handle's precision");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1487,6 +1534,7 @@ sl_status sl_hjb_adjoint(sl_hjb *h, const double *w, double *dJ_dg, double *dJ_d
   if (!h->rec_valid) return fail(h, SL_EINVAL, "sl_hjb_adjoint needs a preceding sl_hjb_solve_record");
   if (nparam > 0 && h->general)
     return fail(h, SL_EINVAL, "dJ/dtheta needs an x-independent sigma (sl_controls.sigma)");
+  if (h->o.precond != 0) return fail(h, SL_EINVAL, "the adjoint's transposed V-cycle needs precond 0");
   if (st) std::memset(st, 0, sizeof(*st));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   sl_status r = ensure_adjoint_buffers(h);

@@ -131,6 +131,10 @@ void launch_argmin_general(const GeneralArgs &g, const FineTab &dtab, const doub
                            const double *F, const double *phi, int nf, double tie_rel, uint8_t *policy,
                            unsigned long long *changes, int *flags, cudaStream_t s);
 
+// out[0..n] = exclusive prefix sums of in[0..n-1], out[n] = total (n >= 1);
+// scratch: 2 * ceil(n / 1024) ints.
+void launch_exclusive_scan(const int *in, int n, int32_t *out, int *scratch, cudaStream_t s);
+
 // ------------------------------------------------------------------ adjoint (transposed solves)
 // Explicit A^T of the fine level: row J (interior index of column j of A) lists the sources i
 // with A[i, j] != 0, i != j, sorted by i; the diagonal is stored apart.
