@@ -17,8 +17,13 @@ Coarsening (one level = two pairwise passes, aggregates of at most four unknowns
     rarely comes with a_ji != 0, and a row-only pattern leaves almost nothing to pair.
     j is a strong neighbour of i when s_ij > 0 and s_ij >= beta * max_k s_ik, beta = 0.25;
   * pairwise matching in rounds: every unmatched unknown proposes its strong unmatched
-    neighbour that is largest in the order of the edge keys (s_ij, h(i, j), -j), where
-    h(i, j) = fmix32(min(i, j) XOR fmix32(max(i, j))) and fmix32 is the 32-bit finalizer of
+    neighbour that is largest in the order of the edge keys (e(s_ij), h(i, j), -j), where
+    e(s) is the binary exponent of s (s = m 2^e, m in [0.5, 1)), so strengths within a factor
+    two rank equal and are ordered by the hash: on the nearly one-dimensional coarse graphs
+    of anisotropic LISL operators, exactly graded strengths form chains along which a
+    locally-dominant matching pairs one edge per round, while hashed ties pair a fixed
+    fraction per round.  h(i, j)
+    = fmix32(min(i, j) XOR fmix32(max(i, j))) and fmix32 is the 32-bit finalizer of
     MurmurHash3 (x ^= x >> 16; x *= 0x85ebca6b; x ^= x >> 13; x *= 0xc2b2ae35; x ^= x >> 16).
     The key of an edge is the same seen from either end, so this is a locally-dominant edge
     matching: the heaviest unmatched edge always pairs, and equal strengths (every interior
@@ -29,6 +34,10 @@ Coarsening (one level = two pairwise passes, aggregates of at most four unknowns
     piecewise constant (P_iI = 1 for i in aggregate I), the coarse matrix is the Galerkin
     product P^T A P.  The second pass repeats the matching on that coarse matrix, and the
     level's aggregates are the unions.
+  * coarsening stops at a level of at most 256 unknowns, or when a level would keep more than
+    3/4 of the unknowns of the one above (or at 16 levels).  The last level is solved exactly
+    (dense) when it has at most 256 unknowns, and otherwise approximately by COARSE_SWEEPS
+    damped-Jacobi sweeps from zero.
 Cycle (K-cycle, damped Jacobi, GCR acceleration of the coarse corrections):
   kcycle(l, b): x = omega D^-1 b, nu1 - 1 further sweeps x += omega D^-1 (b - A x);
                 r = b - A x; e = gcr(l + 1, P^T r) (an exact solve on the coarsest level);
@@ -46,6 +55,7 @@ the second are visited four times per cycle.
 from __future__ import annotations
 
 import dataclasses
+import math
 from typing import List
 
 import numpy as np
@@ -55,6 +65,9 @@ import scipy.linalg as sla
 BETA = 0.25
 ROUNDS = 8
 K_LEVELS = 2
+COARSEST = 256        # exact dense solve at or below this size
+MIN_REDUCTION = 0.75  # a level must keep at most this fraction of the unknowns above it
+COARSE_SWEEPS = 16
 
 
 def strength(A: sp.csr_matrix) -> sp.csr_matrix:
@@ -76,6 +89,11 @@ def fmix32(x: int) -> int:
     x = (x * 0xC2B2AE35) & 0xFFFFFFFF
     x ^= x >> 16
     return x
+
+
+def octave(s: float) -> int:
+    """The binary exponent e of s = m 2^e, m in [0.5, 1) (exact, from the floating-point bits)."""
+    return math.frexp(s)[1]
 
 
 def edge_hash(i: int, j: int) -> int:
@@ -104,7 +122,7 @@ def pairwise_match(A: sp.csr_matrix, beta: float = BETA, rounds: int = ROUNDS) -
                 j, s = S.indices[p], S.data[p]
                 if partner[j] >= 0 or not (s > 0.0) or s < beta * smax[i]:
                     continue
-                key = (s, edge_hash(i, j), -j)
+                key = (octave(s), edge_hash(i, j), -j)
                 if bkey is None or key > bkey:
                     best, bkey = j, key
             prop[i] = best
@@ -146,8 +164,9 @@ class AmgHierarchy:
     P: List[sp.csr_matrix]
 
 
-def build(A: sp.csr_matrix, coarsest: int = 256, max_levels: int = 16) -> AmgHierarchy:
-    """Levels until the coarse matrix has at most `coarsest` unknowns (or stops shrinking)."""
+def build(A: sp.csr_matrix, coarsest: int = COARSEST, max_levels: int = 16) -> AmgHierarchy:
+    """Levels until the coarse matrix has at most `coarsest` unknowns, coarsening stalls
+    (more than MIN_REDUCTION of the unknowns kept) or max_levels is reached."""
     As, aggs, Ps = [A.tocsr()], [], []
     while As[-1].shape[0] > coarsest and len(As) < max_levels:
         Al = As[-1]
@@ -156,7 +175,7 @@ def build(A: sp.csr_matrix, coarsest: int = 256, max_levels: int = 16) -> AmgHie
         A1 = (P1.T @ Al @ P1).tocsr()
         a2 = aggregates_from_pairs(pairwise_match(A1))
         agg = a2[a1]
-        if int(agg.max()) + 1 >= Al.shape[0]:
+        if int(agg.max()) + 1 > MIN_REDUCTION * Al.shape[0]:
             break
         P = prolongation(agg)
         As.append((P.T @ Al @ P).tocsr())
@@ -165,11 +184,22 @@ def build(A: sp.csr_matrix, coarsest: int = 256, max_levels: int = 16) -> AmgHie
     return AmgHierarchy(As, aggs, Ps)
 
 
+def coarsest_solve(A: sp.csr_matrix, b: np.ndarray, omega: float) -> np.ndarray:
+    """Exact for at most COARSEST unknowns, else COARSE_SWEEPS damped-Jacobi sweeps from 0."""
+    if A.shape[0] <= COARSEST:
+        return sla.solve(A.toarray(), b)
+    d = A.diagonal()
+    x = omega * b / d
+    for _ in range(COARSE_SWEEPS - 1):
+        x = x + omega * (b - A @ x) / d
+    return x
+
+
 def kcycle(H: AmgHierarchy, l: int, b: np.ndarray, nu1: int = 1, nu2: int = 1,
            omega: float = 0.8, k_levels: int = K_LEVELS) -> np.ndarray:
     A = H.A[l]
     if l == len(H.A) - 1:
-        return sla.solve(A.toarray(), b)
+        return coarsest_solve(A, b, omega)
     d = A.diagonal()
     x = omega * b / d
     for _ in range(nu1 - 1):
@@ -186,7 +216,7 @@ def gcr(H: AmgHierarchy, l: int, r: np.ndarray, nu1: int, nu2: int, omega: float
         k_levels: int = K_LEVELS) -> np.ndarray:
     A = H.A[l]
     if l == len(H.A) - 1:
-        return sla.solve(A.toarray(), r)
+        return coarsest_solve(A, r, omega)
     v1 = kcycle(H, l, r, nu1, nu2, omega, k_levels)
     w1 = A @ v1
     ww = w1 @ w1

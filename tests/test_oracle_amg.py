@@ -48,6 +48,58 @@ def test_union_pattern_coarsens_far_reaching_directional_stencils():
     assert all(b <= a // 2 for a, b in zip(sizes, sizes[1:])), sizes
 
 
+def test_graded_chain_pairs_within_the_rounds():
+    """A chain whose couplings grow by 0.2 % per edge (all within one octave): ranking by
+    octave and hash pairs most unknowns within ROUNDS rounds, where exact strengths would
+    pair about one edge per round."""
+    n = 200
+    c = 1.0 + 0.002 * np.arange(n - 1)
+    A = sp.diags([-c, 2.1 * np.ones(n) + np.r_[c, 0] + np.r_[0, c], -c], [-1, 0, 1]).tocsr()
+    partner = amg.pairwise_match(A)
+    assert np.mean(partner >= 0) > 0.8
+
+
+def test_octave_is_the_binary_exponent():
+    for s_, e in ((1.0, 1), (0.5, 0), (0.75, 0), (0.4999, -1), (3.0, 2), (2.0 ** -30, -29)):
+        assert amg.octave(s_) == e
+
+
+def test_large_coarsest_level_uses_jacobi_sweeps(monkeypatch):
+    """A hierarchy that stops above COARSEST unknowns solves its last level with
+    COARSE_SWEEPS damped-Jacobi sweeps from zero (closed form written densely)."""
+    A = _lap2d(40)
+    monkeypatch.setattr(amg, "COARSEST", 100)
+    H = amg.build(A, coarsest=100, max_levels=2)
+    assert len(H.A) == 2 and H.A[1].shape[0] > 100
+    Ac = H.A[1].toarray()
+    d = np.diag(Ac)
+    b = np.random.default_rng(7).standard_normal(Ac.shape[0])
+    x = 0.8 * b / d
+    for _ in range(amg.COARSE_SWEEPS - 1):
+        x = x + 0.8 * (b - Ac @ x) / d
+    got = amg.gcr(H, 1, b, 1, 1, 0.8)
+    assert np.max(np.abs(got - x)) <= 1e-12 * np.abs(x).max()
+
+
+def test_coarsening_and_convergence_on_a_129_grid():
+    """Every level keeps at most 3/4 of the unknowns above it, and the K-cycle (with a Jacobi
+    coarsest level where coarsening stalls above 256 unknowns) preconditions BiCGSTAB to
+    1e-10 in a handful of iterations."""
+    p = W.scaled(129, 33, 4, seed=0)
+    pol = lisl.improve(lisl.control_values(p, p.g, p.dt))
+    A, _ = lisl.assemble(p, pol, p.g, p.dt, p.dt)
+    A = A.tocsr()
+    H = amg.build(A)
+    sizes = [a.shape[0] for a in H.A]
+    assert all(b <= amg.MIN_REDUCTION * a for a, b in zip(sizes, sizes[1:])), sizes
+    M = spla.LinearOperator(A.shape, matvec=lambda r: amg.kcycle(H, 0, r))
+    b = np.random.default_rng(8).standard_normal(A.shape[0])
+    cnt = [0]
+    x, info = spla.bicgstab(A, b, M=M, rtol=1e-10, callback=lambda _: cnt.__setitem__(0, cnt[0] + 1))
+    assert info == 0 and cnt[0] <= 12
+    assert np.linalg.norm(A @ x - b) <= 1e-9 * np.linalg.norm(b)
+
+
 def test_fmix32_is_murmur3_finalizer():
     assert amg.fmix32(0) == 0
     assert amg.fmix32(1) == 0x514E28B7
@@ -95,7 +147,7 @@ def test_matching_invariants(heavy):
             j, s = S.indices[p], S.data[p]
             if not free[j] or not (s > 0) or s < amg.BETA * smax[i]:
                 continue
-            key = (s, amg.edge_hash(i, j), -j)
+            key = (amg.octave(s), amg.edge_hash(i, j), -j)
             if bkey is None or key > bkey:
                 best, bkey = j, key
         return best
@@ -113,7 +165,7 @@ def test_heaviest_strong_edge_is_paired():
     Sc = S.tocoo()
     for i, j, s in zip(Sc.row, Sc.col, Sc.data):
         if s > 0 and s >= amg.BETA * smax[i] and S[j, i] >= amg.BETA * smax[j]:
-            key = (s, amg.edge_hash(i, j))
+            key = (amg.octave(s), amg.edge_hash(i, j))
             if bkey is None or key > bkey:
                 best, bkey = (i, j), key
     partner = amg.pairwise_match(A)
@@ -149,7 +201,8 @@ def test_galerkin_row_sums_and_symmetry(which):
     assert amg.complexity(H) < 2.0
 
 
-def test_two_level_kcycle_is_the_two_grid_operator():
+def test_two_level_kcycle_is_the_two_grid_operator(monkeypatch):
+    monkeypatch.setattr(amg, "COARSEST", 2000)   # an exact coarse solve on level 1
     A = _lisl(True)
     H = amg.build(A)
     H2 = amg.AmgHierarchy(H.A[:2], H.agg[:1], H.P[:1])
