@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-amg", action="store_true")
+    p.add_argument("--amg-steps", type=int, default=8)
     p.add_argument("--batched-instances", type=int, default=256)
     p.add_argument("--batched-workers", type=int, default=16)
     p.add_argument("--adjoint-steps", type=int, default=64,
@@ -369,6 +371,13 @@ def run_ours(args):
         adjoint = adjoint_record(slp, W, dev, stream, extra, args.adjoint_steps)
         torch.cuda.nvtx.range_pop()
 
+    # ---- aggregation AMG against the V-cycle on the same steps
+    amg = None
+    if not args.no_amg:
+        torch.cuda.nvtx.range_push("amg")
+        amg = amg_record(slp, prob, dev, stream, args, extra, g)
+        torch.cuda.nvtx.range_pop()
+
     # ---- batched: many independent instances, LPT-sharded over the ranks
     batched = None
     if not args.no_batched:
@@ -405,6 +414,7 @@ def run_ours(args):
             "mixed_vs_fp64_rel_err": err,
             "adjoint": adjoint,
             "batched": batched,
+            "amg": amg,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -457,6 +467,40 @@ def adjoint_record(slp, W, dev, stream, extra, steps=64):
         del sa
         torch.cuda.empty_cache()
     out["value"] = out["mixed"]["value"]
+    return out
+
+
+def amg_record(slp, prob, dev, stream, args, extra, g):
+    """Mixed-precision steps W+1 .. W+K of the headline workload with the aggregation K-cycle
+    (precond 1) and with the V-cycle (precond 0), each timed with CUDA events."""
+    import torch
+    n = prob.n
+    dt = 1.0 / 128
+    k = args.amg_steps
+    out = {"workload": f"steps {args.warmup + 1}..{args.warmup + k} of the headline workload, mixed precision",
+           "unit": UNIT}
+    for pc, key in ((1, "aggregation_kcycle"), (0, "geometric_vcycle")):
+        kw = dict(precision=1, argmin_screen=1, precond=pc)
+        kw.update(extra)
+        s = slp.solver_from_problem(prob, device=dev, **kw)
+        u = g.clone()
+        for i in range(1, args.warmup + 1):
+            s.step(u, i * dt, dt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = {"pi_iters": 0, "krylov_iters": 0, "ir_iters": 0}
+        e0.record(stream)
+        for i in range(1, k + 1):
+            r = s.step(u, (args.warmup + i) * dt, dt)
+            for kk in st:
+                st[kk] += r[kk]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[key] = {"value": n * n * k / (ms / 1e3), "ms_per_step": ms / k, **st}
+        del s
+        torch.cuda.empty_cache()
+    out["value"] = out["aggregation_kcycle"]["value"]
     return out
 
 

@@ -7,9 +7,13 @@
 //   union of the patterns of A and A^T (zeros dropped); j is strong for i when
 //   s_ij > 0 and s_ij >= 0.25 max_k s_ik; in each of kAmgRounds rounds every unmatched
 //   unknown proposes its strong unmatched neighbour that is largest in the edge order
-//   (s_ij, fmix32(min ^ fmix32(max)), -j) (fmix32: MurmurHash3's 32-bit finalizer), and two
+//   (exponent of s_ij, fmix32(min ^ fmix32(max)), -j) (fmix32: MurmurHash3's 32-bit
+//   finalizer; strengths within a factor two rank equal and the hash orders them), and two
 //   unknowns that propose each other pair up; aggregates are numbered in the order of their
 //   lowest member; the coarse matrix is the Galerkin product P^T A P with piecewise-constant P.
+//   Coarsening stops at kAmgCoarsest unknowns or when a level keeps more than 3/4 of the
+//   unknowns above it; a last level above kAmgCoarsest is solved by kAmgCoarseSweeps damped
+//   Jacobi sweeps instead of a dense solve.
 // Cycle: damped Jacobi smoothing; the coarse correction of level l is approximated by GCR on
 //   level l+1 preconditioned by the cycle of level l+1 (two GCR steps on levels 1..k_levels,
 //   one below), with an exact dense solve on the coarsest level.
@@ -113,27 +117,38 @@ __global__ void k_amg_tr_fill(int n, const int32_t *__restrict__ rowptr, const i
   }
 }
 
-__global__ void __launch_bounds__(kAT) k_amg_tr_sort(int n, const int32_t *__restrict__ rpT,
-                                                      int32_t *__restrict__ colT, double *__restrict__ vT,
-                                                      int32_t *__restrict__ err) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const int lo = rpT[j], len = rpT[j + 1] - lo;
-  if (len > kAmgRowMax) {
-    *err = 1;
+// Stable insertion sort of one segment by column (values carried along): in registers when
+// the segment is short, in place otherwise.
+__device__ void sort_segment(int32_t *__restrict__ col, double *__restrict__ val, int lo, int len) {
+  if (len <= kAmgRowMax) {
+    int c[kAmgRowMax];
+    double w[kAmgRowMax];
+    for (int a = 0; a < len; ++a) {
+      const int ca = col[lo + a];
+      const double wa = val[lo + a];
+      int b = a - 1;
+      while (b >= 0 && c[b] > ca) { c[b + 1] = c[b]; w[b + 1] = w[b]; --b; }
+      c[b + 1] = ca;
+      w[b + 1] = wa;
+    }
+    for (int a = 0; a < len; ++a) { col[lo + a] = c[a]; val[lo + a] = w[a]; }
     return;
   }
-  int c[kAmgRowMax];
-  double w[kAmgRowMax];
-  for (int a = 0; a < len; ++a) {
-    const int ca = colT[lo + a];
-    const double wa = vT[lo + a];
+  for (int a = lo + 1; a < lo + len; ++a) {
+    const int ca = col[a];
+    const double wa = val[a];
     int b = a - 1;
-    while (b >= 0 && c[b] > ca) { c[b + 1] = c[b]; w[b + 1] = w[b]; --b; }
-    c[b + 1] = ca;
-    w[b + 1] = wa;
+    while (b >= lo && col[b] > ca) { col[b + 1] = col[b]; val[b + 1] = val[b]; --b; }
+    col[b + 1] = ca;
+    val[b + 1] = wa;
   }
-  for (int a = 0; a < len; ++a) { colT[lo + a] = c[a]; vT[lo + a] = w[a]; }
+}
+
+__global__ void __launch_bounds__(kAT) k_amg_tr_sort(int n, const int32_t *__restrict__ rpT,
+                                                      int32_t *__restrict__ colT, double *__restrict__ vT) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  sort_segment(colT, vT, rpT[j], rpT[j + 1] - rpT[j]);
 }
 
 // Row i of the strength matrix: union of row i of A and of A^T (both sorted), value
@@ -184,17 +199,18 @@ __global__ void __launch_bounds__(kAT) k_amg_propose(int n, const int32_t *__res
     return;
   }
   const double thr = 0.25 * smax[i];
-  int best = -1;
-  double bs = 0.0;
+  int best = -1, be = 0;
   unsigned bh = 0u;
   for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {  // the strength pattern (no diagonal)
     const int j = col[p];
     const double sv = s[p];
     if (partner[j] >= 0 || !(sv > 0.0) || sv < thr) continue;
+    int e;
+    frexp(sv, &e);  // sv = m 2^e, m in [0.5, 1): exact
     const unsigned h = edge_hash(i, j);
-    if (best < 0 || sv > bs || (sv == bs && (h > bh || (h == bh && j < best)))) {
+    if (best < 0 || e > be || (e == be && (h > bh || (h == bh && j < best)))) {
       best = j;
-      bs = sv;
+      be = e;
       bh = h;
     }
   }
@@ -256,48 +272,67 @@ __global__ void k_amg_compose(int n, int nc, const int32_t *__restrict__ a1, con
   }
 }
 
-// Galerkin row I of P^T A P: the member rows' entries with columns mapped to aggregates, sorted
-// and merged (members ascending, entries in column order).  PASS 0 counts, PASS 1 writes.
-template <int PASS, int MS>
-__global__ void __launch_bounds__(kAT) k_amg_galerkin(int nc, const int32_t *__restrict__ mem,
-                                                       const int32_t *__restrict__ agg,
-                                                       const int32_t *__restrict__ rowptr,
-                                                       const int32_t *__restrict__ col,
-                                                       const double *__restrict__ v,
-                                                       const int32_t *__restrict__ rowptr_c,
-                                                       int *__restrict__ cnt_c, int32_t *__restrict__ col_c,
-                                                       double *__restrict__ v_c, int32_t *__restrict__ err) {
+// Galerkin product P^T A P.  The entries of coarse row I are those of its member rows
+// (members ascending, entries in column order) with columns mapped to aggregates; they are
+// written unmerged (their total is nnz(A)), ordered by a stable sort, and merged, so equal
+// columns are summed in that order.
+template <int MS>
+__global__ void k_gal_rawcount(int nc, const int32_t *__restrict__ mem, const int32_t *__restrict__ rowptr,
+                               int *__restrict__ cnt) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nc) return;
-  int c[kAmgRowMax];
-  double w[kAmgRowMax];
-  int len = 0;
+  int c = 0;
+  for (int q = 0; q < MS; ++q) {
+    const int i = mem[MS * I + q];
+    if (i >= 0) c += rowptr[i + 1] - rowptr[i];
+  }
+  cnt[I] = c;
+}
+
+template <int MS>
+__global__ void k_gal_rawfill(int nc, const int32_t *__restrict__ mem, const int32_t *__restrict__ agg,
+                              const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                              const double *__restrict__ v, const int32_t *__restrict__ rawptr,
+                              int32_t *__restrict__ rawcol, double *__restrict__ rawval) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  int o = rawptr[I];
   for (int q = 0; q < MS; ++q) {
     const int i = mem[MS * I + q];
     if (i < 0) continue;
-    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      const int J = agg[col[p]];
-      int a = len - 1;
-      while (a >= 0 && c[a] > J) --a;
-      if (a >= 0 && c[a] == J) {
-        w[a] += v[p];
-      } else if (len < kAmgRowMax) {
-        for (int b = len; b > a + 1; --b) { c[b] = c[b - 1]; w[b] = w[b - 1]; }
-        c[a + 1] = J;
-        w[a + 1] = v[p];
-        ++len;
-      } else {
-        *err = 1;  // row too long for the local buffer: the host reports it
-        return;
-      }
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p, ++o) {
+      rawcol[o] = agg[col[p]];
+      rawval[o] = v[p];
     }
   }
-  if (PASS == 0) {
-    cnt_c[I] = len;
-  } else {
-    const int base = rowptr_c[I];
-    for (int a = 0; a < len; ++a) { col_c[base + a] = c[a]; v_c[base + a] = w[a]; }
+}
+
+__global__ void __launch_bounds__(kAT) k_gal_sort(int nc, const int32_t *__restrict__ rawptr,
+                                                   int32_t *__restrict__ rawcol, double *__restrict__ rawval) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  sort_segment(rawcol, rawval, rawptr[I], rawptr[I + 1] - rawptr[I]);
+}
+
+template <int PASS>
+__global__ void k_gal_merge(int nc, const int32_t *__restrict__ rawptr, const int32_t *__restrict__ rawcol,
+                            const double *__restrict__ rawval, const int32_t *__restrict__ rowptr_c,
+                            int *__restrict__ cnt_c, int32_t *__restrict__ col_c, double *__restrict__ v_c) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  int len = 0;
+  const int base = PASS ? rowptr_c[I] : 0;
+  for (int p = rawptr[I]; p < rawptr[I + 1];) {
+    const int c = rawcol[p];
+    double acc = rawval[p];
+    for (++p; p < rawptr[I + 1] && rawcol[p] == c; ++p) acc += rawval[p];
+    if (PASS) {
+      col_c[base + len] = c;
+      v_c[base + len] = acc;
+    }
+    ++len;
   }
+  if (!PASS) cnt_c[I] = len;
 }
 
 __global__ void k_amg_diag(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
@@ -568,7 +603,7 @@ cudaError_t pairwise_pass(AmgEngine &E, int n, const int32_t *rowptr, const int3
   AMG_CK(cudaMemsetAsync(E.cnt, 0, size_t(n) * sizeof(int), s));
   note_launch(4);
   k_amg_tr_fill<<<nblk(n), kAT, 0, s>>>(n, rowptr, col, v, E.rpT, E.cnt, E.colT, E.vT);
-  k_amg_tr_sort<<<nblk(n), kAT, 0, s>>>(n, E.rpT, E.colT, E.vT, E.err);
+  k_amg_tr_sort<<<nblk(n), kAT, 0, s>>>(n, E.rpT, E.colT, E.vT);
   k_amg_sym<0><<<nblk(n), kAT, 0, s>>>(n, rowptr, col, v, E.rpT, E.colT, E.vT, nullptr, E.cnt, nullptr, nullptr,
                                        nullptr);
   launch_exclusive_scan(E.cnt, n, E.rpS, E.scan, s);
@@ -584,34 +619,27 @@ cudaError_t pairwise_pass(AmgEngine &E, int n, const int32_t *rowptr, const int3
   k_amg_leader<<<nblk(n), kAT, 0, s>>>(n, E.partner, E.flag);
   launch_exclusive_scan(E.flag, n, E.ids, E.scan, s);
   AMG_CK(read_int(E, E.ids + n, nc, s));
-  int err = 0;
-  AMG_CK(read_int(E, E.err, &err, s));
-  if (err) {
-    E.err_msg = "a column of the aggregation hierarchy has more entries than its local buffer";
-    return cudaErrorInvalidValue;
-  }
   note_launch(1);
   k_amg_assign<<<nblk(n), kAT, 0, s>>>(n, E.partner, E.ids, agg, mem);
   return cudaGetLastError();
 }
 
-// Galerkin product into (rowptr_c, col_c, v_c) with capacity checks done by the caller through
-// *nnz (first call: count only when col_c == nullptr).
+// Galerkin product into (rowptr_c, col_c, v_c): own_storage grows the coarse level's arrays,
+// otherwise they are scratch of capacity *cap_c.
 template <int MS>
 cudaError_t galerkin(AmgEngine &E, int nc, const int32_t *mem, const int32_t *agg, const int32_t *rowptr,
                      const int32_t *col, const double *v, int32_t *rowptr_c, int32_t **col_c, double **v_c,
                      float **v32_c, size_t *cap_c, long long *nnz, bool own_storage, cudaStream_t s) {
-  AMG_CK(cudaMemsetAsync(E.err, 0, sizeof(int32_t), s));
+  note_launch(3);
+  k_gal_rawcount<MS><<<nblk(nc), kAT, 0, s>>>(nc, mem, rowptr, E.cnt);
+  launch_exclusive_scan(E.cnt, nc, E.rawptr, E.scan, s);
+  k_gal_rawfill<MS><<<nblk(nc), kAT, 0, s>>>(nc, mem, agg, rowptr, col, v, E.rawptr, E.rawcol, E.rawval);
+  k_gal_sort<<<nblk(nc), kAT, 0, s>>>(nc, E.rawptr, E.rawcol, E.rawval);
   note_launch(1);
-  k_amg_galerkin<0, MS><<<nblk(nc), kAT, 0, s>>>(nc, mem, agg, rowptr, col, v, nullptr, E.cnt, nullptr, nullptr, E.err);
+  k_gal_merge<0><<<nblk(nc), kAT, 0, s>>>(nc, E.rawptr, E.rawcol, E.rawval, nullptr, E.cnt, nullptr, nullptr);
   launch_exclusive_scan(E.cnt, nc, rowptr_c, E.scan, s);
-  int total = 0, err = 0;
+  int total = 0;
   AMG_CK(read_int(E, rowptr_c + nc, &total, s));
-  AMG_CK(read_int(E, E.err, &err, s));
-  if (err) {
-    E.err_msg = "a Galerkin row of the aggregation hierarchy exceeds its local buffer";
-    return cudaErrorInvalidValue;
-  }
   if (own_storage) {  // col, v64 and v32 share one capacity
     size_t c1 = *cap_c, c2 = *cap_c, c3 = *cap_c;
     AMG_CK(grow(E, col_c, &c1, size_t(total)));
@@ -623,7 +651,7 @@ cudaError_t galerkin(AmgEngine &E, int nc, const int32_t *mem, const int32_t *ag
     return cudaErrorInvalidValue;
   }
   note_launch(1);
-  k_amg_galerkin<1, MS><<<nblk(nc), kAT, 0, s>>>(nc, mem, agg, rowptr, col, v, rowptr_c, nullptr, *col_c, *v_c, E.err);
+  k_gal_merge<1><<<nblk(nc), kAT, 0, s>>>(nc, E.rawptr, E.rawcol, E.rawval, rowptr_c, nullptr, *col_c, *v_c);
   *nnz = total;
   return cudaGetLastError();
 }
@@ -670,6 +698,10 @@ cudaError_t amg_reserve_level0(AmgEngine &E, int n, long long nnz) {
     AMG_CK(grow(E, &E.t_v, &c, size_t(nnz)));
     AMG_CK(grow(E, &E.colT, &f, size_t(nnz)));
     AMG_CK(grow(E, &E.vT, &g, size_t(nnz)));
+    size_t h1 = E.cap_nnz, h2 = E.cap_nnz, h3 = E.cap_n ? E.cap_n + 1 : 0;
+    AMG_CK(grow(E, &E.rawcol, &h1, size_t(nnz)));
+    AMG_CK(grow(E, &E.rawval, &h2, size_t(nnz)));
+    AMG_CK(grow(E, &E.rawptr, &h3, size_t(n) + 1));
     size_t r1 = E.cap_n ? E.cap_n + 1 : 0, r2 = r1;
     AMG_CK(grow(E, &E.rpT, &r1, size_t(n) + 1));
     AMG_CK(grow(E, &E.rpS, &r2, size_t(n) + 1));
@@ -739,7 +771,7 @@ cudaError_t amg_setup(AmgEngine &E, cudaStream_t s) {
     AMG_CK(grow(E, &A.agg, &A.cap_agg, size_t(A.n)));
     int32_t *a2 = E.flag;  // free after pass 1's numbering
     AMG_CK(pairwise_pass(E, n1, E.t_rowptr, E.t_col, E.t_v, a2, E.mem2, &n2, s));
-    if (n2 >= A.n) break;  // no coarsening
+    if (double(n2) > kAmgMinReduction * double(A.n)) break;  // coarsening stalls
     AMG_CK(grow(E, &A.mem, &A.cap_mem, 4 * size_t(n2)));
     note_launch(1);
     k_amg_compose<<<nblk(std::max(A.n, n2)), kAT, 0, s>>>(A.n, n2, E.a1, a2, E.mem1, E.mem2, A.agg, A.mem);
@@ -760,12 +792,13 @@ cudaError_t amg_setup(AmgEngine &E, cudaStream_t s) {
   }
   E.L = l + 1;
   AmgLevel &Lc = E.lev[E.L - 1];
-  if (Lc.n > kAmgCoarsest) {
-    E.err_msg = "aggregation stopped above the dense coarsest size";
-    return cudaErrorInvalidValue;
+  E.dense_coarsest = Lc.n <= kAmgCoarsest;
+  if (E.dense_coarsest) {
+    note_launch(1);
+    k_amg_dense_inverse<<<1, 256, 0, s>>>(Lc.n, Lc.rowptr, Lc.col, Lc.v64, E.work, E.Ainv64, E.Ainv32);
+  } else if (!Lc.vec64[AV_T]) {
+    AMG_CK(level_vectors(E, Lc, true));
   }
-  note_launch(1);
-  k_amg_dense_inverse<<<1, 256, 0, s>>>(Lc.n, Lc.rowptr, Lc.col, Lc.v64, E.work, E.Ainv64, E.Ainv32);
   return cudaGetLastError();
 }
 
@@ -794,12 +827,33 @@ void dots(AmgEngine &E, int n, const T *a, const T *b, const T *c, const T *d, d
 template <typename T>
 void gcr(AmgEngine &E, int l, const T *r, T *e, cudaStream_t s);
 
+// The last level: x = A^{-1} b (dense), or kAmgCoarseSweeps damped-Jacobi sweeps from zero.
+template <typename T>
+void coarsest(AmgEngine &E, const T *b, T *x, cudaStream_t s) {
+  AmgLevel &A = E.lev[E.L - 1];
+  if (E.dense_coarsest) {
+    note_launch();
+    k_amg_dense<T><<<1, 256, 0, s>>>(A.n, ainv<T>(E), b, x);
+    return;
+  }
+  const T om = T(E.omega);
+  T *cur = x, *oth = vec<T>(A, AV_T);
+  amg_op<T>(OP_JACOBI0, A, om, nullptr, b, cur, s);
+  for (int k = 1; k < kAmgCoarseSweeps; ++k) {
+    amg_op<T>(OP_JACOBI, A, om, cur, b, oth, s);
+    std::swap(cur, oth);
+  }
+  if (cur != x) {
+    note_launch();
+    k_amg_copy<T><<<nblk(A.n), kAT, 0, s>>>(A.n, cur, x);
+  }
+}
+
 template <typename T>
 void kcyc(AmgEngine &E, int l, const T *b, T *x, cudaStream_t s) {
   AmgLevel &A = E.lev[l];
   if (l == E.L - 1) {
-    note_launch();
-    k_amg_dense<T><<<1, 256, 0, s>>>(A.n, ainv<T>(E), b, x);
+    coarsest<T>(E, b, x, s);
     return;
   }
   const T om = T(E.omega);
@@ -831,8 +885,7 @@ template <typename T>
 void gcr(AmgEngine &E, int l, const T *r, T *e, cudaStream_t s) {
   AmgLevel &A = E.lev[l];
   if (l == E.L - 1) {
-    note_launch();
-    k_amg_dense<T><<<1, 256, 0, s>>>(A.n, ainv<T>(E), r, e);
+    coarsest<T>(E, r, e, s);
     return;
   }
   T *v1 = vec<T>(A, AV_V1), *w1 = vec<T>(A, AV_W1), *v2 = vec<T>(A, AV_V2), *w2 = vec<T>(A, AV_W2),

@@ -17,8 +17,10 @@ namespace sl {
 
 constexpr int kAmgMaxLevels = 16;
 constexpr int kAmgRounds = 8;      // matching rounds per pass
-constexpr int kAmgRowMax = 256;    // entries of one coarse row before merging
+constexpr int kAmgRowMax = 128;    // rows up to this length are sorted in registers, longer ones in place
 constexpr int kAmgCoarsest = 256;  // dense solve at or below this many unknowns
+constexpr double kAmgMinReduction = 0.75;  // a level keeps at most this fraction of the unknowns above
+constexpr int kAmgCoarseSweeps = 16;        // Jacobi sweeps on a last level above kAmgCoarsest
 
 enum AmgVec { AV_X = 0, AV_B, AV_R, AV_T, AV_V1, AV_W1, AV_V2, AV_W2, AV_E, AV_R2, AV_COUNT };
 
@@ -39,6 +41,7 @@ struct AmgLevel {
 
 struct AmgEngine {
   int L = 0;
+  bool dense_coarsest = true;  // false: the last level is solved by kAmgCoarseSweeps Jacobi sweeps
   AmgLevel lev[kAmgMaxLevels];
   int k_levels = 2, nu1 = 1, nu2 = 1;
   double omega = 0.8;
@@ -51,6 +54,8 @@ struct AmgEngine {
   double *t_v = nullptr;
   int32_t *rpT = nullptr, *colT = nullptr, *rpS = nullptr, *colS = nullptr;  // A^T; strength pattern
   double *vT = nullptr;
+  int32_t *rawptr = nullptr, *rawcol = nullptr;  // Galerkin: unmerged entries of every coarse row
+  double *rawval = nullptr;
   double *Ainv64 = nullptr, *work = nullptr, *partials = nullptr;
   float *Ainv32 = nullptr;
   int *h_int = nullptr;  // pinned
