@@ -693,8 +693,9 @@ sl_status true_residual(sl_hjb *h, double dt, double tolk, double *r, ResNorms *
 sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
   const size_t N = NN(h, 0);
   // ||F||: the residual at X = (0 inside, psi on the boundary) is F itself
-  if (!h->transposed)
-    launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, s);
+  if (!h->transposed)  // Xb vanishes inside: rows beyond the stencil reach need no taps
+    launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, s,
+                     std::max(1, h->cl[0].R));
   CK(cudaGetLastError());
   double *X = h->transposed ? h->mu : h->X;
   KBuf &k = h->kb;

@@ -303,17 +303,48 @@ __global__ void __launch_bounds__(256) k_coarse_op(CoarseLev<T> L, const int *__
     }
     return;
   }
+  // Explicit rows: four threads per row, each taking every fourth row of the window, then a
+  // shuffle reduction.  A single thread per row walked (2R+1)^2 dependent iterations of a DRAM
+  // load and a gather; four keep four times as many loads in flight with the same sectors
+  // (neighbouring slots stay neighbours in memory).
   const int nexpl = *nexpl_dev;
   const int nb = gridDim.x - tiles;
-  for (int slot = (blockIdx.x - tiles) * blockDim.x + threadIdx.x; slot < nexpl; slot += nb * blockDim.x)
-    coarse_expl_row<T, OP>(L, slot, omega, x, b, y);
+  const int part = threadIdx.x & 3;
+  const int stride = (nb * blockDim.x) >> 2;
+  for (int slot = ((blockIdx.x - tiles) * blockDim.x + threadIdx.x) >> 2;
+       __any_sync(0xffffffffu, slot < nexpl); slot += stride) {
+    const bool act = slot < nexpl;
+    T acc = T(0), d = T(1);
+    int j = 0;
+    if (act) {
+      j = L.erow[slot];
+      const int I1 = j % L.n, I2 = j / L.n;
+      const int R = L.R, Wd = 2 * R + 1;
+      d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
+      if (OP != OP_JACOBI0) {
+        const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
+        const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
+        for (int dy = ylo + part; dy <= yhi; dy += 4) {
+          const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
+          const T *xrow = x + j + dy * L.n;
+          for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[size_t(dx) * L.cap], __ldg(xrow + dx), acc);
+        }
+      }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (act && part == 0) {
+      if (OP == OP_JACOBI0) y[j] = omega * b[j] / d;
+      else coarse_finish<T, OP>(y, x, b, j, acc, d, omega);
+    }
+  }
 }
 
 template <typename T>
 void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T omega, const T *x,
                       const T *b, T *y, cudaStream_t s) {
   const int tx = (L.m + 31) / 32, tiles = tx * ((L.m + kCRowsY - 1) / kCRowsY);
-  const int eg = std::max(1, std::min(kRedBlocks, (L.cap + 255) / 256));
+  const int eg = std::max(1, std::min(2 * kRedBlocks, (4 * L.cap + 255) / 256));  // 4 threads per explicit row
   const int grid = tiles + eg;
   const size_t bytes = op == OP_JACOBI0 ? 0 : size_t(32 + 2 * L.R) * (kCRowsY + 2 * L.R) * sizeof(T);
   note_launch();

@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256) k_hjb_resid(FineTab tab, const uint8_t *_
                                                    const double *__restrict__ U,
                                                    const double *__restrict__ F,
                                                    const double *__restrict__ phi, int nf, double dt,
-                                                   double *__restrict__ r) {
+                                                   double *__restrict__ r, int zero_inside) {
   const int i1 = 1 + blockIdx.x * 32 + threadIdx.x;
   const int i2 = 1 + blockIdx.y * 8 + threadIdx.y;
   const int n = tab.n, m = tab.m;
@@ -484,16 +484,23 @@ __global__ void __launch_bounds__(256) k_hjb_resid(FineTab tab, const uint8_t *_
   double f = 0.0;
   for (int mm = 0; mm < nf; ++mm) f = fma(__ldg(phi + k * nf + mm), F[mm * N + j], f);
   const double Xj = X[j];
+  // zero_inside = R > 0: X vanishes on the interior and no tap of a row farther than R from
+  // the boundary reaches it, so L X + c X = 0 there (the right-hand side F of the step)
+  const int R = zero_inside;
+  if (R > 0 && i1 > R && i1 < n - 1 - R && i2 > R && i2 < n - 1 - R) {
+    r[j] = U[j] + dt * f;
+    return;
+  }
   const double v = eval_global64(tab, e, X, j) + (f + tab.c64[k] * Xj);
   r[j] = (U[j] - Xj) + dt * v;
 }
 
 void launch_hjb_resid(const FineTab &tab, const uint8_t *policy, const double *X,
                       const double *Uprev, const double *F, const double *phi, int nf, double dt,
-                      double *r, cudaStream_t s) {
+                      double *r, cudaStream_t s, int zero_inside) {
   dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + 7) / 8);
   note_launch();
-  k_hjb_resid<<<grd, blk, 0, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r);
+  k_hjb_resid<<<grd, blk, 0, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside);
 }
 
 // ----------------------------------------------------------------------------- transfers

@@ -59,10 +59,12 @@ void launch_fine_op(int op, const FineTab &tab, const int32_t *slin, const uint8
 // Jacobi scale omega / d_e of every fine table entry for step size dt (into od64 / od32).
 void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, float *od32, cudaStream_t s);
 
-// r = U_prev - X + dt (L X + c X + f) for the current policy (interior), FP64.
+// r = U_prev - X + dt (L X + c X + f) for the current policy (interior), FP64.  With
+// zero_inside = R > 0 the caller promises X = 0 on the interior and R >= the longest tap:
+// rows farther than R from the boundary then skip their taps (r = U_prev + dt f).
 void launch_hjb_resid(const FineTab &tab, const uint8_t *policy, const double *X,
                       const double *Uprev, const double *F, const double *phi, int nf, double dt,
-                      double *r, cudaStream_t s);
+                      double *r, cudaStream_t s, int zero_inside = 0);
 
 template <typename T>
 void launch_restrict(const T *rf, int nf, T *bc, int nc, cudaStream_t s);
