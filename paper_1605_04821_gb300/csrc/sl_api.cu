@@ -137,6 +137,7 @@ struct sl_hjb {
   double rec_t0 = 0.0, rec_dt = 0.0;
   bool rec_valid = false;
   AmgEngine amg;                               // precond 1
+  ArgminITaps *itaps = nullptr;                // interior-class taps for the argmin's parameter
   long long amg_gen = 0;                       // bumped by every AMG setup (its sizes change)
   std::vector<void *> allocs;
   std::string err;
@@ -258,7 +259,7 @@ sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_
   a.screen = h->o.argmin_screen;
   CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
-  CK(launch_argmin(a, s));
+  CK(launch_argmin(a, *h->itaps, s));
   CK(cudaMemcpyAsync(h->h_changes, h->d_changes, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1114,6 +1115,7 @@ void sl_hjb_destroy(sl_hjb *h) {
   if (h->h_changes) cudaFreeHost(h->h_changes);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->h_count) cudaFreeHost(h->h_count);
+  delete h->itaps;
   delete h;
 }
 
@@ -1226,6 +1228,17 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   std::vector<float> w32(ft.w.begin(), ft.w.end()), W32(ft.W.begin(), ft.W.end()),
       ws32(ft.ws.begin(), ft.ws.end()), c32(ft.c.begin(), ft.c.end()),
       phi32(h->phi.begin(), h->phi.end());
+  // interior-class taps of every control for the argmin (the class path only)
+  h->itaps = new (std::nothrow) ArgminITaps();
+  if (!h->itaps) return fail(h, SL_ENOMEM, "host allocation failed");
+  h->itaps->n = 0;
+  if (!h->general && h->n - 1 >= 2 * ft.B && size_t(h->K) * ft.tmax <= size_t(kITapMax)) {
+    for (int k = 0; k < h->K; ++k) {
+      const int e = ft.entry(k, ft.B, ft.B);
+      for (int t = 0; t < ft.tmax; ++t) h->itaps->t[k * ft.tmax + t] = pk32[size_t(e) * ft.tmax + t];
+    }
+    h->itaps->n = h->K * ft.tmax;
+  }
   UP(h->d_lin, lin);
   UP(h->d_slin, slin);
   UP(h->d_off, off);

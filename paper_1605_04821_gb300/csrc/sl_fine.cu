@@ -123,13 +123,31 @@ __device__ __forceinline__ float eval_smem32(const FineTab &tab, int e, const fl
   return acc;
 }
 
+// The same screen for an interior-class row, with the taps from the kernel parameter.
+template <int TMAX>
+__device__ __forceinline__ float eval_itap32(const ArgminITaps &it, int k, const float *__restrict__ xs,
+                                             int sidx, float x0, float &S) {
+  float acc = 0.f, sa = 0.f;
+#pragma unroll
+  for (int t = 0; t < TMAX; ++t) {
+    const int2 p = it.t[k * TMAX + t];
+    const float dd = xs[sidx + p.x] - x0;
+    const float w = __int_as_float(p.y);
+    acc = fmaf(w, dd, acc);
+    sa = fmaf(w, fabsf(dd), sa);
+  }
+  S = sa;
+  return acc;
+}
+
 __device__ __forceinline__ void cand_push(unsigned long long &cand, int &ncand, bool &overflow, int k) {
   if (ncand < kMaxCand) cand |= (unsigned long long)k << (8 * ncand++);
   else overflow = true;
 }
 
 template <int SCREEN, int TMAX>
-__global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
+__global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ ArgminArgs a,
+                                                     const __grid_constant__ ArgminITaps it) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned red_cnt[kTX * kTY / 32];
   __shared__ float red_max[kTX * kTY / 32];
@@ -201,12 +219,14 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
       const float Ef = u * ((nf + 3.0f) * Fabs * 1.001f + 3.0f * float(a.cmax) * fabsf(xj32) * 1.001f);
       const float eta = 2.0f * u * Dmax * 1.001f + 1e-30f;
       const float x0 = xs32[sidx];
+      const bool itap = TMAX > 0 && it.n > 0 && q1 == tab.B && q2 == tab.B;
       const float tw_rel = float(a.tie_rel) * 2.0f;
       float Umin = INFINITY, Lmin = INFINITY;
       for (int k = 0; k < tab.K; ++k) {
         const int e = (k * tab.Q + q2) * tab.Q + q1;
         float S;
-        const float acc = eval_smem32<TMAX>(tab, e, xs32, sidx, x0, S);
+        const float acc = itap ? eval_itap32<TMAX>(it, k, xs32, sidx, x0, S)
+                               : eval_smem32<TMAX>(tab, e, xs32, sidx, x0, S);
         float f = 0.f;
         for (int mm = 0; mm < nf && mm < 4; ++mm) f = fmaf(__ldg(a.phi32 + k * nf + mm), Fv32[mm], f);
         const float v = acc + fmaf(tab.c32[k], xj32, f);
@@ -305,22 +325,23 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(ArgminArgs a) {
 }
 
 template <int SCREEN, int TMAX>
-cudaError_t argmin_launch(const ArgminArgs &a, dim3 grd, dim3 blk, size_t bytes, cudaStream_t s) {
+cudaError_t argmin_launch(const ArgminArgs &a, const ArgminITaps &it, dim3 grd, dim3 blk, size_t bytes,
+                          cudaStream_t s) {
   note_launch();
-  k_argmin<SCREEN, TMAX><<<grd, blk, bytes, s>>>(a);
+  k_argmin<SCREEN, TMAX><<<grd, blk, bytes, s>>>(a, it);
   return cudaGetLastError();
 }
 
-cudaError_t launch_argmin(const ArgminArgs &a, cudaStream_t s) {
+cudaError_t launch_argmin(const ArgminArgs &a, const ArgminITaps &it, cudaStream_t s) {
   dim3 blk(kTX, kTY), grd((a.tab.m + kTX - 1) / kTX, (a.tab.m + kTY - 1) / kTY);
   const size_t bytes = size_t(a.SW) * a.SH * (a.screen ? sizeof(float) : sizeof(double));
-  if (!a.screen) return argmin_launch<0, 0>(a, grd, blk, bytes, s);
+  if (!a.screen) return argmin_launch<0, 0>(a, it, grd, blk, bytes, s);
   switch (a.tab.tmax) {
-    case 8: return argmin_launch<1, 8>(a, grd, blk, bytes, s);
-    case 12: return argmin_launch<1, 12>(a, grd, blk, bytes, s);
-    case 16: return argmin_launch<1, 16>(a, grd, blk, bytes, s);
-    case 20: return argmin_launch<1, 20>(a, grd, blk, bytes, s);
-    default: return argmin_launch<1, 0>(a, grd, blk, bytes, s);
+    case 8: return argmin_launch<1, 8>(a, it, grd, blk, bytes, s);
+    case 12: return argmin_launch<1, 12>(a, it, grd, blk, bytes, s);
+    case 16: return argmin_launch<1, 16>(a, it, grd, blk, bytes, s);
+    case 20: return argmin_launch<1, 20>(a, it, grd, blk, bytes, s);
+    default: return argmin_launch<1, 0>(a, it, grd, blk, bytes, s);
   }
 }
 

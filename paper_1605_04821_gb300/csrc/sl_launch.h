@@ -46,10 +46,20 @@ struct ArgminArgs {
   int screen;
 };
 
+// The packed taps {tile offset, fp32 weight bits} of the interior class of every control,
+// [k*tmax + t], passed as a kernel parameter: rows of the interior class (all but a band of
+// width B along the boundary) read them through the constant cache, every lane of a warp the
+// same entry, instead of through L1.  n = 0 when they do not fit (K * tmax > kITapMax).
+constexpr int kITapMax = 3584;  // 28 KB of kernel parameters
+struct ArgminITaps {
+  int n;
+  int2 t[kITapMax];
+};
+
 void launch_coef(const double *G, int nf, int nq, const double *tau, const double *Psi, int npsi,
                  const double *tau_psi, int n, double *F, float *F32, double *Xext, double *Xb,
                  cudaStream_t s);
-cudaError_t launch_argmin(const ArgminArgs &a, cudaStream_t s);
+cudaError_t launch_argmin(const ArgminArgs &a, const ArgminITaps &it, cudaStream_t s);
 
 // slin: staged-tile tap offsets (pitch SW = 32 + 2 halo), the same table as the argmin's.
 template <typename T>
