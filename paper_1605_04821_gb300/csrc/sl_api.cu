@@ -287,6 +287,7 @@ CoarseLev<T> lev_view(sl_hjb *h, int l) {
   L.cnt = c.cnt;
   L.cdiag = pick<T>(c.cdiag64, c.cdiag32);
   L.ctmax = c.ctmax;
+  L.nk = h->K;
   L.ewin = pick<T>(c.ewin64, c.ewin32);
   L.erow = c.erow;
   L.cap = c.cap;

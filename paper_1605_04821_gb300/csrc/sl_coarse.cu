@@ -248,19 +248,36 @@ __device__ __forceinline__ void coarse_expl_row(const CoarseLev<T> &L, int slot,
 
 // Class rows from a shared-memory tile of x: 32 x 32 rows per block (four per thread, one
 // column) plus a halo of R (the level's stencil reach).  Class taps are packed {tile offset,
-// weight}.
+// weight}.  With STAB the block first copies the level's whole class table (nk * ctmax taps,
+// 12-21 KB in FP32 at 2049^2) into shared memory beside the tile, in the same pass as the
+// staging: on the small levels, where an SM runs one or two tiles, the table is cold in L1
+// and every group of global tap loads cost an L2 round trip.
 constexpr int kCRowsY = 32;
+constexpr size_t kClassTabSmemMax = 48 * 1024;  // larger tables stay in global memory
+constexpr int kClassTabSmemTiles = 256;          // only levels with at most this many tiles
 
-template <typename T, int OP>
+template <typename T>
+__host__ __device__ inline size_t coarse_tile_bytes(int R) {
+  return (size_t(32 + 2 * R) * (kCRowsY + 2 * R) * sizeof(T) + 15) / 16 * 16;
+}
+
+template <typename T, int OP, int STAB>
 __global__ void __launch_bounds__(256) k_coarse_op(CoarseLev<T> L, const int *__restrict__ nexpl_dev,
                                                    int tiles_x, int tiles, T omega, const T *__restrict__ x,
                                                    const T *__restrict__ b, T *__restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (int(blockIdx.x) < tiles) {
+    using PK = typename ClassTap<T>::Packed;
     T *xs = reinterpret_cast<T *>(smem_raw);
+    PK *ts = reinterpret_cast<PK *>(smem_raw + coarse_tile_bytes<T>(L.R));
     const int R = L.R, SW = 32 + 2 * R, SH = kCRowsY + 2 * R;
     const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (STAB && OP != OP_JACOBI0) {
+      const PK *src = ClassTap<T>::table(L);
+      const int nt_all = L.nk * L.ctmax;
+      for (int i = threadIdx.x; i < nt_all; i += blockDim.x) ts[i] = src[i];
+    }
     if (OP != OP_JACOBI0) {
       const int o1 = 1 + bx * 32 - R, o2 = 1 + by * kCRowsY - R;
       for (int r = ty; r < SH; r += 8) {
@@ -290,12 +307,23 @@ __global__ void __launch_bounds__(256) k_coarse_op(CoarseLev<T> L, const int *__
       const int sidx = (ty + 8 * r + R) * SW + tx + R;
       T acc = T(0);
       const int nt = L.cnt[k];
+      if (STAB) {
+        const PK *tk = ts + k * L.ctmax;
 #pragma unroll 4
-      for (int t = 0; t < nt; ++t) {
-        int off;
-        T w;
-        ClassTap<T>::get(L, k * L.ctmax + t, off, w);
-        acc = fma(w, xs[sidx + off], acc);
+        for (int t = 0; t < nt; ++t) {
+          int off;
+          T w;
+          ClassTap<T>::unpack(tk[t], off, w);
+          acc = fma(w, xs[sidx + off], acc);
+        }
+      } else {
+#pragma unroll 4
+        for (int t = 0; t < nt; ++t) {
+          int off;
+          T w;
+          ClassTap<T>::get(L, k * L.ctmax + t, off, w);
+          acc = fma(w, xs[sidx + off], acc);
+        }
       }
       if (OP == OP_APPLY) y[j] = acc;
       else if (OP == OP_RESID) y[j] = b[j] - acc;
@@ -346,14 +374,19 @@ void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T ome
   const int tx = (L.m + 31) / 32, tiles = tx * ((L.m + kCRowsY - 1) / kCRowsY);
   const int eg = std::max(1, std::min(2 * kRedBlocks, (4 * L.cap + 255) / 256));  // 4 threads per explicit row
   const int grid = tiles + eg;
-  const size_t bytes = op == OP_JACOBI0 ? 0 : size_t(32 + 2 * L.R) * (kCRowsY + 2 * L.R) * sizeof(T);
+  const size_t tab_bytes = size_t(L.nk) * L.ctmax * sizeof(typename ClassTap<T>::Packed);
+  const bool stab = op != OP_JACOBI0 && L.nk > 0 && tab_bytes <= kClassTabSmemMax && tiles <= kClassTabSmemTiles;
+  const size_t bytes = op == OP_JACOBI0 ? 0 : coarse_tile_bytes<T>(L.R) + (stab ? tab_bytes : 0);
   note_launch();
+#define SL_COARSE_LAUNCH(OPV, ST) \
+  k_coarse_op<T, OPV, ST><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y)
   switch (op) {
-    case OP_APPLY: k_coarse_op<T, OP_APPLY><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
-    case OP_RESID: k_coarse_op<T, OP_RESID><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
-    case OP_JACOBI: k_coarse_op<T, OP_JACOBI><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
-    default: k_coarse_op<T, OP_JACOBI0><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y); break;
+    case OP_APPLY: if (stab) SL_COARSE_LAUNCH(OP_APPLY, 1); else SL_COARSE_LAUNCH(OP_APPLY, 0); break;
+    case OP_RESID: if (stab) SL_COARSE_LAUNCH(OP_RESID, 1); else SL_COARSE_LAUNCH(OP_RESID, 0); break;
+    case OP_JACOBI: if (stab) SL_COARSE_LAUNCH(OP_JACOBI, 1); else SL_COARSE_LAUNCH(OP_JACOBI, 0); break;
+    default: SL_COARSE_LAUNCH(OP_JACOBI0, 0); break;
   }
+#undef SL_COARSE_LAUNCH
 }
 template void launch_coarse_op<double>(int, const CoarseLev<double> &, const int *, double,
                                        const double *, const double *, double *, cudaStream_t);
@@ -584,10 +617,13 @@ template void launch_coarsest_apply<float>(const float *, int, const float *, fl
 template <typename T>
 static cudaError_t prepare_coarse_T() {
   const void *fs[] = {reinterpret_cast<const void *>(k_rap_explicit<T>),
-                      reinterpret_cast<const void *>(k_coarse_op<T, OP_APPLY>),
-                      reinterpret_cast<const void *>(k_coarse_op<T, OP_RESID>),
-                      reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI>),
-                      reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI0>)};
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_APPLY, 0>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_RESID, 0>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI, 0>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI0, 0>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_APPLY, 1>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_RESID, 1>),
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI, 1>)};
   for (const void *f : fs) {
     cudaError_t e = allow_dynamic_smem(f);
     if (e != cudaSuccess) return e;

@@ -110,6 +110,7 @@ struct CoarseLev {
   const int32_t *cnt;      // [k]
   const T *cdiag;          // [k]
   int ctmax;
+  int nk;                  // number of classes (controls): the class tables hold nk * ctmax taps
   // explicit rows
   const T *ewin;           // [e*cap + slot], e = (dy+R)*(2R+1) + (dx+R)
   const int32_t *erow;     // [slot] linear full-grid index of the row
@@ -136,15 +137,27 @@ template <> struct PackedTap<double> {
 
 template <typename T> struct ClassTap;
 template <> struct ClassTap<float> {
+  using Packed = int2;
+  static __device__ __forceinline__ const int2 *table(const CoarseLev<float> &L) { return L.cpk32; }
   static __device__ __forceinline__ void get(const CoarseLev<float> &L, int ix, int &off, float &w) {
     const int2 p = __ldg(L.cpk32 + ix);
     off = p.x;
     w = __int_as_float(p.y);
   }
+  static __device__ __forceinline__ void unpack(const int2 &p, int &off, float &w) {
+    off = p.x;
+    w = __int_as_float(p.y);
+  }
 };
 template <> struct ClassTap<double> {
+  using Packed = longlong2;
+  static __device__ __forceinline__ const longlong2 *table(const CoarseLev<double> &L) { return L.cpk64; }
   static __device__ __forceinline__ void get(const CoarseLev<double> &L, int ix, int &off, double &w) {
     const longlong2 p = __ldg(L.cpk64 + ix);
+    off = int(p.x);
+    w = __longlong_as_double(p.y);
+  }
+  static __device__ __forceinline__ void unpack(const longlong2 &p, int &off, double &w) {
     off = int(p.x);
     w = __longlong_as_double(p.y);
   }

@@ -350,12 +350,15 @@ cudaError_t launch_argmin(const ArgminArgs &a, const ArgminITaps &it, cudaStream
 // zero boundary entries, so boundary taps drop out as they belong to the right-hand side).
 // Diagonal entry d_j = 1 + dt (W - c_k - w_self).
 //
-// Each block stages a 32 x 16 tile of x plus a halo of the longest tap in shared memory; each
-// thread computes two rows of one column (i2 = base + ty and base + ty + 8) independently (the
-// policy changes too often along a column for rows to share their taps).  Taps are packed
-// {tile offset, weight} and the loop runs over the padded table width TMAX (unused slots carry
-// weight 0 at offset 0), fully unrolled, so all table loads of a row are issued together.
-constexpr int kOpRowsY = 16;
+// Each block stages a 32 x 32 tile of x plus a halo of the longest tap in shared memory; each
+// thread computes kFineRPT = 4 rows of one column (i2 = base + ty + 8 r) independently (the
+// policy changes too often along a column for rows to share their taps).  With a halo of ten
+// nodes the 32 x 32 tile stages 2.6 values per row against 3.7 for a 32 x 16 one, which took
+// the FP32 apply at 2049^2 from 36 to 33 us.  The rows' controls are read before the tile is
+// staged.  Taps are packed {tile offset, weight} and the loop runs over the padded table width
+// TMAX (unused slots carry weight 0 at offset 0), fully unrolled, so all table loads of a row
+// are issued together.
+constexpr int kFineRPT = 4;  // rows per thread: a block covers 32 x (8 kFineRPT) rows
 
 template <typename T, int OP>
 __device__ __forceinline__ void fine_finish(T *y, const T *b, int j, T xj, T ax, T od) {
@@ -365,14 +368,20 @@ __device__ __forceinline__ void fine_finish(T *y, const T *b, int j, T xj, T ax,
 }
 
 // Stages rows [o2, o2 + SH) x columns [o1, o1 + SW) of a full-grid vector into shared memory,
-// with zeros outside the grid; tiles whose halo lies inside the grid skip the bounds checks.
+// with zeros outside the grid; tiles whose halo lies inside the grid skip the bounds checks
+// and walk two row pointers, so that the copies of one row need no index arithmetic.
 template <typename T>
 __device__ __forceinline__ void stage_tile(T *xs, const T *__restrict__ x, int n, int o1, int o2, int SW,
                                            int SH, int tx, int ty) {
   if (o1 >= 0 && o2 >= 0 && o1 + SW <= n && o2 + SH <= n) {
-    const T *src = x + size_t(o2) * n + o1;
-    for (int r = ty; r < SH; r += 8)
-      for (int c = tx; c < SW; c += 32) xs[r * SW + c] = src[size_t(r) * n + c];
+    const T *src = x + (size_t(o2) + ty) * n + o1 + tx;
+    T *dst = xs + ty * SW + tx;
+    const size_t gstep = size_t(8) * n;
+    const int sstep = 8 * SW, cols = SW - tx;
+    for (int r = ty; r < SH; r += 8, src += gstep, dst += sstep) {
+#pragma unroll 2
+      for (int c = 0; c < cols; c += 32) dst[c] = src[c];
+    }
   } else {
     for (int r = ty; r < SH; r += 8) {
       const int g2 = o2 + r;
@@ -385,7 +394,7 @@ __device__ __forceinline__ void stage_tile(T *xs, const T *__restrict__ x, int n
   }
 }
 
-template <typename T, int OP, int TMAX>
+template <typename T, int OP, int TMAX, int RPT = kFineRPT>
 __global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__restrict__ policy, T dt, T omega,
                                                  const T *__restrict__ x, const T *__restrict__ b,
                                                  T *__restrict__ y, int halo, int SW) {
@@ -393,19 +402,32 @@ __global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__r
   T *xs = reinterpret_cast<T *>(smem_raw);
   const int n = tab.n, m = tab.m;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i1 = 1 + blockIdx.x * 32 + tx;
+  // the rows' controls are read before the tile is staged, so that both loads are in flight
+  int kr[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int i2 = 1 + blockIdx.y * (8 * RPT) + ty + 8 * r;
+    kr[r] = i1 <= m && i2 <= m ? int(policy[(i2 - 1) * m + (i1 - 1)]) : 0;
+  }
   if (OP != OP_JACOBI0) {
-    stage_tile<T>(xs, x, n, 1 + blockIdx.x * 32 - halo, 1 + blockIdx.y * kOpRowsY - halo, SW,
-                  kOpRowsY + 2 * halo, tx, ty);
+    stage_tile<T>(xs, x, n, 1 + blockIdx.x * 32 - halo, 1 + blockIdx.y * (8 * RPT) - halo, SW,
+                  (8 * RPT) + 2 * halo, tx, ty);
     __syncthreads();
   }
-  const int i1 = 1 + blockIdx.x * 32 + tx;
   if (i1 > m) return;
+  // a block whose rows all lie in the interior class (q1 = q2 = B) finds its table entries
+  // without the boundary-distance classification
+  const int B = tab.B, Q = tab.Q;
+  const int r1 = blockIdx.x * 32, r2 = blockIdx.y * (8 * RPT);
+  const bool inner = !tab.general && n - 1 >= 2 * B && 1 + r1 >= B && r1 + 32 <= n - 1 - B &&
+                     1 + r2 >= B && r2 + 8 * RPT <= n - 1 - B;
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int i2 = 1 + blockIdx.y * kOpRowsY + ty + 8 * r;
+  for (int r = 0; r < RPT; ++r) {
+    const int i2 = 1 + blockIdx.y * (8 * RPT) + ty + 8 * r;
     if (i2 > m) continue;
-    const int k = policy[(i2 - 1) * m + (i1 - 1)];
-    const int e = fine_row_entry(tab, k, i1, i2);
+    const int k = kr[r];
+    const int e = inner ? (k * Q + B) * Q + B : fine_row_entry(tab, k, i1, i2);
     const int j = i2 * n + i1;
     if (OP == OP_JACOBI0) {
       y[j] = tab_od<T>(tab)[e] * b[j];
@@ -439,8 +461,8 @@ __global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__r
 template <typename T, int OP>
 void fine_op_dispatch(const FineTab &tab, const uint8_t *policy, T dt, T omega, const T *x, const T *b,
                       T *y, int halo, int SW, cudaStream_t s) {
-  dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + kOpRowsY - 1) / kOpRowsY);
-  const size_t bytes = OP == OP_JACOBI0 ? 0 : size_t(SW) * (kOpRowsY + 2 * halo) * sizeof(T);
+  dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + 8 * kFineRPT - 1) / (8 * kFineRPT));
+  const size_t bytes = OP == OP_JACOBI0 ? 0 : size_t(SW) * (8 * kFineRPT + 2 * halo) * sizeof(T);
   note_launch();
   switch (tab.tmax) {
     case 8: k_fine_op<T, OP, 8><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
