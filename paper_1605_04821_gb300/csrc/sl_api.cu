@@ -78,6 +78,10 @@ struct sl_hjb {
   double *d_phi = nullptr, *d_phimax = nullptr, *d_tau = nullptr, *d_tpsi = nullptr;
   double *d_od64 = nullptr;
   float *d_od32 = nullptr;
+  int4 *d_ipk32 = nullptr;          // interior taps, tap-major (FineTab::ipk32)
+  longlong2 *d_ipk64 = nullptr;
+  double *d_iWc64 = nullptr, *d_iod64 = nullptr;
+  float *d_iWc32 = nullptr, *d_iod32 = nullptr;
   // general fine level (x-dependent diffusion): drift tables, per-row diffusion taps, and the
   // per-row table assembled for the current policy (h->tab then describes the latter)
   bool general = false;
@@ -442,7 +446,7 @@ sl_status build_hierarchy(sl_hjb *h, double dt, cudaStream_t s) {
   if (!h->class_valid || h->class_dt != dt) {
     sl_status st = build_class_tables(h, dt);
     if (st != SL_OK) return st;
-    if (!h->general) launch_fine_od(h->tab, dt, h->o.omega, h->d_od64, h->d_od32, s);
+    if (!h->general) launch_fine_od(h->tab, dt, h->o.omega, h->d_od64, h->d_od32, h->d_iod64, h->d_iod32, s);
     CK(cudaGetLastError());
   }
   sl_status st = (h->o.precision == 0) ? build_hierarchy_T<double>(h, dt, s)
@@ -1264,6 +1268,36 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   t.lin = h->d_lin; t.w64 = h->d_w64; t.w32 = h->d_w32; t.nt = h->d_nt; t.W64 = h->d_W64;
   t.W32 = h->d_W32; t.ws64 = h->d_ws64; t.ws32 = h->d_ws32; t.c64 = h->d_c64; t.c32 = h->d_c32;
   t.pk32 = h->d_pk32; t.pk64 = h->d_pk64;
+  t.ipk32 = nullptr; t.ipk64 = nullptr; t.iWc64 = nullptr; t.iWc32 = nullptr;
+  t.iod64 = nullptr; t.iod32 = nullptr;
+  if (!h->general && h->n - 1 >= 2 * ft.B && ft.tmax % 2 == 0) {
+    // the interior entries again, tap-major with the controls adjacent
+    const int K = h->K, tm = ft.tmax;
+    std::vector<int4> ipk32(size_t(tm / 2) * K);
+    std::vector<longlong2> ipk64(size_t(tm) * K);
+    std::vector<double> iWc64(K);
+    std::vector<float> iWc32(K);
+    for (int k = 0; k < K; ++k) {
+      const int e = ft.entry(k, ft.B, ft.B);
+      for (int tt = 0; tt < tm; ++tt) {
+        const int2 p = pk32[size_t(e) * tm + tt];
+        int4 &q = ipk32[size_t(tt / 2) * K + k];
+        if (tt % 2 == 0) { q.x = p.x; q.y = p.y; } else { q.z = p.x; q.w = p.y; }
+        ipk64[size_t(tt) * K + k] = pk64[size_t(e) * tm + tt];
+      }
+      iWc64[k] = ft.W[e] - ft.c[k];
+      const float Wf = W32[e], cf = c32[k];
+      iWc32[k] = Wf - cf;
+    }
+    UP(h->d_ipk32, ipk32);
+    UP(h->d_ipk64, ipk64);
+    UP(h->d_iWc64, iWc64);
+    UP(h->d_iWc32, iWc32);
+    AL(h->d_iod64, size_t(K));
+    AL(h->d_iod32, size_t(K));
+    t.ipk32 = h->d_ipk32; t.ipk64 = h->d_ipk64; t.iWc64 = h->d_iWc64; t.iWc32 = h->d_iWc32;
+    t.iod64 = h->d_iod64; t.iod32 = h->d_iod32;
+  }
   AL(h->d_od64, size_t(h->K) * ft.Q * ft.Q);
   AL(h->d_od32, size_t(h->K) * ft.Q * ft.Q);
   t.od64 = h->d_od64; t.od32 = h->d_od32;

@@ -68,6 +68,16 @@ struct FineTab {
   const int2 *pk32;       // [e*tmax + t] {staged-tile offset, fp32 weight bits}
   const longlong2 *pk64;  // [e*tmax + t] {staged-tile offset, fp64 weight bits}
   int general;            // 1: x-dependent sigma; entry e = interior row, assembled per policy
+  // The interior class (q1 = q2 = B) of every control again, tap-major with the controls
+  // adjacent, so that the rows of a warp, whose controls are few and close together, find
+  // tap t of all their controls in one or two cache lines (null on a general level or for an
+  // odd tap stride).
+  const int4 *ipk32;      // [(t / 2) * K + k] {offset_t, w_t bits, offset_t+1, w_t+1 bits}
+  const longlong2 *ipk64; // [t * K + k] {offset, w bits}
+  const double *iWc64;    // [k] W_e - c_k of the interior entry e of control k
+  const float *iWc32;     // [k] the same difference taken in FP32 (W32[e] - c32[k])
+  const double *iod64;    // [k] od of the interior entry
+  const float *iod32;
 };
 
 // Table entry of row (i1, i2) whose control is k: the (control, boundary class) entry, or, on

@@ -394,6 +394,39 @@ __device__ __forceinline__ void stage_tile(T *xs, const T *__restrict__ x, int n
   }
 }
 
+// Sum of w_t x_{j+o_t} over the taps of control k's interior entry, from the tap-major table;
+// the taps are added in the order of the entry (t = 0, 1, ...), as on the general path.
+template <typename T, int TMAX> struct InnerTaps;
+template <int TMAX> struct InnerTaps<float, TMAX> {
+  static __device__ __forceinline__ float sum(const FineTab &tab, int k, const float *xs, int sidx) {
+    const int4 *p = tab.ipk32 + k;
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t < TMAX / 2; ++t) {
+      const int4 q = __ldg(p + t * tab.K);
+      acc = fmaf(__int_as_float(q.y), xs[sidx + q.x], acc);
+      acc = fmaf(__int_as_float(q.w), xs[sidx + q.z], acc);
+    }
+    return acc;
+  }
+  static __device__ __forceinline__ float Wc(const FineTab &tab, int k) { return tab.iWc32[k]; }
+  static __device__ __forceinline__ float od(const FineTab &tab, int k) { return tab.iod32[k]; }
+};
+template <int TMAX> struct InnerTaps<double, TMAX> {
+  static __device__ __forceinline__ double sum(const FineTab &tab, int k, const double *xs, int sidx) {
+    const longlong2 *p = tab.ipk64 + k;
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < TMAX; ++t) {
+      const longlong2 q = __ldg(p + t * tab.K);
+      acc = fma(__longlong_as_double(q.y), xs[sidx + int(q.x)], acc);
+    }
+    return acc;
+  }
+  static __device__ __forceinline__ double Wc(const FineTab &tab, int k) { return tab.iWc64[k]; }
+  static __device__ __forceinline__ double od(const FineTab &tab, int k) { return tab.iod64[k]; }
+};
+
 template <typename T, int OP, int TMAX, int RPT = kFineRPT>
 __global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__restrict__ policy, T dt, T omega,
                                                  const T *__restrict__ x, const T *__restrict__ b,
@@ -416,19 +449,32 @@ __global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__r
     __syncthreads();
   }
   if (i1 > m) return;
-  // a block whose rows all lie in the interior class (q1 = q2 = B) finds its table entries
-  // without the boundary-distance classification
-  const int B = tab.B, Q = tab.Q;
+  // a block whose rows all lie in the interior class (q1 = q2 = B) reads the tap-major
+  // interior table, indexed by the control alone
+  const int B = tab.B;
   const int r1 = blockIdx.x * 32, r2 = blockIdx.y * (8 * RPT);
-  const bool inner = !tab.general && n - 1 >= 2 * B && 1 + r1 >= B && r1 + 32 <= n - 1 - B &&
-                     1 + r2 >= B && r2 + 8 * RPT <= n - 1 - B;
+  const bool inner = TMAX > 0 && tab.ipk32 != nullptr && !tab.general && n - 1 >= 2 * B &&
+                     1 + r1 >= B && r1 + 32 <= n - 1 - B && 1 + r2 >= B && r2 + 8 * RPT <= n - 1 - B;
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int i2 = 1 + blockIdx.y * (8 * RPT) + ty + 8 * r;
     if (i2 > m) continue;
     const int k = kr[r];
-    const int e = inner ? (k * Q + B) * Q + B : fine_row_entry(tab, k, i1, i2);
     const int j = i2 * n + i1;
+    if (inner) {
+      if (OP == OP_JACOBI0) {
+        y[j] = InnerTaps<T, TMAX>::od(tab, k) * b[j];
+        continue;
+      }
+      const int sidx = (ty + 8 * r + halo) * SW + tx + halo;
+      const T acc = InnerTaps<T, TMAX>::sum(tab, k, xs, sidx);
+      const T xj = xs[sidx];
+      const T diag = T(1) + dt * InnerTaps<T, TMAX>::Wc(tab, k);
+      fine_finish<T, OP>(y, b, j, xj, diag * xj - dt * acc,
+                         OP == OP_JACOBI ? InnerTaps<T, TMAX>::od(tab, k) : T(0));
+      continue;
+    }
+    const int e = fine_row_entry(tab, k, i1, i2);
     if (OP == OP_JACOBI0) {
       y[j] = tab_od<T>(tab)[e] * b[j];
       continue;
@@ -492,19 +538,26 @@ template void launch_fine_op<float>(int, const FineTab &, const int32_t *, const
                                     cudaStream_t);
 
 // omega / d_e for every fine table entry, d_e = 1 + dt (W_e - c_k - w_self,e) (the Jacobi scale).
-__global__ void k_fine_od(FineTab tab, double dt, double omega, int E, double *od64, float *od32) {
+// The interior entry of each control (q1 = q2 = B) also goes to iod[k] when iod64 is given.
+__global__ void k_fine_od(FineTab tab, double dt, double omega, int E, double *od64, float *od32,
+                          double *iod64, float *iod32) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
     const int k = e / (tab.Q * tab.Q);
     const double d64 = 1.0 + dt * (tab.W64[e] - tab.c64[k] - tab.ws64[e]);
     const float d32 = 1.0f + float(dt) * (tab.W32[e] - tab.c32[k] - tab.ws32[e]);
     od64[e] = omega / d64;
     od32[e] = float(omega) / d32;
+    if (iod64 && e % (tab.Q * tab.Q) == tab.B * tab.Q + tab.B) {
+      iod64[k] = od64[e];
+      iod32[k] = od32[e];
+    }
   }
 }
-void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, float *od32, cudaStream_t s) {
+void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, float *od32,
+                    double *iod64, float *iod32, cudaStream_t s) {
   const int E = tab.K * tab.Q * tab.Q;
   note_launch();
-  k_fine_od<<<(E + 255) / 256, 256, 0, s>>>(tab, dt, omega, E, od64, od32);
+  k_fine_od<<<(E + 255) / 256, 256, 0, s>>>(tab, dt, omega, E, od64, od32, iod64, iod32);
 }
 
 // ----------------------------------------------------------------------------- HJB residual

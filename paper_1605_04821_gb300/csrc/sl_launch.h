@@ -67,7 +67,8 @@ void launch_fine_op(int op, const FineTab &tab, const int32_t *slin, const uint8
                     T omega, const T *x, const T *b, T *y, int halo, int SW, cudaStream_t s);
 
 // Jacobi scale omega / d_e of every fine table entry for step size dt (into od64 / od32).
-void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, float *od32, cudaStream_t s);
+void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, float *od32,
+                    double *iod64, float *iod32, cudaStream_t s);
 
 // r = U_prev - X + dt (L X + c X + f) for the current policy (interior), FP64.  With
 // zero_inside = R > 0 the caller promises X = 0 on the interior and R >= the longest tap:
