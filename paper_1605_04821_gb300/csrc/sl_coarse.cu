@@ -223,6 +223,49 @@ __device__ __forceinline__ void coarse_class_row(const CoarseLev<T> &L, int k, i
   coarse_finish<T, OP>(y, x, b, j, acc, d, omega);
 }
 
+// Partial product of explicit row `slot` (centre j = (I1, I2)) with x over the window rows
+// dy = ylo + part, ylo + part + step, ...: sum of w(dy, dx) x_{j + dy n + dx}, dx ascending
+// within a row.  With RR > 0 the reach is a compile-time constant and each window row is
+// unrolled with a predicate per entry, so its 2 RR + 1 weight and value loads are in flight
+// together (with runtime bounds every FMA waited for its own pair of loads); RR = 0 reads the
+// reach from the level.  Both orders of summation are the same.
+template <typename T, int RR>
+__device__ __forceinline__ T expl_window_sum(const CoarseLev<T> &L, int slot, int j, int I1, int I2,
+                                             const T *__restrict__ x, int part, int step) {
+  const int R = RR > 0 ? RR : L.R, Wd = 2 * R + 1;
+  const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
+  const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
+  T acc = T(0);
+  for (int dy = ylo + part; dy <= yhi; dy += step) {
+    const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
+    const T *xrow = x + j + dy * L.n;
+    if (RR > 0) {
+#pragma unroll
+      for (int dx = -RR; dx <= RR; ++dx)
+        if (dx >= xlo && dx <= xhi) acc = fma(wrow[ptrdiff_t(dx) * L.cap], __ldg(xrow + dx), acc);
+    } else {
+      for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[ptrdiff_t(dx) * L.cap], __ldg(xrow + dx), acc);
+    }
+  }
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T expl_window_sum_any(const CoarseLev<T> &L, int slot, int j, int I1, int I2,
+                                                 const T *__restrict__ x, int part, int step) {
+  switch (L.R) {
+    case 1: return expl_window_sum<T, 1>(L, slot, j, I1, I2, x, part, step);
+    case 2: return expl_window_sum<T, 2>(L, slot, j, I1, I2, x, part, step);
+    case 3: return expl_window_sum<T, 3>(L, slot, j, I1, I2, x, part, step);
+    case 4: return expl_window_sum<T, 4>(L, slot, j, I1, I2, x, part, step);
+    case 5: return expl_window_sum<T, 5>(L, slot, j, I1, I2, x, part, step);
+    case 6: return expl_window_sum<T, 6>(L, slot, j, I1, I2, x, part, step);
+    case 7: return expl_window_sum<T, 7>(L, slot, j, I1, I2, x, part, step);
+    case 8: return expl_window_sum<T, 8>(L, slot, j, I1, I2, x, part, step);
+    default: return expl_window_sum<T, 0>(L, slot, j, I1, I2, x, part, step);
+  }
+}
+
 template <typename T, int OP>
 __device__ __forceinline__ void coarse_expl_row(const CoarseLev<T> &L, int slot, T omega,
                                                 const T *__restrict__ x, const T *__restrict__ b,
@@ -235,14 +278,7 @@ __device__ __forceinline__ void coarse_expl_row(const CoarseLev<T> &L, int slot,
     y[j] = omega * b[j] / d;
     return;
   }
-  const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
-  const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
-  T acc = T(0);
-  for (int dy = ylo; dy <= yhi; ++dy) {
-    const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
-    const T *xrow = x + j + dy * L.n;
-    for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[size_t(dx) * L.cap], __ldg(xrow + dx), acc);
-  }
+  const T acc = expl_window_sum_any<T>(L, slot, j, I1, I2, x, 0, 1);
   coarse_finish<T, OP>(y, x, b, j, acc, d, omega);
 }
 
@@ -262,7 +298,7 @@ __host__ __device__ inline size_t coarse_tile_bytes(int R) {
 }
 
 template <typename T, int OP, int STAB>
-__global__ void __launch_bounds__(256) k_coarse_op(CoarseLev<T> L, const int *__restrict__ nexpl_dev,
+__global__ void __launch_bounds__(256, 6) k_coarse_op(CoarseLev<T> L, const int *__restrict__ nexpl_dev,
                                                    int tiles_x, int tiles, T omega, const T *__restrict__ x,
                                                    const T *__restrict__ b, T *__restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -332,9 +368,9 @@ __global__ void __launch_bounds__(256) k_coarse_op(CoarseLev<T> L, const int *__
     return;
   }
   // Explicit rows: four threads per row, each taking every fourth row of the window, then a
-  // shuffle reduction.  A single thread per row walked (2R+1)^2 dependent iterations of a DRAM
-  // load and a gather; four keep four times as many loads in flight with the same sectors
-  // (neighbouring slots stay neighbours in memory).
+  // shuffle reduction.  Four threads keep four times as many loads in flight with the same
+  // sectors (neighbouring slots stay neighbours in memory), and each window row issues all of
+  // its loads at once (expl_window_sum).
   const int nexpl = *nexpl_dev;
   const int nb = gridDim.x - tiles;
   const int part = threadIdx.x & 3;
@@ -349,15 +385,7 @@ __global__ void __launch_bounds__(256) k_coarse_op(CoarseLev<T> L, const int *__
       const int I1 = j % L.n, I2 = j / L.n;
       const int R = L.R, Wd = 2 * R + 1;
       d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
-      if (OP != OP_JACOBI0) {
-        const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
-        const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
-        for (int dy = ylo + part; dy <= yhi; dy += 4) {
-          const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
-          const T *xrow = x + j + dy * L.n;
-          for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[size_t(dx) * L.cap], __ldg(xrow + dx), acc);
-        }
-      }
+      if (OP != OP_JACOBI0) acc = expl_window_sum_any<T>(L, slot, j, I1, I2, x, part, 4);
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
