@@ -67,6 +67,12 @@ void launch_coef(const double *G, int nf, int nq, const double *tau, const doubl
 
 constexpr int kTX = 32, kTY = 8;
 
+// Bytes of the staged argmin tile, rounded up to 16 so that the per-control constants of the
+// screen start aligned behind it.
+__host__ __device__ inline size_t argmin_tile_bytes(int SW, int SH, bool screen) {
+  return (size_t(SW) * SH * (screen ? sizeof(float) : sizeof(double)) + 15) / 16 * 16;
+}
+
 __device__ __forceinline__ double eval_global64(const FineTab &tab, int e, const double *__restrict__ X,
                                                 int j) {
   const int nt = tab.nt[e];
@@ -153,6 +159,12 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
   __shared__ float red_max[kTX * kTY / 32];
   double *xs64 = reinterpret_cast<double *>(smem_raw);
   float *xs32 = reinterpret_cast<float *>(smem_raw);
+  // screen: the per-control constants every lane reads in the same order, staged once per
+  // block beside the tile (one broadcast shared load each instead of global loads and
+  // address arithmetic per control): phi_k (zero-padded to four source functions) and
+  // {c_k, W and tap count of the control's interior entry, 0}
+  float4 *ctl_phi = reinterpret_cast<float4 *>(smem_raw + argmin_tile_bytes(a.SW, a.SH, true));
+  float4 *ctl_cw = ctl_phi + a.tab.K;
 
   const FineTab &tab = a.tab;
   const int n = tab.n, m = tab.m;
@@ -184,6 +196,16 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
   if (SCREEN) {
     for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if ((tid & 31) == 0) red_max[tid >> 5] = dmax;
+    const bool inner_exists = n - 1 >= 2 * tab.B;
+    for (int k = tid; k < tab.K; k += kTX * kTY) {
+      float p[4];
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) p[mm] = mm < a.nf ? __ldg(a.phi32 + k * a.nf + mm) : 0.f;
+      ctl_phi[k] = make_float4(p[0], p[1], p[2], p[3]);
+      const int ei = (k * tab.Q + tab.B) * tab.Q + tab.B;
+      ctl_cw[k] = make_float4(tab.c32[k], inner_exists ? tab.W32[ei] : 0.f,
+                              inner_exists ? float(tab.nt[ei]) : 0.f, 0.f);
+    }
   }
   __syncthreads();
   float Dmax = 0.f;
@@ -198,14 +220,15 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
     const int q1 = class_q(i1, n, tab.B), q2 = class_q(i2, n, tab.B);
     const int sidx = (threadIdx.y + a.halo) * a.SW + threadIdx.x + a.halo;
     const size_t N = size_t(n) * n;
-    const int nf = a.nf;
+    const int nf = a.nf;  // 1..4 (checked at create)
     double Fv[4];
     float Fv32[4];
     float Fabs = 0.f;
-    for (int mm = 0; mm < nf && mm < 4; ++mm) {
-      Fv[mm] = a.F[mm * N + j];
-      Fv32[mm] = a.F32[mm * N + j];
-      Fabs = fmaf(float(a.phimax[mm]), fabsf(Fv32[mm]), Fabs);
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) {
+      Fv[mm] = mm < nf ? a.F[mm * N + j] : 0.0;
+      Fv32[mm] = mm < nf ? a.F32[mm * N + j] : 0.f;
+      if (mm < nf) Fabs = fmaf(float(a.phimax[mm]), fabsf(Fv32[mm]), Fabs);
     }
     const double Xj = a.X[j];
     unsigned long long cand = 0ull;
@@ -227,13 +250,20 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
         float S;
         const float acc = itap ? eval_itap32<TMAX>(it, k, xs32, sidx, x0, S)
                                : eval_smem32<TMAX>(tab, e, xs32, sidx, x0, S);
-        float f = 0.f;
-        for (int mm = 0; mm < nf && mm < 4; ++mm) f = fmaf(__ldg(a.phi32 + k * nf + mm), Fv32[mm], f);
-        const float v = acc + fmaf(tab.c32[k], xj32, f);
+        const float4 ph = ctl_phi[k], cw = ctl_cw[k];
+        // f_k = sum_m phi_km F_m, in the order m = 0, 1, ... (padding terms add +0)
+        float f = fmaf(ph.x, Fv32[0], 0.f);
+        f = fmaf(ph.y, Fv32[1], f);
+        f = fmaf(ph.z, Fv32[2], f);
+        if (nf > 3) f = fmaf(ph.w, Fv32[3], f);
+        const float v = acc + fmaf(cw.x, xj32, f);
         if (!(v == v)) continue;  // NaN never enters the candidate list
-        const int nt = tab.nt[e];
-        const float E = 2.0f * (u * ((nt + 4.0f) * S * 1.001f + 2.0f * fabsf(v)) + Ef +
-                                eta * __ldg(tab.W32 + e)) + 4.0f * u * fabsf(v);
+        // tap count and W of the entry: the interior ones from shared memory; the count
+        // becomes a float by the exponent trick (exact below 2^23), not a conversion
+        const float ntf = itap ? cw.z : __int_as_float(0x4B000000 | int(tab.nt[e])) - 8388608.0f;
+        const float We = itap ? cw.y : __ldg(tab.W32 + e);
+        const float E = 2.0f * (u * ((ntf + 4.0f) * S * 1.001f + 2.0f * fabsf(v)) + Ef +
+                                eta * We) + 4.0f * u * fabsf(v);
         const float lb = v - E, ub = v + E;
         const float tw = tw_rel * fmaxf(1.0f, fabsf(v)) + 4.0f * u * fabsf(v);
         Umin = fminf(Umin, ub);
@@ -252,7 +282,9 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
       for (int k = 0; k < tab.K; ++k) {
         const int e = (k * tab.Q + q2) * tab.Q + q1;
         double f = 0.0;
-        for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
+        #pragma unroll
+        for (int mm = 0; mm < 4; ++mm)
+          if (mm < nf) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
         const double v = eval_smem64(tab, a.slin, e, xs64, sidx) + fma(tab.c64[k], Xj, f);
         if (!(v == v)) continue;
         const double margin = 2.0 * a.tie_rel * fmax(1.0, fabs(v < vmin ? v : vmin)) * (1.0 + 1e-9);
@@ -282,7 +314,9 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
         const int k = overflow ? c : int((cand >> (8 * c)) & 0xffull);
         const int e = (k * tab.Q + q2) * tab.Q + q1;
         double f = 0.0;
-        for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
+        #pragma unroll
+        for (int mm = 0; mm < 4; ++mm)
+          if (mm < nf) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
         const double v = eval_global64(tab, e, a.X, j) + fma(tab.c64[k], Xj, f);
         if (c < kMaxCand) vals[c] = v;
         vm = fmin(vm, v);
@@ -296,7 +330,9 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
         } else {
           const int e = (k * tab.Q + q2) * tab.Q + q1;
           double f = 0.0;
-          for (int mm = 0; mm < nf && mm < 4; ++mm) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
+          #pragma unroll
+        for (int mm = 0; mm < 4; ++mm)
+          if (mm < nf) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
           v = eval_global64(tab, e, a.X, j) + fma(tab.c64[k], Xj, f);
         }
         if (v <= thr) best = k;
@@ -334,7 +370,7 @@ cudaError_t argmin_launch(const ArgminArgs &a, const ArgminITaps &it, dim3 grd, 
 
 cudaError_t launch_argmin(const ArgminArgs &a, const ArgminITaps &it, cudaStream_t s) {
   dim3 blk(kTX, kTY), grd((a.tab.m + kTX - 1) / kTX, (a.tab.m + kTY - 1) / kTY);
-  const size_t bytes = size_t(a.SW) * a.SH * (a.screen ? sizeof(float) : sizeof(double));
+  const size_t bytes = argmin_tile_bytes(a.SW, a.SH, a.screen) + (a.screen ? 2 * size_t(a.tab.K) * sizeof(float4) : 0);
   if (!a.screen) return argmin_launch<0, 0>(a, it, grd, blk, bytes, s);
   switch (a.tab.tmax) {
     case 8: return argmin_launch<1, 8>(a, it, grd, blk, bytes, s);
