@@ -115,7 +115,13 @@ typedef struct {
   int argmin_screen;    /* 1: screen controls in FP32 with a rigorous rounding bound, then
                            decide in FP64 among the survivors (identical result); 0: all FP64 */
   double rebuild_frac;  /* rebuild the Galerkin hierarchy when more than rebuild_frac * N
-                           rows changed control since the last build (0: on any change) */
+                           rows changed control since the last build (0: on any change).
+                           The fine level always applies the current policy; a coarse
+                           hierarchy built for a policy that differs in a few rows is still
+                           a close preconditioner, and the solve tolerance is unchanged.
+                           Default 0.01: at 2049^2 fewer than 0.1 % of the rows change per
+                           step, and rebuilding every step cost about 1.3 ms of a 19 ms step
+                           for the same iteration count. */
   int use_graphs;       /* 1: each BiCGSTAB iteration is one CUDA-graph launch (captured once
                            per precision and step size); 0: plain stream launches */
   int coarse_tail_rows; /* levels with at most this many rows run, from the first such level
@@ -148,7 +154,7 @@ typedef struct {
 
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
- * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0, use_graphs 1, coarse_tail_rows -1,
+ * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 1, coarse_tail_rows -1,
  * extrapolate 1, precond 0, amg_k_levels 2. */
 void sl_opts_default(sl_opts *o);
 

@@ -1095,7 +1095,7 @@ void sl_opts_default(sl_opts *o) {
   o->pi_max = 100;
   o->tie_rel = 1e-12;
   o->argmin_screen = 0;
-  o->rebuild_frac = 0.0;
+  o->rebuild_frac = 0.01;
   o->use_graphs = 1;
   o->coarse_tail_rows = -1;
   o->extrapolate = 1;
