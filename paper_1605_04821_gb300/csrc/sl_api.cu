@@ -671,7 +671,7 @@ sl_status true_residual(sl_hjb *h, double dt, double tolk, double *r, ResNorms *
   if (h->transposed)  // backward solve A^T mu = lambda
     launch_fineT_op<double>(OP_RESID, csrT_view<double>(h), h->o.omega, h->mu, h->lam, r, s);
   else
-    launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r, s);
+    launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r, h->halo, h->SW, s);
   launch_init_scalars(h->S, tolk * tolk, s);
   launch_norms(h->transposed ? h->lam : h->Fvec, N, 0, h->S, h->partials, h->counter, s);
   launch_norms(r, N, 1, h->S, h->partials, h->counter, s);
@@ -700,8 +700,8 @@ sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
   const size_t N = NN(h, 0);
   // ||F||: the residual at X = (0 inside, psi on the boundary) is F itself
   if (!h->transposed)  // Xb vanishes inside: rows beyond the stencil reach need no taps
-    launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, s,
-                     std::max(1, h->cl[0].R));
+    launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, h->halo,
+                     h->SW, s, std::max(1, h->cl[0].R));
   CK(cudaGetLastError());
   double *X = h->transposed ? h->mu : h->X;
   KBuf &k = h->kb;

@@ -599,40 +599,102 @@ void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, f
 // ----------------------------------------------------------------------------- HJB residual
 // r_j = F_j - (A X)_j = U^{n-1}_j - X_j + dt (sum_t w_t (X_{j+o_t} - X_j) + c_k X_j + f_k(j)),
 // X carrying psi on the boundary (the boundary columns of Remark 2.2 are included here).
+//
+// FP64 is thin on this GPU, so the differences X_{j+o_t} - X_j are not formed per tap.  The
+// block stages x' = X - X_c on its 32 x 32 tile plus halo (X_c: X at the tile's centre node),
+// one subtraction per staged value, and forms sum_t w_t x'_t - W x'_j: 12 + 1 FMAs instead of
+// 12 subtractions and 12 FMAs.  In exact arithmetic this equals sum_t w_t (X_t - X_j), since
+// sum_t w_t = W for every table entry.  The rounding error stays of the order of
+// u W max_tile |X - X_c| (the variation of X over the tile), far below the u W |X| of the
+// plain form W X_j - sum_t w_t X_t.
+template <int TMAX>
 __global__ void __launch_bounds__(256) k_hjb_resid(FineTab tab, const uint8_t *__restrict__ policy,
                                                    const double *__restrict__ X,
                                                    const double *__restrict__ U,
                                                    const double *__restrict__ F,
                                                    const double *__restrict__ phi, int nf, double dt,
-                                                   double *__restrict__ r, int zero_inside) {
-  const int i1 = 1 + blockIdx.x * 32 + threadIdx.x;
-  const int i2 = 1 + blockIdx.y * 8 + threadIdx.y;
+                                                   double *__restrict__ r, int zero_inside, int halo,
+                                                   int SW) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *xs = reinterpret_cast<double *>(smem_raw);
+  constexpr int RPT = kFineRPT;
   const int n = tab.n, m = tab.m;
-  if (i1 > m || i2 > m) return;
-  const int j = i2 * n + i1;
-  const int k = policy[(i2 - 1) * m + (i1 - 1)];
-  const int e = fine_row_entry(tab, k, i1, i2);
-  const size_t N = size_t(n) * n;
-  double f = 0.0;
-  for (int mm = 0; mm < nf; ++mm) f = fma(__ldg(phi + k * nf + mm), F[mm * N + j], f);
-  const double Xj = X[j];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r1 = blockIdx.x * 32, r2 = blockIdx.y * (8 * RPT);
+  const int i1 = 1 + r1 + tx;
   // zero_inside = R > 0: X vanishes on the interior and no tap of a row farther than R from
-  // the boundary reaches it, so L X + c X = 0 there (the right-hand side F of the step)
+  // the boundary reaches it, so L X + c X = 0 there (the right-hand side F of the step); a
+  // block made only of such rows stages nothing
   const int R = zero_inside;
-  if (R > 0 && i1 > R && i1 < n - 1 - R && i2 > R && i2 < n - 1 - R) {
-    r[j] = U[j] + dt * f;
-    return;
+  const bool far_blk = R > 0 && 1 + r1 > R && r1 + 32 < n - 1 - R && 1 + r2 > R && r2 + 8 * RPT < n - 1 - R;
+  double xc = 0.0;
+  if (!far_blk) {
+    const int c1 = min(1 + r1 + 16, n - 2), c2 = min(1 + r2 + 4 * RPT, n - 2);
+    xc = X[size_t(c2) * n + c1];
+    const int o1 = 1 + r1 - halo, o2 = 1 + r2 - halo, SH = 8 * RPT + 2 * halo;
+    for (int rr = ty; rr < SH; rr += 8) {
+      const int g2 = o2 + rr;
+      const bool rowin = g2 >= 0 && g2 < n;
+      for (int cc = tx; cc < SW; cc += 32) {
+        const int g1 = o1 + cc;
+        xs[rr * SW + cc] = (rowin && g1 >= 0 && g1 < n) ? X[size_t(g2) * n + g1] - xc : 0.0;
+      }
+    }
   }
-  const double v = eval_global64(tab, e, X, j) + (f + tab.c64[k] * Xj);
-  r[j] = (U[j] - Xj) + dt * v;
+  __syncthreads();
+  if (i1 > m) return;
+  const bool inner = TMAX > 0 && tab.ipk64 != nullptr && !tab.general && n - 1 >= 2 * tab.B &&
+                     1 + r1 >= tab.B && r1 + 32 <= n - 1 - tab.B && 1 + r2 >= tab.B &&
+                     r2 + 8 * RPT <= n - 1 - tab.B;
+  const size_t N = size_t(n) * n;
+#pragma unroll
+  for (int rr = 0; rr < RPT; ++rr) {
+    const int i2 = 1 + r2 + ty + 8 * rr;
+    if (i2 > m) continue;
+    const int j = i2 * n + i1;
+    const int k = policy[(i2 - 1) * m + (i1 - 1)];
+    double f = 0.0;
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm)
+      if (mm < nf) f = fma(__ldg(phi + k * nf + mm), F[mm * N + j], f);
+    if (R > 0 && i1 > R && i1 < n - 1 - R && i2 > R && i2 < n - 1 - R) {
+      r[j] = U[j] + dt * f;
+      continue;
+    }
+    const int sidx = (ty + 8 * rr + halo) * SW + tx + halo;
+    const int e = fine_row_entry(tab, k, i1, i2);
+    double acc;
+    if (inner) {
+      acc = InnerTaps<double, TMAX>::sum(tab, k, xs, sidx);
+    } else {
+      acc = 0.0;
+      const int nt = tab.nt[e];
+      for (int t = 0; t < nt; ++t) {
+        int off;
+        double w;
+        PackedTap<double>::get(tab, e * tab.tmax + t, off, w);
+        acc = fma(w, xs[sidx + off], acc);
+      }
+    }
+    const double Xj = X[j];
+    const double v = fma(-tab.W64[e], xs[sidx], acc) + (f + tab.c64[k] * Xj);
+    r[j] = (U[j] - Xj) + dt * v;
+  }
 }
 
 void launch_hjb_resid(const FineTab &tab, const uint8_t *policy, const double *X,
                       const double *Uprev, const double *F, const double *phi, int nf, double dt,
-                      double *r, cudaStream_t s, int zero_inside) {
-  dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + 7) / 8);
+                      double *r, int halo, int SW, cudaStream_t s, int zero_inside) {
+  dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + 8 * kFineRPT - 1) / (8 * kFineRPT));
+  const size_t bytes = size_t(SW) * (8 * kFineRPT + 2 * halo) * sizeof(double);
   note_launch();
-  k_hjb_resid<<<grd, blk, 0, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside);
+  switch (tab.tmax) {
+    case 8: k_hjb_resid<8><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
+    case 12: k_hjb_resid<12><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
+    case 16: k_hjb_resid<16><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
+    case 20: k_hjb_resid<20><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
+    default: k_hjb_resid<0><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
+  }
 }
 
 // ----------------------------------------------------------------------------- transfers
@@ -686,7 +748,12 @@ static cudaError_t prepare_fine_op() {
 }
 
 cudaError_t prepare_fine_kernels() {
-  const void *fs[] = {reinterpret_cast<const void *>(k_argmin<0, 0>),
+  const void *fs[] = {reinterpret_cast<const void *>(k_hjb_resid<8>),
+                      reinterpret_cast<const void *>(k_hjb_resid<12>),
+                      reinterpret_cast<const void *>(k_hjb_resid<16>),
+                      reinterpret_cast<const void *>(k_hjb_resid<20>),
+                      reinterpret_cast<const void *>(k_hjb_resid<0>),
+                      reinterpret_cast<const void *>(k_argmin<0, 0>),
                       reinterpret_cast<const void *>(k_argmin<1, 8>),
                       reinterpret_cast<const void *>(k_argmin<1, 12>),
                       reinterpret_cast<const void *>(k_argmin<1, 16>),

@@ -75,7 +75,7 @@ void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, f
 // rows farther than R from the boundary then skip their taps (r = U_prev + dt f).
 void launch_hjb_resid(const FineTab &tab, const uint8_t *policy, const double *X,
                       const double *Uprev, const double *F, const double *phi, int nf, double dt,
-                      double *r, cudaStream_t s, int zero_inside = 0);
+                      double *r, int halo, int SW, cudaStream_t s, int zero_inside = 0);
 
 template <typename T>
 void launch_restrict(const T *rf, int nf, T *bc, int nc, cudaStream_t s);

@@ -219,3 +219,23 @@ def test_stencil_radius_figure_2_2():
         radii.append(math.hypot(z1[0] - c, z2[0] - c))
     assert max(radii) - min(radii) < 1e-9
     assert abs(radii[0] - gold["radius"]) < 0.005
+
+
+@pytest.mark.parametrize("make", [lambda: W.oracle_scale(), lambda: W.oracle_scale(truncation_heavy=True),
+                                  lambda: W.problem_A(33), lambda: W.problem_B(33)],
+                         ids=["plain", "truncated", "problemA", "problemB"])
+def test_tap_weights_sum_to_W(make):
+    """Every row's tap weights add up to its W: each of the scheme's points is split over the
+    corners of its cell with bilinear weights that sum to one (Section 2.1), and W is the sum
+    of the point weights.  The FP64 residual kernel relies on this identity: it forms
+    sum_t w_t (X_t - X_j) as sum_t w_t x'_t - W x'_j on a tile centred at one value."""
+    p = make()
+    n = p.n
+    i1, i2 = np.meshgrid(np.arange(1, n - 1), np.arange(1, n - 1))
+    i1, i2 = i1.ravel(), i2.ravel()
+    K = p.sigma.shape[0] if p.sigma is not None else 8
+    for k in range(min(K, 8)):
+        tp = lisl.control_taps(p, k, i1, i2)
+        s = np.bincount(tp.rows, weights=tp.w, minlength=len(i1))
+        assert np.all(tp.W > 0)
+        np.testing.assert_allclose(s, tp.W, rtol=4 * np.finfo(float).eps, atol=0)
