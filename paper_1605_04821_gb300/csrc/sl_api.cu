@@ -1240,7 +1240,10 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   if (!h->general && h->n - 1 >= 2 * ft.B && size_t(h->K) * ft.tmax <= size_t(kITapMax)) {
     for (int k = 0; k < h->K; ++k) {
       const int e = ft.entry(k, ft.B, ft.B);
-      for (int t = 0; t < ft.tmax; ++t) h->itaps->t[k * ft.tmax + t] = pk32[size_t(e) * ft.tmax + t];
+      for (int t = 0; t < ft.tmax; ++t) {
+        const int2 p = pk32[size_t(e) * ft.tmax + t];
+        h->itaps->t[k * ft.tmax + t] = make_int2(p.x * int(sizeof(float)), p.y);  // byte offset
+      }
     }
     h->itaps->n = h->K * ft.tmax;
   }

@@ -134,10 +134,11 @@ template <int TMAX>
 __device__ __forceinline__ float eval_itap32(const ArgminITaps &it, int k, const float *__restrict__ xs,
                                              int sidx, float x0, float &S) {
   float acc = 0.f, sa = 0.f;
+  const char *xb = reinterpret_cast<const char *>(xs + sidx);
 #pragma unroll
   for (int t = 0; t < TMAX; ++t) {
     const int2 p = it.t[k * TMAX + t];
-    const float dd = xs[sidx + p.x] - x0;
+    const float dd = *reinterpret_cast<const float *>(xb + p.x) - x0;
     const float w = __int_as_float(p.y);
     acc = fmaf(w, dd, acc);
     sa = fmaf(w, fabsf(dd), sa);

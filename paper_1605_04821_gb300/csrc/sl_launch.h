@@ -46,10 +46,12 @@ struct ArgminArgs {
   int screen;
 };
 
-// The packed taps {tile offset, fp32 weight bits} of the interior class of every control,
-// [k*tmax + t], passed as a kernel parameter: rows of the interior class (all but a band of
-// width B along the boundary) read them through the constant cache, every lane of a warp the
-// same entry, instead of through L1.  n = 0 when they do not fit (K * tmax > kITapMax).
+// The packed taps {byte offset in the FP32 staged tile, fp32 weight bits} of the interior
+// class of every control, [k*tmax + t], passed as a kernel parameter: rows of the interior
+// class (all but a band of width B along the boundary) read them through the constant cache,
+// every lane of a warp the same entry, instead of through L1.  The offset is in bytes so that
+// the shared load can take it as a uniform register beside the thread's own address.  n = 0
+// when they do not fit (K * tmax > kITapMax).
 constexpr int kITapMax = 3584;  // 28 KB of kernel parameters
 struct ArgminITaps {
   int n;
