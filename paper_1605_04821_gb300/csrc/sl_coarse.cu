@@ -312,18 +312,26 @@ __global__ void __launch_bounds__(256, 6) k_coarse_op(CoarseLev<T> L, const int 
     if (STAB && OP != OP_JACOBI0) {
       const PK *src = ClassTap<T>::table(L);
       const int nt_all = L.nk * L.ctmax;
-      for (int i = threadIdx.x; i < nt_all; i += blockDim.x) ts[i] = src[i];
+      for (int i0 = threadIdx.x; i0 < nt_all; i0 += 4 * blockDim.x) {  // four loads, then four stores
+        PK v[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = i0 + b * blockDim.x;
+          if (i < nt_all) v[b] = src[i];
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = i0 + b * blockDim.x;
+          if (i < nt_all) ts[i] = v[b];
+        }
+      }
     }
     if (OP != OP_JACOBI0) {
       const int o1 = 1 + bx * 32 - R, o2 = 1 + by * kCRowsY - R;
-      for (int r = ty; r < SH; r += 8) {
-        const int g2 = o2 + r;
-        const bool rowin = g2 >= 0 && g2 < L.n;
-        for (int c = tx; c < SW; c += 32) {
-          const int g1 = o1 + c;
-          xs[r * SW + c] = (rowin && g1 >= 0 && g1 < L.n) ? x[size_t(g2) * L.n + g1] : T(0);
-        }
-      }
+      stage_window<4, T>(xs, SW, SH, tx, ty, [&](int r, int c) {
+        const int g2 = o2 + r, g1 = o1 + c;
+        return (g2 >= 0 && g2 < L.n && g1 >= 0 && g1 < L.n) ? x[size_t(g2) * L.n + g1] : T(0);
+      });
       __syncthreads();
     }
     const int I1 = 1 + bx * 32 + tx;

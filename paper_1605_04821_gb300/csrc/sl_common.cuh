@@ -145,6 +145,36 @@ template <> struct PackedTap<double> {
   }
 };
 
+// Copies the SH x SW window whose element (r, c) is load(r, c) into xs (row pitch SW) with a
+// block of 32 x 8 threads (tx, ty).  Each pass covers 8 NR rows and the first 64 columns: a
+// thread issues its 2 NR loads into registers before any of its stores, so one round of memory
+// latency serves the whole pass.  (A loop that stores each value right after loading it makes
+// every load wait for the previous one, since the store waits for its data and instructions
+// issue in order; on a level with one block per SM nothing hides that.)  Columns from 64 on,
+// for wide halos, are copied one by one.
+template <int NR, typename T, typename Load>
+__device__ __forceinline__ void stage_window(T *xs, int SW, int SH, int tx, int ty, Load load) {
+  for (int r0 = 0; r0 < SH; r0 += 8 * NR) {
+    T v[NR][2];
+#pragma unroll
+    for (int i = 0; i < NR; ++i)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int r = r0 + ty + 8 * i, c = tx + 32 * q;
+        v[i][q] = (r < SH && c < SW) ? load(r, c) : T(0);
+      }
+#pragma unroll
+    for (int i = 0; i < NR; ++i)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int r = r0 + ty + 8 * i, c = tx + 32 * q;
+        if (r < SH && c < SW) xs[r * SW + c] = v[i][q];
+      }
+  }
+  for (int r = ty; r < SH; r += 8)
+    for (int c = tx + 64; c < SW; c += 32) xs[r * SW + c] = load(r, c);
+}
+
 template <typename T> struct ClassTap;
 template <> struct ClassTap<float> {
   using Packed = int2;

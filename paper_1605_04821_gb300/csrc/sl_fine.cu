@@ -179,20 +179,20 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
     xc = a.X[size_t(c2) * n + c1];
   }
   float dmax = 0.f;
-  for (int r = threadIdx.y; r < a.SH; r += kTY) {
-    const int g2 = o2 + r;
-    for (int cc = threadIdx.x; cc < a.SW; cc += kTX) {
-      const int g1 = o1 + cc, s = r * a.SW + cc;
+  if (SCREEN) {
+    // taps never leave the grid: the values staged outside it are unused (and not in D)
+    stage_window<4, float>(xs32, a.SW, a.SH, threadIdx.x, threadIdx.y, [&](int r, int cc) {
+      const int g2 = o2 + r, g1 = o1 + cc;
       const bool in = g1 >= 0 && g1 < n && g2 >= 0 && g2 < n;
-      const double xv = in ? a.X[size_t(g2) * n + g1] : 0.0;
-      if (SCREEN) {
-        const float xd = float(xv - xc);  // taps never leave the grid: outside values are unused
-        xs32[s] = xd;
-        if (in) dmax = fmaxf(dmax, fabsf(xd));
-      } else {
-        xs64[s] = xv;
-      }
-    }
+      const float xd = float((in ? a.X[size_t(g2) * n + g1] : 0.0) - xc);
+      if (in) dmax = fmaxf(dmax, fabsf(xd));
+      return xd;
+    });
+  } else {
+    stage_window<4, double>(xs64, a.SW, a.SH, threadIdx.x, threadIdx.y, [&](int r, int cc) {
+      const int g2 = o2 + r, g1 = o1 + cc;
+      return (g1 >= 0 && g1 < n && g2 >= 0 && g2 < n) ? a.X[size_t(g2) * n + g1] : 0.0;
+    });
   }
   if (SCREEN) {
     for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -405,29 +405,18 @@ __device__ __forceinline__ void fine_finish(T *y, const T *b, int j, T xj, T ax,
 }
 
 // Stages rows [o2, o2 + SH) x columns [o1, o1 + SW) of a full-grid vector into shared memory,
-// with zeros outside the grid; tiles whose halo lies inside the grid skip the bounds checks
-// and walk two row pointers, so that the copies of one row need no index arithmetic.
+// with zeros outside the grid; tiles whose halo lies inside the grid skip the bounds checks.
 template <typename T>
 __device__ __forceinline__ void stage_tile(T *xs, const T *__restrict__ x, int n, int o1, int o2, int SW,
                                            int SH, int tx, int ty) {
   if (o1 >= 0 && o2 >= 0 && o1 + SW <= n && o2 + SH <= n) {
-    const T *src = x + (size_t(o2) + ty) * n + o1 + tx;
-    T *dst = xs + ty * SW + tx;
-    const size_t gstep = size_t(8) * n;
-    const int sstep = 8 * SW, cols = SW - tx;
-    for (int r = ty; r < SH; r += 8, src += gstep, dst += sstep) {
-#pragma unroll 2
-      for (int c = 0; c < cols; c += 32) dst[c] = src[c];
-    }
+    const T *src = x + size_t(o2) * n + o1;
+    stage_window<4, T>(xs, SW, SH, tx, ty, [&](int r, int c) { return src[size_t(r) * n + c]; });
   } else {
-    for (int r = ty; r < SH; r += 8) {
-      const int g2 = o2 + r;
-      const bool rowin = g2 >= 0 && g2 < n;
-      for (int c = tx; c < SW; c += 32) {
-        const int g1 = o1 + c;
-        xs[r * SW + c] = (rowin && g1 >= 0 && g1 < n) ? x[size_t(g2) * n + g1] : T(0);
-      }
-    }
+    stage_window<4, T>(xs, SW, SH, tx, ty, [&](int r, int c) {
+      const int g2 = o2 + r, g1 = o1 + c;
+      return (g2 >= 0 && g2 < n && g1 >= 0 && g1 < n) ? x[size_t(g2) * n + g1] : T(0);
+    });
   }
 }
 
@@ -633,14 +622,10 @@ __global__ void __launch_bounds__(256) k_hjb_resid(FineTab tab, const uint8_t *_
     const int c1 = min(1 + r1 + 16, n - 2), c2 = min(1 + r2 + 4 * RPT, n - 2);
     xc = X[size_t(c2) * n + c1];
     const int o1 = 1 + r1 - halo, o2 = 1 + r2 - halo, SH = 8 * RPT + 2 * halo;
-    for (int rr = ty; rr < SH; rr += 8) {
-      const int g2 = o2 + rr;
-      const bool rowin = g2 >= 0 && g2 < n;
-      for (int cc = tx; cc < SW; cc += 32) {
-        const int g1 = o1 + cc;
-        xs[rr * SW + cc] = (rowin && g1 >= 0 && g1 < n) ? X[size_t(g2) * n + g1] - xc : 0.0;
-      }
-    }
+    stage_window<4, double>(xs, SW, SH, tx, ty, [&](int rr, int cc) {
+      const int g2 = o2 + rr, g1 = o1 + cc;
+      return (g2 >= 0 && g2 < n && g1 >= 0 && g1 < n) ? X[size_t(g2) * n + g1] - xc : 0.0;
+    });
   }
   __syncthreads();
   if (i1 > m) return;
