@@ -16,6 +16,11 @@
 namespace sl {
 
 constexpr int kVecThreads = 256;
+// The grid-stride loops below take kU consecutive strides per pass and issue all of their
+// loads before any arithmetic or store: a loop that computed and stored each element before
+// loading the next made every load wait for the one before it (instructions issue in order).
+// A thread still visits its elements in the same order, so every sum is unchanged.
+constexpr int kU = 4;
 
 static std::atomic<long long> g_launches{0};
 static thread_local long long t_launches = 0;  // this host thread's launches (graph captures)
@@ -169,9 +174,24 @@ __global__ void __launch_bounds__(kVecThreads) k_dot2(const T *__restrict__ a, c
                                                       double *partials, unsigned *counter) {
   double v[2] = {0.0, 0.0};
   T s0 = T(0), s1 = T(0);
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
-    s0 = fma(a[i], b[i], s0);
-    if (c) s1 = fma(c[i], d[i], s1);
+  const size_t st = size_t(gridDim.x) * blockDim.x;
+  for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+    T av[kU], bv[kU], cv[kU], dv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = i0 + u * st;
+      av[u] = i < N ? a[i] : T(0);
+      bv[u] = i < N ? b[i] : T(0);
+      cv[u] = (c && i < N) ? c[i] : T(0);
+      dv[u] = (c && i < N) ? d[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (i0 + u * st < N) {
+        s0 = fma(av[u], bv[u], s0);
+        if (c) s1 = fma(cv[u], dv[u], s1);
+      }
+    }
   }
   v[0] = double(s0);
   v[1] = double(s1);
@@ -194,9 +214,21 @@ __global__ void __launch_bounds__(kVecThreads) k_bicg_p(T *__restrict__ p, const
   const int first = first_host || S->first;
   const double beta_d = first ? 0.0 : (S->rho / S->rho_old) * (S->alpha / S->omega);
   const T beta = T(beta_d), om = T(S->omega);
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
-    if (first) p[i] = r[i];
-    else p[i] = r[i] + beta * (p[i] - om * v[i]);
+  const size_t st = size_t(gridDim.x) * blockDim.x;
+  for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+    T rv[kU], pv[kU], vv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = i0 + u * st;
+      rv[u] = i < N ? r[i] : T(0);
+      pv[u] = (!first && i < N) ? p[i] : T(0);
+      vv[u] = (!first && i < N) ? v[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = i0 + u * st;
+      if (i < N) p[i] = first ? rv[u] : rv[u] + beta * (pv[u] - om * vv[u]);
+    }
   }
 }
 
@@ -214,10 +246,24 @@ __global__ void __launch_bounds__(kVecThreads) k_bicg_s(T *__restrict__ sv, cons
                                                         double *partials, unsigned *counter) {
   const T alpha = T(S->alpha);
   T acc = T(0);
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
-    const T si = r[i] - alpha * v[i];
-    sv[i] = si;
-    acc = fma(si, si, acc);
+  const size_t st = size_t(gridDim.x) * blockDim.x;
+  for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+    T rv[kU], vv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = i0 + u * st;
+      rv[u] = i < N ? r[i] : T(0);
+      vv[u] = i < N ? v[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = i0 + u * st;
+      if (i < N) {
+        const T si = rv[u] - alpha * vv[u];
+        sv[i] = si;
+        acc = fma(si, si, acc);
+      }
+    }
   }
   double vv[1] = {double(acc)};
   finish<1>(vv, POST_SS, S, partials, counter);
@@ -241,12 +287,32 @@ __global__ void __launch_bounds__(kVecThreads) k_bicg_xr(TX *__restrict__ x, con
   const double alpha = S->alpha, omega = S->omega;
   const T om = T(omega);
   T a0 = T(0), a1 = T(0);
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
-    x[i] = x[i] + TX(alpha) * TX(phat[i]) + TX(omega) * TX(shat[i]);
-    const T ri = sv[i] - om * t[i];
-    r[i] = ri;
-    a0 = fma(rhat[i], ri, a0);
-    a1 = fma(ri, ri, a1);
+  const size_t st = size_t(gridDim.x) * blockDim.x;
+  for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+    TX xv[kU];
+    T pv[kU], shv[kU], svv[kU], tv[kU], rhv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = i0 + u * st;
+      const bool in = i < N;
+      xv[u] = in ? x[i] : TX(0);
+      pv[u] = in ? phat[i] : T(0);
+      shv[u] = in ? shat[i] : T(0);
+      svv[u] = in ? sv[i] : T(0);
+      tv[u] = in ? t[i] : T(0);
+      rhv[u] = in ? rhat[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = i0 + u * st;
+      if (i < N) {
+        x[i] = xv[u] + TX(alpha) * TX(pv[u]) + TX(omega) * TX(shv[u]);
+        const T ri = svv[u] - om * tv[u];
+        r[i] = ri;
+        a0 = fma(rhv[u], ri, a0);
+        a1 = fma(ri, ri, a1);
+      }
+    }
   }
   double vv[2] = {double(a0), double(a1)};
   finish<2>(vv, POST_RHO, S, partials, counter);
@@ -287,8 +353,15 @@ void launch_fill(T *x, size_t N, T v, cudaStream_t s) {
 
 template <typename Tin, typename Tout>
 __global__ void k_convert(const Tin *__restrict__ x, Tout *__restrict__ y, size_t N) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x)
-    y[i] = Tout(x[i]);
+  const size_t st = size_t(gridDim.x) * blockDim.x;
+  for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+    Tin v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[u] = i0 + u * st < N ? x[i0 + u * st] : Tin(0);
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + u * st < N) y[i0 + u * st] = Tout(v[u]);
+  }
 }
 template <typename Tin, typename Tout>
 void launch_convert(const Tin *x, Tout *y, size_t N, cudaStream_t s) {
@@ -312,8 +385,19 @@ void launch_extrapolate(double *X, const double *U, const double *V, int n, cuda
 }
 
 __global__ void k_add_f32(double *__restrict__ x, const float *__restrict__ e, size_t N) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x)
-    x[i] += double(e[i]);
+  const size_t st = size_t(gridDim.x) * blockDim.x;
+  for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+    double xv[kU];
+    float ev[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      xv[u] = i0 + u * st < N ? x[i0 + u * st] : 0.0;
+      ev[u] = i0 + u * st < N ? e[i0 + u * st] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + u * st < N) x[i0 + u * st] = xv[u] + double(ev[u]);
+  }
 }
 void launch_add_f32_to_f64(double *x, const float *e, size_t N, cudaStream_t s) {
   note_launch();
@@ -326,10 +410,19 @@ __global__ void __launch_bounds__(kVecThreads) k_norms(const double *__restrict_
                                                        BicgScalars *S, double *partials,
                                                        unsigned *counter) {
   double s2 = 0.0, mx = 0.0;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
-    s2 = fma(a[i], a[i], s2);
-    mx = fmax(mx, fabs(a[i]));
-    if (!(a[i] == a[i])) mx = INFINITY;
+  const size_t st = size_t(gridDim.x) * blockDim.x;
+  for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+    double av[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) av[u] = i0 + u * st < N ? a[i0 + u * st] : 0.0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (i0 + u * st < N) {
+        s2 = fma(av[u], av[u], s2);
+        mx = fmax(mx, fabs(av[u]));
+        if (!(av[u] == av[u])) mx = INFINITY;
+      }
+    }
   }
   s2 = warp_sum(s2);
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
