@@ -15,21 +15,38 @@ __global__ void k_coef(const double *__restrict__ G, int nf, int nq, const doubl
                        int n, double *__restrict__ F, float *__restrict__ F32,
                        double *__restrict__ Xext, double *__restrict__ Xb) {
   const size_t N = size_t(n) * n;
-  for (size_t j = blockIdx.x * size_t(blockDim.x) + threadIdx.x; j < N;
-       j += size_t(gridDim.x) * blockDim.x) {
+  const size_t st = size_t(gridDim.x) * blockDim.x;
+  for (size_t j0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; j0 < N; j0 += 4 * st) {
+    // four nodes per pass, the loads of each (m, q) issued for all four before the sums
     for (int m = 0; m < nf; ++m) {
-      double acc = 0.0;
-      for (int q = 0; q < nq; ++q) acc += tau[q] * G[(size_t(m) * nq + q) * N + j];
-      F[size_t(m) * N + j] = acc;
-      F32[size_t(m) * N + j] = float(acc);
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int q = 0; q < nq; ++q) {
+        double g[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) g[u] = j0 + u * st < N ? G[(size_t(m) * nq + q) * N + j0 + u * st] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += tau[q] * g[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const size_t j = j0 + u * st;
+        if (j < N) {
+          F[size_t(m) * N + j] = acc[u];
+          F32[size_t(m) * N + j] = float(acc[u]);
+        }
+      }
     }
-    const int i1 = int(j % n), i2 = int(j / n);
-    if (i1 == 0 || i2 == 0 || i1 == n - 1 || i2 == n - 1) {
-      double ps = 0.0;
-      for (int q = 0; q < npsi; ++q) ps += tpsi[q] * Psi[size_t(q) * N + j];
-      Xext[j] = ps;
-      Xb[j] = ps;
-    }
+  }
+  // the 4 (n - 1) boundary nodes, walked side by side: bottom, right, top, left
+  for (size_t b = blockIdx.x * size_t(blockDim.x) + threadIdx.x; b < size_t(4) * (n - 1); b += st) {
+    const int side = int(b / (n - 1)), p = int(b % (n - 1));
+    const int i1 = side == 0 ? p : side == 1 ? n - 1 : side == 2 ? n - 1 - p : 0;
+    const int i2 = side == 0 ? 0 : side == 1 ? p : side == 2 ? n - 1 : n - 1 - p;
+    const size_t j = size_t(i2) * n + i1;
+    double ps = 0.0;
+    for (int q = 0; q < npsi; ++q) ps += tpsi[q] * Psi[size_t(q) * N + j];
+    Xext[j] = ps;
+    Xb[j] = ps;
   }
 }
 

@@ -480,12 +480,25 @@ __global__ void __launch_bounds__(kVecThreads) k_maxabs_diff(const double *__res
                                                              double *partials) {
   double d = 0.0, x = 0.0;
   const size_t N = size_t(n) * n;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
-    const int i1 = int(i % n), i2 = int(i / n);
-    if (i1 == 0 || i2 == 0 || i1 == n - 1 || i2 == n - 1) continue;
-    d = fmax(d, fabs(a[i] - b[i]));
-    x = fmax(x, fabs(a[i]));
-    if (!(a[i] == a[i])) d = INFINITY;
+  const size_t st = size_t(gridDim.x) * blockDim.x;
+  for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+    double av[kU], bv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = i0 + u * st;
+      av[u] = i < N ? a[i] : 0.0;
+      bv[u] = i < N ? b[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = i0 + u * st;
+      if (i >= N) continue;
+      const int i1 = int(i % n), i2 = int(i / n);
+      if (i1 == 0 || i2 == 0 || i1 == n - 1 || i2 == n - 1) continue;
+      d = fmax(d, fabs(av[u] - bv[u]));
+      x = fmax(x, fabs(av[u]));
+      if (!(av[u] == av[u])) d = INFINITY;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
