@@ -230,7 +230,24 @@ __global__ void __launch_bounds__(kAdjThreads) k_fineT_op(CsrTView<T> A, T omega
   }
   T acc = d * x[j];
   const int lo = A.rowptr[J], hi = A.rowptr[J + 1];
-  for (int e = lo; e < hi; ++e) acc = fma(A.v[e], __ldg(x + A.col[e]), acc);
+  // eight entries per pass: their columns and values, then the eight x values, are loaded
+  // before the FMAs (a loop that chained column -> x -> FMA per entry paid two memory round
+  // trips for every entry); the entries are added in the same order
+  for (int e0 = lo; e0 < hi; e0 += 8) {
+    int cj[8];
+    T vv[8], xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool in = e0 + u < hi;
+      cj[u] = in ? A.col[e0 + u] : j;
+      vv[u] = in ? A.v[e0 + u] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) xv[u] = e0 + u < hi ? __ldg(x + cj[u]) : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (e0 + u < hi) acc = fma(vv[u], xv[u], acc);
+  }
   finishT<T, OP>(y, x, b, j, acc, d, omega);
 }
 
@@ -280,10 +297,14 @@ void launch_denseT_build(const CoarseLev<T> &L, const T *cdense, T *WT, cudaStre
 template void launch_denseT_build<double>(const CoarseLev<double> &, const double *, double *, cudaStream_t);
 template void launch_denseT_build<float>(const CoarseLev<float> &, const float *, float *, cudaStream_t);
 
-template <typename T, int OP>
-__global__ void __launch_bounds__(kAdjThreads) k_denseT_op(int n, int R, const T *__restrict__ WT, T omega,
+// With RR > 0 the reach is a compile-time constant and each window row is unrolled with a
+// predicate per entry, so its weight and value loads are in flight together (same order of
+// summation as the runtime loop, which serves other reaches).
+template <typename T, int OP, int RR>
+__global__ void __launch_bounds__(kAdjThreads) k_denseT_op(int n, int Rrt, const T *__restrict__ WT, T omega,
                                                             const T *__restrict__ x, const T *__restrict__ b,
                                                             T *__restrict__ y) {
+  const int R = RR > 0 ? RR : Rrt;
   const int m = n - 2, mm = m * m, Wd = 2 * R + 1;
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= mm) return;
@@ -300,9 +321,26 @@ __global__ void __launch_bounds__(kAdjThreads) k_denseT_op(int n, int R, const T
   for (int oy = ylo; oy <= yhi; ++oy) {
     const T *wrow = WT + size_t((oy + R) * Wd + R) * mm + J;
     const T *xrow = x + j + oy * n;
-    for (int ox = xlo; ox <= xhi; ++ox) acc = fma(wrow[size_t(ox) * mm], __ldg(xrow + ox), acc);
+    if (RR > 0) {
+#pragma unroll
+      for (int ox = -RR; ox <= RR; ++ox)
+        if (ox >= xlo && ox <= xhi) acc = fma(wrow[ptrdiff_t(ox) * mm], __ldg(xrow + ox), acc);
+    } else {
+      for (int ox = xlo; ox <= xhi; ++ox) acc = fma(wrow[ptrdiff_t(ox) * mm], __ldg(xrow + ox), acc);
+    }
   }
   finishT<T, OP>(y, x, b, j, acc, d, omega);
+}
+
+template <typename T, int RR>
+void denseT_dispatch(int op, int g, int n, int R, const T *WT, T omega, const T *x, const T *b, T *y,
+                     cudaStream_t s) {
+  switch (op) {
+    case OP_APPLY: k_denseT_op<T, OP_APPLY, RR><<<g, kAdjThreads, 0, s>>>(n, R, WT, omega, x, b, y); break;
+    case OP_RESID: k_denseT_op<T, OP_RESID, RR><<<g, kAdjThreads, 0, s>>>(n, R, WT, omega, x, b, y); break;
+    case OP_JACOBI: k_denseT_op<T, OP_JACOBI, RR><<<g, kAdjThreads, 0, s>>>(n, R, WT, omega, x, b, y); break;
+    default: k_denseT_op<T, OP_JACOBI0, RR><<<g, kAdjThreads, 0, s>>>(n, R, WT, omega, x, b, y); break;
+  }
 }
 
 template <typename T>
@@ -310,11 +348,16 @@ void launch_denseT_op(int op, int n, int R, const T *WT, T omega, const T *x, co
                       cudaStream_t s) {
   const int g = ((n - 2) * (n - 2) + kAdjThreads - 1) / kAdjThreads;
   note_launch();
-  switch (op) {
-    case OP_APPLY: k_denseT_op<T, OP_APPLY><<<g, kAdjThreads, 0, s>>>(n, R, WT, omega, x, b, y); break;
-    case OP_RESID: k_denseT_op<T, OP_RESID><<<g, kAdjThreads, 0, s>>>(n, R, WT, omega, x, b, y); break;
-    case OP_JACOBI: k_denseT_op<T, OP_JACOBI><<<g, kAdjThreads, 0, s>>>(n, R, WT, omega, x, b, y); break;
-    default: k_denseT_op<T, OP_JACOBI0><<<g, kAdjThreads, 0, s>>>(n, R, WT, omega, x, b, y); break;
+  switch (R) {
+    case 1: denseT_dispatch<T, 1>(op, g, n, R, WT, omega, x, b, y, s); break;
+    case 2: denseT_dispatch<T, 2>(op, g, n, R, WT, omega, x, b, y, s); break;
+    case 3: denseT_dispatch<T, 3>(op, g, n, R, WT, omega, x, b, y, s); break;
+    case 4: denseT_dispatch<T, 4>(op, g, n, R, WT, omega, x, b, y, s); break;
+    case 5: denseT_dispatch<T, 5>(op, g, n, R, WT, omega, x, b, y, s); break;
+    case 6: denseT_dispatch<T, 6>(op, g, n, R, WT, omega, x, b, y, s); break;
+    case 7: denseT_dispatch<T, 7>(op, g, n, R, WT, omega, x, b, y, s); break;
+    case 8: denseT_dispatch<T, 8>(op, g, n, R, WT, omega, x, b, y, s); break;
+    default: denseT_dispatch<T, 0>(op, g, n, R, WT, omega, x, b, y, s); break;
   }
 }
 template void launch_denseT_op<double>(int, int, int, const double *, double, const double *,
