@@ -420,8 +420,26 @@ __global__ void __launch_bounds__(kAT) k_amg_op(int n, const int32_t *__restrict
     y[i] = omega * b[i] / d[i];
     return;
   }
+  // eight entries per pass, their columns and values and then the x values loaded before the
+  // FMAs (chaining column -> x -> FMA per entry cost two memory round trips per entry); the
+  // entries are added in the same order
   T acc = T(0);
-  for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) acc = fma(v[p], x[col[p]], acc);
+  const int lo = rowptr[i], hi = rowptr[i + 1];
+  for (int p0 = lo; p0 < hi; p0 += 8) {
+    int cj[8];
+    T vv[8], xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool in = p0 + u < hi;
+      cj[u] = in ? col[p0 + u] : i;
+      vv[u] = in ? v[p0 + u] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) xv[u] = p0 + u < hi ? x[cj[u]] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (p0 + u < hi) acc = fma(vv[u], xv[u], acc);
+  }
   if (OP == OP_APPLY) y[i] = acc;
   else if (OP == OP_RESID) y[i] = b[i] - acc;
   else y[i] = x[i] + omega * (b[i] - acc) / d[i];
@@ -450,7 +468,17 @@ template <typename T>
 __global__ void k_amg_dense(int n, const T *__restrict__ Ainv, const T *__restrict__ b, T *__restrict__ x) {
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     T acc = T(0);
-    for (int c = 0; c < n; ++c) acc = fma(Ainv[size_t(r) * n + c], b[c], acc);
+    for (int c0 = 0; c0 < n; c0 += 8) {  // eight loads in flight, then the FMAs in order
+      T av[8], bv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        av[u] = c0 + u < n ? Ainv[size_t(r) * n + c0 + u] : T(0);
+        bv[u] = c0 + u < n ? b[c0 + u] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (c0 + u < n) acc = fma(av[u], bv[u], acc);
+    }
     x[r] = acc;
   }
 }
@@ -467,9 +495,25 @@ __global__ void __launch_bounds__(kAT) k_amg_dots(int n, const T *__restrict__ a
                                                    const T *__restrict__ c, const T *__restrict__ d,
                                                    double *__restrict__ partials) {
   double s0 = 0.0, s1 = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    s0 = fma(double(a[i]), double(b[i]), s0);
-    s1 = fma(double(c[i]), double(d[i]), s1);
+  const int st = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * st) {
+    T av[4], bv[4], cv[4], dv[4];  // four elements' loads, then the sums in the same order
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * st;
+      const bool in = i < n;
+      av[u] = in ? a[i] : T(0);
+      bv[u] = in ? b[i] : T(0);
+      cv[u] = in ? c[i] : T(0);
+      dv[u] = in ? d[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (i0 + u * st < n) {
+        s0 = fma(double(av[u]), double(bv[u]), s0);
+        s1 = fma(double(cv[u]), double(dv[u]), s1);
+      }
+    }
   }
   __shared__ double sh[2][kAT / 32];
   for (int o = 16; o > 0; o >>= 1) {
