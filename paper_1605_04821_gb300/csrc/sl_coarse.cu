@@ -297,6 +297,9 @@ __host__ __device__ inline size_t coarse_tile_bytes(int R) {
   return (size_t(32 + 2 * R) * (kCRowsY + 2 * R) * sizeof(T) + 15) / 16 * 16;
 }
 
+// Capped at six blocks of 256 threads per SM (40 registers): the explicit rows' unrolled
+// windows alone would take 62, which halved the residency of the class-row tiles that share
+// the launch; the cap costs a few bytes of spill and measured faster over a whole step.
 template <typename T, int OP, int STAB>
 __global__ void __launch_bounds__(256, 6) k_coarse_op(CoarseLev<T> L, const int *__restrict__ nexpl_dev,
                                                    int tiles_x, int tiles, T omega, const T *__restrict__ x,
