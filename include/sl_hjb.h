@@ -6,11 +6,11 @@
  *
  * on a square grid with Dirichlet data psi and initial data g (Section 1, Eqs. 1.1-1.3).
  *
- * Each implicit Euler step (theta = 1 in Eq. FullScheme) solves the nonlinear system
- * max_k (A^k X - F^k) = 0 (Eq. nonlinear_sys) by Howard policy iteration. Each iteration runs
+ * Each implicit Euler step (theta = 1 in Eq. 2.11) solves the nonlinear system
+ * max_k (A^k X - F^k) = 0 (Eq. 1.10) by Howard policy iteration. Each iteration runs
  * two phases:
  *   - a per-node argmin over the discrete control set of the truncated wide-stencil operator
- *     (Section 2.1, Proposition 2.2, Eq. Lhat);
+ *     (Section 2.1, Proposition 2.2, Eq. 2.9);
  *   - a BiCGSTAB solve at the fixed policy, right-preconditioned by a geometric multigrid
  *     V-cycle with Galerkin coarse operators (Section 3.3).
  *
@@ -61,7 +61,7 @@ typedef struct {
   double x_lo, x_hi, y_lo, y_hi;  /* square cells: x_hi - x_lo == y_hi - y_lo */
 } sl_grid;
 
-/* Discrete control set {k = 0..K-1} with x-independent coefficients (Eq. def_L).
+/* Discrete control set {k = 0..K-1} with x-independent coefficients (Eq. 1.4).
  * Column p of sigma^k (a 2 x P matrix) is (sigma[(k*2+0)*P + p], sigma[(k*2+1)*P + p]).
  * Scheme 2 (Section 1) uses the directions +-sqrt(h) sigma_p and h b. */
 typedef struct {
@@ -166,7 +166,7 @@ void sl_opts_default(sl_opts *o);
 sl_status sl_hjb_create(sl_hjb **h, const sl_grid *grid, const sl_controls *ctrl,
                         const sl_source *src, const sl_opts *opts, void *stream);
 
-/* One implicit step from t_n - dt to t_n (Eq. FullScheme, theta = 1) with Howard iteration.
+/* One implicit step from t_n - dt to t_n (Eq. 2.11, theta = 1) with Howard iteration.
  * u_dev (n*n, FP64): in U^{n-1} (boundary ignored), out U^n with psi(t_n) on the boundary.
  * The policy of the previous step is the starting policy; the first step starts from an
  * improvement on U^{n-1}.  policy_out_dev ((n-2)^2 uint8) receives the final policy if not
@@ -183,7 +183,7 @@ sl_status sl_hjb_solve(sl_hjb *h, double *u_dev, double t0, double T, int n_step
 
 /* ---- Discrete adjoint: gradients of J = sum_x w(x) U^N(x) through the implicit march ----
  *
- * Each step of Eq. FullScheme (theta = 1) at its converged policy alpha_n is the linear system
+ * Each step of Eq. 2.11 (theta = 1) at its converged policy alpha_n is the linear system
  * A_n U^n = U^{n-1} + dt f^{alpha_n}(t_n) + (boundary terms).  The paper solves these
  * systems forwards; the adjoint differentiates the same discrete march backwards at fixed
  * policies (valid wherever no policy switches under a small perturbation):
@@ -192,7 +192,7 @@ sl_status sl_hjb_solve(sl_hjb *h, double *u_dev, double t0, double T, int n_step
  *   dJ/dG[m][q](x)          = sum_n dt tau_q(t_n) phi[alpha_n(x), m] mu_n(x),
  *   dJ/dtheta                = sum_n dt mu_n^T (dL^{alpha_n}/dtheta U^n)
  * for a scalar parameter theta of the diffusion coefficients, with dL/dtheta the derivative
- * of the truncated Scheme-2 operator (Proposition 2.2, Eq. Lhat: endpoints, truncation
+ * of the truncated Scheme-2 operator (Proposition 2.2, Eq. 2.9: endpoints, truncation
  * factors mu, weights A_p, B_p and the bilinear taps) on the piece of its piecewise-smooth
  * dependence on sigma that the current sigma lies in.  Each backward system is solved like a
  * forward one (BiCGSTAB preconditioned by a V-cycle built from the transposed Galerkin levels
@@ -297,7 +297,7 @@ void sl_batch_destroy(sl_batch *b);
 
 /* ---- Stage entry points: single phases of a step, for parity checks and diagnostics ---- */
 
-/* Policy improvement (row-wise linear search of Eq. nonlinear_sys) on x_ext_dev (n*n FP64,
+/* Policy improvement (row-wise linear search of Eq. 1.10) on x_ext_dev (n*n FP64,
  * psi on the boundary) at time t: v_k(j) = (L^k X)_j + c^k X_j + f^k(t, x_j); the new policy
  * becomes the handle's policy and is copied to policy_out_dev if not NULL.  *changes
  * (host, may be NULL) receives the number of rows whose control changed. */
@@ -327,17 +327,22 @@ sl_status sl_hjb_apply(sl_hjb *h, int level, int precision, const void *x_dev, v
 sl_status sl_hjb_vcycle(sl_hjb *h, int precision, const void *b_dev, void *x_dev, void *stream);
 
 /* sl_hjb_vcycle without any device allocation.  The paper has no counterpart: this entry
- * point is for callers that must not allocate device memory while they run, such as code in
- * the middle of a global-mode CUDA stream capture (where cudaMalloc is refused) or a loop that
- * runs under a fixed device-memory budget.  Same arguments and same result as sl_hjb_vcycle,
- * but the V-cycle's work vectors live in one 2 MiB file-scope device array of the library
- * instead of the handle's buffers, so they must fit there: fine grids up to 257 x 257 nodes in
- * either precision (513 x 513 would need about 3.5 MB in FP32).  Larger grids get SL_EINVAL
- * with a message giving the bytes needed; nothing is allocated and nothing runs.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current): make that first call before any stream capture.  Every call
- * shares the one array and clears the part it uses first; calls that overlap on the GPU
- * (other streams, threads or handles) race with one another.  Stream-ordered; returns without
+ * point is for callers that cannot call cudaMalloc while they run.  Examples are a host
+ * application whose own pool allocator has reserved the device memory, so that a library's
+ * cudaMalloc would fail or split that pool, and a latency-bound loop in which the device-wide
+ * synchronisation that cudaMalloc and cudaFree may cause is not acceptable.  Same arguments
+ * and same result as sl_hjb_vcycle (to rounding: the coarse levels run one launch per level
+ * operation instead of the single-block tail), but the V-cycle's work vectors live in one
+ * 2 MiB file-scope device array of the library instead of the handle's buffers, so they must
+ * fit there: fine grids up to 257 x 257 nodes in either precision (513 x 513 would need
+ * about 3.5 MB in FP32).  Larger grids get SL_EINVAL with a message giving the bytes needed;
+ * nothing is allocated and nothing runs.  Every GPU that loads the library holds the array
+ * until the process exits.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); that first call should come before any
+ * stream capture.  Every call shares the one array, keeps nothing from the previous call
+ * (it clears the part it uses first), and calls that overlap on the GPU (other streams,
+ * threads or handles) race with one another.  Stream-ordered; returns without
  * synchronising. */
 sl_status sl_hjb_vcycle_noalloc(sl_hjb *h, int precision, const void *b_dev, void *x_dev,
                                 void *stream);

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 Each step n defines U^n through the residual of the converged policy alpha_n (the policy of the
 step's last linear solve):
     G_n(U^n, U^{n-1}; theta) = A^{alpha_n} U^n - F^{alpha_n} = U^n - U^{n-1} - dt (L U^n_ext + c U^n + f_n),
-(Eq. FullScheme with theta = 1, boundary terms inside L U_ext).  For J = sum_x w(x) U^N(x), away
+(Eq. 2.11 with theta = 1, boundary terms inside L U_ext).  For J = sum_x w(x) U^N(x), away
 from policy switches (where alpha_n does not move under small perturbations) the Lagrangian
 J - sum_n mu_n^T G_n gives the backward recursion
     A_N^T mu_N = w,   A_n^T mu_n = mu_{n+1}   (dG_{n+1}/dU^n = -I),

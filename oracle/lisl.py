@@ -9,29 +9,29 @@ What is computed, with the passage each piece follows
   y_p^{+-} = +-sqrt(dx) sigma_p for p <= P and y_{P+1} = dx b, M = P + 1 (drift present) or P.
 * Truncation (Section 2.1 and Proposition 2.2): mu^{+-}_p is the largest value in (0, 1]
   with x + mu y in the closed domain; the truncated endpoint is x + mu y.
-* Truncated weights (Proposition 2.2, Eqs. eqn_APp1 / eqn_Ap):
+* Truncated weights (Proposition 2.2, Eqs. 2.2 / 2.3):
   A_p = 2 / (mu+^2 + mu+ mu-), B_p = 2 / (mu-^2 + mu- mu+) for diffusion directions and
   A = B = 1 / mu for the drift direction.
-* Bilinear interpolation at the endpoints (Eqs. monotone_int, monotone_int_2).
-* Graph-Laplacian form of the truncated operator (Eq. Lhat):
+* Bilinear interpolation at the endpoints (Eqs. 1.7, 2.10).
+* Graph-Laplacian form of the truncated operator (Eq. 2.9):
   (L U)_j = sum_i l_{j,i} (U_i - U_j),
   l_{j,i} = sum_p [A_p w_i(x_j + y+_p) + B_p w_i(x_j + y-_p)] / (2 dx).
-* Fully implicit step (Eq. FullScheme with theta = 1): row j of A has diagonal
+* Fully implicit step (Eq. 2.11 with theta = 1): row j of A has diagonal
   1 + dt (sum_p (A_p + B_p)/(2 dx) - l_{j,j} - c_j) and off-diagonals -dt l_{j,i} on interior
   columns; boundary columns move to the right-hand side as +dt l_{j,i} psi_i (Remark 2.2).
   F_j = U^{n-1}_j + dt f_j.
-* Nonlinear system max_alpha (A^alpha X - F^alpha) = 0 (Eq. nonlinear_sys), solved by Howard
+* Nonlinear system max_alpha (A^alpha X - F^alpha) = 0 (Eq. 1.10), solved by Howard
   policy iteration (Section 1, policy iteration of Bokanowski et al.): solve at a fixed policy,
   then improve row by row by linear search over the discrete control set.
 
 Readings where the paper is silent (each is listed with its reason in the design notes):
 * Coordinates are handled in grid-index units: node j sits at integer index (i1, i2), and a
   displacement y becomes s = y / dx.  For a diffusion column, s = sigma_p / sqrt(dx), which is
-  the stencil length of Eq. def_mAlpha.  Truncation then asks that i + mu s stays in
+  the stencil length of Eq. 3.2.  Truncation then asks that i + mu s stays in
   [0, n-1]^2, which is the same condition as x + mu y in the closed rectangle.
 * A truncated endpoint is placed exactly on the boundary line of the binding component.
 * The boundary value at a truncated endpoint is interpolated from the boundary nodes
-  (Eq. Lhat); `lhat_apply_exact_endpoints` gives the exact-value variant of Remark 2.2.
+  (Eq. 2.9); `lhat_apply_exact_endpoints` gives the exact-value variant of Remark 2.2.
 * Policy improvement picks the lowest control index whose value is within
   1e-12 * max(1, |v_min|) of the minimum.
 * Howard iteration starts from the previous step's final policy (the first step starts from
@@ -87,7 +87,7 @@ def truncate(i1, i2, s1, s2, n):
 
 
 def bilinear(z1, z2, n):
-    """Bilinear interpolation nodes and weights at index-space points z (Eq. monotone_int).
+    """Bilinear interpolation nodes and weights at index-space points z (Eq. 1.7).
 
     Returns four (col, weight) pairs, col = flat full-grid index i2 * n + i1.
     """
@@ -167,7 +167,7 @@ def scheme2_taps(i1, i2, sig, drift, n, h, periodic=False) -> Taps:
         add(zm1, zm2, B / (2.0 * h))
         W += (A + B) / (2.0 * h)
     if drift is not None:
-        # y_{P+1} = dx b, i.e. b itself in index units; A = B = 1/mu (Eq. eqn_APp1).
+        # y_{P+1} = dx b, i.e. b itself in index units; A = B = 1/mu (Eq. 2.2).
         s1 = drift[:, 0]
         s2 = drift[:, 1]
         if periodic:
@@ -208,14 +208,14 @@ def control_taps(prob, k, i1, i2, periodic=False) -> Taps:
 
 
 def apply_lhat(taps: Taps, X_full: np.ndarray, rows_full: np.ndarray) -> np.ndarray:
-    """(L U)_j = sum_i l_{j,i} (U_i - U_j) for the rows of `taps` (Eq. Lhat)."""
+    """(L U)_j = sum_i l_{j,i} (U_i - U_j) for the rows of `taps` (Eq. 2.9)."""
     x = X_full.ravel()
     contrib = taps.w * (x[taps.cols] - x[rows_full[taps.rows]])
     return np.bincount(taps.rows, weights=contrib, minlength=len(taps.W))
 
 
 def lhat_apply_exact_endpoints(prob, k, i1, i2, q: Callable) -> np.ndarray:
-    """Truncated scheme (Eq. TruncScheme) with exact function values at the endpoints.
+    """Truncated scheme (Eq. 2.1) with exact function values at the endpoints.
 
     No interpolation: sum_p [A q(x + y+) - (A + B) q(x) + B q(x + y-)] / (2 dx), the form
     Remark 2.2 allows at boundary endpoints.  Used to check the weights' consistency.
@@ -255,7 +255,7 @@ def assemble(prob, policy: np.ndarray, U_prev: np.ndarray, t: float, dt: float,
              f_full: Optional[np.ndarray] = None, psi_full: Optional[np.ndarray] = None):
     """System A^alpha X = F^alpha of the implicit step at time t for a fixed policy.
 
-    Row j (Eq. FullScheme, theta = 1): diagonal 1 + dt (W_j - l_{j,j} - c_j), interior
+    Row j (Eq. 2.11, theta = 1): diagonal 1 + dt (W_j - l_{j,j} - c_j), interior
     off-diagonals -dt l_{j,i}; F_j = U^{n-1}_j + dt f_j + dt sum_{i on boundary} l_{j,i} psi_i.
     Returns (A as CSR over the interior unknowns, F).
     """
@@ -299,7 +299,7 @@ def control_values(prob, X_full: np.ndarray, t: float, f_full: Optional[np.ndarr
     """v_k(j) = (L^k X)_j + c^k X_j + f^k_j for every control k and interior node j.
 
     A^k X - F^k = X - U^{n-1} - dt v_k once the boundary terms sit inside L X (X carries psi
-    on the boundary), so the row-wise maximisation of Eq. nonlinear_sys is the row-wise
+    on the boundary), so the row-wise maximisation of Eq. 1.10 is the row-wise
     minimisation of v_k.
     """
     n = prob.n
@@ -357,16 +357,6 @@ def direct_solve(A, F):
     return spla.splu(A.tocsc()).solve(F)
 
 
-def iterative_solve(A, F, x0=None, rtol=1e-13):
-    """SciPy BiCGSTAB with an incomplete-LU preconditioner (CPU timing of large grids)."""
-    ilu = spla.spilu(A.tocsc(), drop_tol=1e-5, fill_factor=10)
-    M = spla.LinearOperator(A.shape, ilu.solve)
-    x, info = spla.bicgstab(A, F, x0=x0, rtol=rtol, atol=0.0, M=M, maxiter=2000)
-    if info != 0:
-        raise RuntimeError(f"oracle BiCGSTAB did not converge (info={info})")
-    return x
-
-
 @dataclasses.dataclass
 class StepResult:
     X: np.ndarray            # full grid, psi(t_n) on the boundary
@@ -378,7 +368,7 @@ class StepResult:
 
 
 def howard_step(prob, U_prev: np.ndarray, t: float, dt: float, policy0=None,
-                solver: str = "direct", pi_tol: float = PI_TOL, pi_max: int = PI_MAX,
+                pi_tol: float = PI_TOL, pi_max: int = PI_MAX,
                 keep_iterates: bool = False) -> StepResult:
     """One implicit step: Howard policy iteration on max_k (A^k X - F^k) = 0."""
     n = prob.n
@@ -397,10 +387,7 @@ def howard_step(prob, U_prev: np.ndarray, t: float, dt: float, policy0=None,
     iterates = []
     for it in range(1, pi_max + 1):
         A, F = assemble(prob, policy, U_prev, t, dt, f_full, psi)
-        if solver == "direct":
-            X = direct_solve(A, F)
-        else:
-            X = iterative_solve(A, F, x0=X_prev)
+        X = direct_solve(A, F)
         X_full.ravel()[flat] = X
         if keep_iterates:
             iterates.append(X.copy())
@@ -423,7 +410,7 @@ class SolveResult:
     converged: bool
 
 
-def solve(prob, n_steps: Optional[int] = None, T: Optional[float] = None, solver: str = "direct",
+def solve(prob, n_steps: Optional[int] = None, T: Optional[float] = None,
           U0: Optional[np.ndarray] = None, t0: float = 0.0) -> SolveResult:
     """Implicit Euler over n_steps uniform steps from U0 = g (Section 1, theta = 1)."""
     n_steps = prob.n_steps if n_steps is None else n_steps
@@ -435,7 +422,7 @@ def solve(prob, n_steps: Optional[int] = None, T: Optional[float] = None, solver
     ok = True
     for s in range(1, n_steps + 1):
         t = t0 + s * dt
-        res = howard_step(prob, U, t, dt, policy0=policy, solver=solver)
+        res = howard_step(prob, U, t, dt, policy0=policy)
         U, policy = res.X, res.policy
         policies.append(policy.copy())
         iters.append(res.pi_iters)

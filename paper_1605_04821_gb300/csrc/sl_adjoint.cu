@@ -2,7 +2,7 @@
 // the gradient accumulations.
 //
 // At a fixed policy the implicit step is the linear system A^alpha U^n = F^alpha (Eq.
-// FullScheme, theta = 1).  The adjoint recursion solves A_n^T mu_n = lambda_n, so every
+// 2.11, theta = 1).  The adjoint recursion solves A_n^T mu_n = lambda_n, so every
 // operator of the V-cycle is needed transposed:
 //   - fine level: an explicit transpose in CSR form (rows = interior columns of A), built once
 //     per step from the stencil tables and the policy.  Entries are scattered with atomics

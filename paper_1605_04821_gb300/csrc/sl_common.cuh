@@ -1,10 +1,10 @@
 // sl_common.cuh - data layout shared by the host orchestration and the sm_103a kernels.
 //
-// Fine level (level 0): matrix-free.  Row j = (i1, i2) of A^alpha (Eq. FullScheme, theta = 1)
+// Fine level (level 0): matrix-free.  Row j = (i1, i2) of A^alpha (Eq. 2.11, theta = 1)
 // is described by its control k = alpha_j and its boundary-distance class (q1, q2):
 //   (A x)_j = (1 + dt (W - c_k)) x_j - dt sum_t w_t x_{j + o_t}
 // where the taps (o_t, w_t) are the bilinear interpolation weights of the truncated Scheme-2
-// endpoints scaled by A_p/(2h), B_p/(2h) (Proposition 2.2, Eq. Lhat), and
+// endpoints scaled by A_p/(2h), B_p/(2h) (Proposition 2.2, Eq. 2.9), and
 // W = sum_p (A_p + B_p)/(2h).  Rows farther than B cells from the boundary in both
 // dimensions are never truncated and share one table entry per control; rows in the band
 // get one entry per (distance to the low side, distance to the high side) pair, so every

@@ -58,7 +58,7 @@ void launch_coef(const double *G, int nf, int nq, const double *tau, const doubl
 }
 
 // ----------------------------------------------------------------------------- argmin
-// Policy improvement (Eq. nonlinear_sys, linear search over the control set):
+// Policy improvement (Eq. 1.10, linear search over the control set):
 //   v_k(j) = sum_t w_t (X_{j+o_t} - X_j) + c_k X_j + sum_m phi_km F_m(j)
 // alpha_j = lowest k with v_k <= v_min + tie_rel max(1, |v_min|), decided in FP64.
 //
@@ -400,7 +400,7 @@ cudaError_t launch_argmin(const ArgminArgs &a, const ArgminITaps &it, cudaStream
 }
 
 // ----------------------------------------------------------------------------- fine operator
-// (A x)_j = (1 + dt (W - c_k)) x_j - dt sum_t w_t x_{j+o_t}  (Eq. FullScheme, theta = 1; x has
+// (A x)_j = (1 + dt (W - c_k)) x_j - dt sum_t w_t x_{j+o_t}  (Eq. 2.11, theta = 1; x has
 // zero boundary entries, so boundary taps drop out as they belong to the right-hand side).
 // Diagonal entry d_j = 1 + dt (W - c_k - w_self).
 //

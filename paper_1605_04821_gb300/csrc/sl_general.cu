@@ -3,8 +3,8 @@
 // per-control drift.
 //
 // Row j of L^k is the sum of a diffusion part that depends on the node only (Scheme 2 with
-// sigma(x_j), truncated at the boundary: Proposition 2.2, Eq. Lhat) and a drift part that
-// depends on the control and on the distance to the boundary (A = B = 1/mu, Eq. eqn_APp1).
+// sigma(x_j), truncated at the boundary: Proposition 2.2, Eq. 2.9) and a drift part that
+// depends on the control and on the distance to the boundary (A = B = 1/mu, Eq. 2.2).
 // The node parts come from a per-row table built once on the host, the drift parts from the
 // (control, boundary class) tables of the regular path.  After each policy improvement every
 // row's entry of the fine table is assembled for its control, so that the operator, residual,
@@ -82,7 +82,7 @@ void launch_assemble_general(const GeneralArgs &g, const FineTab &dtab, const ui
                                                                                  omega, SW, o);
 }
 
-// Policy improvement on a general fine level, in FP64 (Eq. nonlinear_sys, linear search):
+// Policy improvement on a general fine level, in FP64 (Eq. 1.10, linear search):
 // v_k(j) = (L_sigma X)_j + (L_b^k X)_j + c_k X_j + sum_m phi_km F_m(j), where the diffusion
 // part is the same for every control and is evaluated once per row.  alpha_j = lowest k with
 // v_k <= v_min + tie_rel max(1, |v_min|).

@@ -2,12 +2,12 @@
 //
 // For control k and a node at integer grid index i = (i1, i2), every diffusion column
 // sigma_p contributes the directions +-s_p with s_p = sigma_p / sqrt(h) in grid-index units
-// (the stencil length of Eq. def_mAlpha), and a drift b contributes s = b (y = h b).  The
+// (the stencil length of Eq. 3.2), and a drift b contributes s = b (y = h b).  The
 // truncation factor mu in (0, 1] is the largest value keeping i + mu s inside [0, n-1]^2
 // (Proposition 2.2); a component that hits the boundary is placed exactly on it.  Weights:
-// A_p = 2/(mu+^2 + mu+ mu-), B_p = 2/(mu-^2 + mu- mu+) (Eq. eqn_Ap), A = B = 1/mu for the
-// drift (Eq. eqn_APp1).  The endpoint value is the bilinear interpolant of the four nodes of
-// its cell (Eq. monotone_int); each tap weight is A_p w_i / (2h) (Eq. Lhat) and
+// A_p = 2/(mu+^2 + mu+ mu-), B_p = 2/(mu-^2 + mu- mu+) (Eq. 2.3), A = B = 1/mu for the
+// drift (Eq. 2.2).  The endpoint value is the bilinear interpolant of the four nodes of
+// its cell (Eq. 1.7); each tap weight is A_p w_i / (2h) (Eq. 2.9) and
 // W = sum_p (A_p + B_p) / (2h).
 #include "sl_geometry.h"
 

@@ -27,7 +27,7 @@ FineTabHost build_fine_tables(int n, double h, int K, int P, const double *sigma
 // Diffusion taps of every interior row for an x-dependent sigma shared by all controls:
 // field[((i2*n + i1)*2 + d)*P + p] is component d of column p at node (i1, i2).  Row
 // I = (i2-1)(n-2) + (i1-1) has nt[I] taps (dy, dx, w) at [I*stride + t] and the weight sum
-// W[I] = sum_p (A_p + B_p)/(2h) (Proposition 2.2, Eq. Lhat); R0 is the longest tap.
+// W[I] = sum_p (A_p + B_p)/(2h) (Proposition 2.2, Eq. 2.9); R0 is the longest tap.
 struct NodeTabHost {
   int stride = 0, R0 = 0;
   std::vector<int32_t> dx, dy;

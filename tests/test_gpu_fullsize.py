@@ -3,7 +3,7 @@ benchmark (V(1,1) cycles, FP32 argmin screen in mixed precision), node by node a
 oracle at sampled nodes.
 
 After each of the first two implicit steps the discrete HJB equation
-max_k (A^k X - F^k)_j = X_j - U^{n-1}_j - dt min_k v_k(j) = 0 (Eq. nonlinear_sys) must hold at
+max_k (A^k X - F^k)_j = X_j - U^{n-1}_j - dt min_k v_k(j) = 0 (Eq. 1.10) must hold at
 every sampled node j, with v_k(j) evaluated by the oracle from the GPU's U^{n-1} and X = U^n,
 and the GPU's final policy must be the oracle's argmin there (apart from near-ties).  The
 samples are random interior nodes, the corners, nodes of the truncation band and nodes on the

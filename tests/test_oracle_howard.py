@@ -5,7 +5,7 @@
   (A^alpha)^{-1} F^alpha (the system matrices are inverse-positive M-matrices with row-wise
   independent controls), and Howard's iteration must reach it.
 * Monotonicity of Howard's iterates: X^{m+1} <= X^m componentwise.
-* At convergence max_k (A^k X - F^k) = 0 row by row (Eq. nonlinear_sys).
+* At convergence max_k (A^k X - F^k) = 0 row by row (Eq. 1.10).
 """
 import itertools
 

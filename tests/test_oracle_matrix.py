@@ -1,8 +1,8 @@
 """Pins of the oracle's assembled system against invariants the paper proves.
 
-Positive type / M-matrix structure (Corollary 2.3 a, Eq. FullScheme), row sums (Section 3.4:
+Positive type / M-matrix structure (Corollary 2.3 a, Eq. 2.11), row sums (Section 3.4:
 1 + dt (M/dx - c) - dt M/dx >= 0, including the boundary columns), the lower bound
-sum_i l_{j,i} >= M/dx with equality exactly when nothing is truncated (after Eq. Lhat),
+sum_i l_{j,i} >= M/dx with equality exactly when nothing is truncated (after Eq. 2.9),
 column sums under the step-size condition of Proposition 3.1, and the discrete maximum
 principle that monotonicity implies.
 """
@@ -125,7 +125,7 @@ def test_bilinear_discrete_solution_with_boundary_data_and_discount(heavy):
     """A bilinear q is differentiated exactly by every row (interpolation reproduces it and the
     truncated weights are consistent), so with psi = q on the boundary, discount c, f = 0 and
     U^{n-1} = q - dt (L q + c q), the implicit step's solution is X = q exactly.  This fixes
-    the boundary right-hand side (Remark 2.2) and the -dt c diagonal term (Eq. FullScheme)."""
+    the boundary right-hand side (Remark 2.2) and the -dt c diagonal term (Eq. 2.11)."""
     p = W.oracle_scale(heavy)
     rng = np.random.default_rng(9)
     p.c = rng.uniform(0.0, 2.0, size=p.K)

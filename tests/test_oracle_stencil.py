@@ -2,7 +2,7 @@
 
 Each check fixes a fact the paper or plain mathematics determines independently of the
 oracle's code: exactness of interpolation on bilinear functions, the interpolation-error
-term on x1^2, the consistency equations of the truncated weights (Eqs. AB1, AB2), the
+term on x1^2, the consistency equations of the truncated weights (Eqs. 2.5, 2.6), the
 growth bounds of Corollary 2.3, and the printed stencil lengths / radius.
 """
 import json
@@ -50,7 +50,7 @@ SIGMAS = [
 @pytest.mark.parametrize("n", [17, 33])
 def test_bilinear_functions_are_differentiated_exactly(sig, n):
     """Bilinear interpolation reproduces span{1, x1, x2, x1 x2}, and the truncated weights are
-    exact on quadratics along each direction (Eqs. AB1, AB2), so L q = tr(a D^2 q) exactly
+    exact on quadratics along each direction (Eqs. 2.5, 2.6), so L q = tr(a D^2 q) exactly
     for these q at every row, truncated or not: 0 for 1, x1, x2 and (sigma sigma^T)_12 for x1 x2."""
     p = _const_problem(n, sig)
     S = np.asarray(sig)
@@ -89,7 +89,7 @@ def test_interpolation_error_term_on_x1_squared(sig):
 
 
 def test_truncated_weights_consistency_and_bounds():
-    """A s+ + B s- = 0 and A s+ s+^T + B s- s-^T = 2 s s^T (Eqs. AB1, AB2 in index units,
+    """A s+ + B s- = 0 and A s+ s+^T + B s- s-^T = 2 s s^T (Eqs. 2.5, 2.6 in index units,
     s = sigma / sqrt(dx)), A, B >= 1 (Corollary 2.3 a), A = B = 1 without truncation."""
     n = 33
     i1, i2 = lisl.interior_nodes(n)
@@ -120,7 +120,7 @@ def test_truncated_weights_consistency_and_bounds():
 
 @pytest.mark.parametrize("sig", SIGMAS)
 def test_exact_endpoint_scheme_is_exact_on_quadratics(sig):
-    """Remark 2.2 variant (exact values at the truncated endpoints): by Eqs. AB1/AB2 the
+    """Remark 2.2 variant (exact values at the truncated endpoints): by Eqs. 2.5/2.6 the
     truncated diffusion part is exact for every quadratic, including rows with two-sided
     overstepping."""
     n = 33
@@ -141,7 +141,7 @@ def test_exact_endpoint_scheme_is_exact_on_quadratics(sig):
 
 
 def test_truncated_drift_is_exact_on_linear_functions():
-    """Drift direction with A = B = 1/mu (Eq. eqn_APp1 / AB_drift): the truncated one-sided
+    """Drift direction with A = B = 1/mu (Eqs. 2.2 / 2.4): the truncated one-sided
     difference reproduces b . Dq exactly for linear q, also where x + dx b oversteps."""
     n = 17
     drift = [7.5, -3.2]            # index units: 7.5 cells, so rows near the boundary truncate
@@ -191,7 +191,7 @@ def test_weight_growth_rates():
 
 
 def test_stencil_length_table_3_1():
-    """Stencil length of Eq. def_mAlpha: for sigma = s I the nearest positive-weight tap of the
+    """Stencil length of Eq. 3.2: for sigma = s I the nearest positive-weight tap of the
     oracle's stencil along x1 sits m = floor(s / sqrt(dx)) cells from the node (Table 3.1)."""
     gold = json.load(open(os.path.join(GOLD, "table_3_1_stencil_length.json")))
     for key, sig in (("sigma_2", 2.0), ("sigma_sqrt5", math.sqrt(5.0))):

@@ -1,11 +1,12 @@
 """sl_hjb_vcycle_noalloc, the V-cycle entry point that allocates no device memory.
 
-It serves callers that must not allocate while they run (for example code inside a global-mode
-CUDA stream capture, where cudaMalloc is refused, or a loop with a fixed device-memory
-budget): its work vectors live in a 2 MiB static device array of the library.  The checks call
-it through the C ABI twice in a row and compare each result with sl_hjb_vcycle on the same
-input, within the V-cycle parity tolerance of the other GPU tests.  This file is collected last
-so that a failure here never hides the others.
+It serves callers that cannot call cudaMalloc while they run, for example a host application
+whose own pool allocator has reserved the device memory, or a latency-bound loop that cannot
+take the device-wide synchronisation of cudaMalloc/cudaFree: its work vectors live in a 2 MiB
+static device array of the library.  The checks call it through the C ABI twice in a row and
+compare each result with sl_hjb_vcycle on the same input, within the V-cycle parity tolerance
+of the other GPU tests.  This file is collected last so that a failure here never hides the
+others.
 """
 import numpy as np
 import pytest
