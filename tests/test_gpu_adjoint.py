@@ -1,10 +1,11 @@
 """GPU parity of the discrete adjoint (sl_hjb_solve_record + sl_hjb_adjoint).
 
 Small cases run against the oracle's dense-transpose adjoint element by element: dJ/dg and
-dJ/dG in relative max-norm, dJ/dtheta per parameter.  The tolerance of dJ/dtheta covers the
-oracle's own central difference of the operator in theta (about 5e-11 relative at its step).
-The full-size case (1025^2, 33 controls, 64 steps, Gaussian-bump weights) is checked against
-central differences of the library's own forward march, which hold at any size.
+dJ/dG in relative max-norm, dJ/dtheta per parameter (the oracle writes dL/dtheta U in closed
+form, so both sides are exact up to the solves' tolerance).  The full-size case (1025^2,
+33 controls, 64 steps, checkpoints every 8 steps, Gaussian-bump weights) is checked against
+central differences of the library's own forward march at 1e-6 relative, with every step's
+policy and Howard count unchanged under the perturbations (away from policy switches).
 """
 import copy
 
@@ -17,7 +18,7 @@ from tests._gpu_util import TOL_FP64, TOL_MIXED, rel_maxnorm, to_dev
 pytestmark = pytest.mark.gpu
 
 ADJ_TOL = {0: 1e-9, 1: 1e-8}     # dJ/dg, dJ/dG, relative max-norm
-THETA_TOL = {0: 1e-8, 1: 1e-8}   # dJ/dtheta, relative
+THETA_TOL = {0: 1e-10, 1: 1e-10}  # dJ/dtheta, relative
 
 
 def _lib():
@@ -49,7 +50,7 @@ def _case(name):
 
 def _oracle(p, w, dirs):
     from oracle import adjoint as adj
-    return adj.adjoint(p, w, list(dirs), eps_rel=1e-5)
+    return adj.adjoint(p, w, list(dirs))
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -122,37 +123,56 @@ def test_autograd_function_returns_the_adjoint_gradients():
 
 
 def test_full_size_gradient_matches_central_differences_of_the_march():
-    """1025^2, 33 controls, 64 steps: <dJ/dg, w> and dJ/dtheta against central differences
-    (step 1e-5) of the library's own FP64 forward march."""
+    """1025^2, 33 controls, 64 steps, checkpoints every 8 steps: <dJ/dg, w> and dJ/dtheta
+    against central differences of the library's own FP64 forward march at 1e-6 relative.
+    Every perturbed march must take the base march's policy and Howard count at every step,
+    so the differences stay on the piece of the piecewise-smooth map that the gradient is of."""
     import torch
     S = _lib()
     p, w = W.adjoint_1025(seed=0)
     dirs = W.sigma_directions(p)
-    sol = S.solver_from_problem(p, precision=0)
+    tol = 1e-13   # forward and backward solves, so that the differences resolve 1e-6
+    sol = S.solver_from_problem(p, precision=0, krylov_tol=tol)
     u = to_dev(p.g)
     sol.solve_record(u, 0.0, p.T, p.n_steps, 8)
     wd = to_dev(w)
-    J0 = float((wd * u).sum())
     dg = torch.zeros_like(u)
     dth, _ = sol.adjoint(wd, dg, None, dirs)
     sol.close()
+    m = p.n - 2
+    dt = p.T / p.n_steps
 
-    def J_of(sigma=None, g=None):
+    def march(sigma=None, g=None):
         q = copy.copy(p)
         if sigma is not None:
             q.sigma = sigma
-        s = S.solver_from_problem(q, precision=0)
+        s = S.solver_from_problem(q, precision=0, krylov_tol=tol)
         uu = to_dev(p.g if g is None else g)
-        s.solve(uu, 0.0, p.T, p.n_steps)
+        pols = torch.empty((p.n_steps, m * m), dtype=torch.uint8, device=uu.device)
+        its = []
+        for i in range(1, p.n_steps + 1):
+            st = s.step(uu, i * dt, dt, policy_out=pols[i - 1])
+            its.append(st["pi_iters"])
         s.close()
-        return float((wd * uu).sum())
+        return float((wd * uu).sum()), pols, its
+
+    J0, pol0, it0 = march()
+
+    def same_piece(pols, its):
+        return bool(torch.equal(pols, pol0)) and its == it0
 
     d = w  # a coherent direction: the bump itself
-    eps_g = 1e-5
-    fd_g = (J_of(g=p.g + eps_g * d) - J_of(g=p.g - eps_g * d)) / (2 * eps_g)
+    eps_g = 1e-3
+    Jp, pp, ip = march(g=p.g + eps_g * d)
+    Jm, pm, im = march(g=p.g - eps_g * d)
+    assert same_piece(pp, ip) and same_piece(pm, im), "a policy switched under the g perturbation"
+    fd_g = (Jp - Jm) / (2 * eps_g)
     ad_g = float((dg.cpu().numpy() * d).sum())
-    assert abs(fd_g - ad_g) <= 1e-5 * abs(fd_g), (fd_g, ad_g)
-    eps = 1e-5
+    assert abs(fd_g - ad_g) <= 1e-6 * abs(fd_g), (fd_g, ad_g)
+    eps = 2e-5
     for i, ds in enumerate(dirs):
-        fd = (J_of(sigma=p.sigma + eps * ds) - J_of(sigma=p.sigma - eps * ds)) / (2 * eps)
-        assert abs(fd - dth[i]) <= 1e-4 * abs(fd), (i, fd, dth[i], J0)
+        Jp, pp, ip = march(sigma=p.sigma + eps * ds)
+        Jm, pm, im = march(sigma=p.sigma - eps * ds)
+        assert same_piece(pp, ip) and same_piece(pm, im), f"a policy switched under theta_{i} +- eps"
+        fd = (Jp - Jm) / (2 * eps)
+        assert abs(fd - dth[i]) <= 1e-6 * abs(fd), (i, fd, dth[i], J0)
