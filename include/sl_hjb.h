@@ -80,9 +80,29 @@ typedef struct {
 /* Time factors tau(t) of the separable source and boundary data. */
 enum { SL_TAU_ONE = 0, SL_TAU_EXP = 1 /* exp(rate t) */, SL_TAU_LINEAR = 2 /* t */ };
 
-/* Source f^k(t, x) = sum_m phi[k*nf + m] sum_q tau_q(t) G[((m*nq + q)*n + i2)*n + i1]
- * and boundary data psi(t, x) = sum_q tau'_q(t) Psi[(q*n + i2)*n + i1] (boundary entries).
- * G and Psi stay in the caller's device memory and must outlive the handle. */
+/* Coefficient callback.  Eqs. 1.1-1.3 let the source f^k(t, x) and the Dirichlet data psi(t, x)
+ * be general functions of time and space; a callback fills their values on the device at each
+ * implicit step's time t_n (theta = 1 evaluates them at t_n, Section 1).  The library calls it
+ * on the host thread that runs the step, before any kernel of that step reads the values:
+ *   - source callback: once for each m = 0 .. nf-1, to write F_m(t_n, .) into dev_out; the
+ *     source of control k is then f^k(t_n, .) = sum_m phi[k*nf + m] F_m(t_n, .);
+ *   - boundary callback: once (m = 0), to write psi(t_n, .) into dev_out on the boundary nodes
+ *     (interior entries are ignored).
+ * dev_out is library-owned device memory of n*n FP64 values in the full-grid layout; it is
+ * valid for the duration of the call.  The callback must enqueue its writes on `stream` (a
+ * cudaStream_t, the handle's stream for this call) or finish them before it returns; the
+ * library reads dev_out in stream order afterwards.  `user` is sl_source.cb_user.  A callback
+ * must not call back into the library with the same handle. */
+typedef void (*sl_field_cb)(double t, const sl_grid *grid, int m, double *dev_out, void *user,
+                            void *stream);
+
+/* Source and boundary data.  Either the separable form
+ *   f^k(t, x) = sum_m phi[k*nf + m] sum_q tau_q(t) G[((m*nq + q)*n + i2)*n + i1],
+ *   psi(t, x) = sum_q tau'_q(t) Psi[(q*n + i2)*n + i1] (boundary entries),
+ * whose tables G and Psi stay in the caller's device memory and must outlive the handle (the
+ * fast path: the per-step tables are one kernel), or callbacks (sl_field_cb) for data of any
+ * other form: with f_cb set, G_dev, nq, tau_kind and tau_rate are ignored; with psi_cb set,
+ * npsi, Psi_dev, psi_kind and psi_rate are ignored.  phi and nf are used in both cases. */
 typedef struct {
   int nf, nq;
   const double *phi;       /* host, K*nf */
@@ -93,6 +113,9 @@ typedef struct {
   const double *Psi_dev;   /* device, npsi*n*n, or NULL */
   const int *psi_kind;     /* host, npsi */
   const double *psi_rate;  /* host, npsi */
+  sl_field_cb f_cb;        /* NULL: separable source from G_dev and tau */
+  sl_field_cb psi_cb;      /* NULL: separable boundary data from Psi_dev (or psi = 0) */
+  void *cb_user;           /* passed to both callbacks */
 } sl_source;
 
 typedef struct {
@@ -211,7 +234,9 @@ sl_status sl_hjb_solve_record(sl_hjb *h, double *u_dev, double t0, double T, int
 /* Backward pass over the last sl_hjb_solve_record.
  *   w_dev        device, n*n: weights of J (boundary entries do not enter).
  *   dJ_dg_dev    device, n*n out: dJ/dg (zero on the boundary, where g is not used).
- *   dJ_dG_dev    device, nf*nq*n*n out (layout of sl_source.G_dev), or NULL to skip.
+ *   dJ_dG_dev    device, nf*nq*n*n out (layout of sl_source.G_dev), or NULL to skip.  With a
+ *                source callback, nq counts as 1 with tau = 1: dJ_dG[m] is then the gradient
+ *                with respect to a time-independent additive change of the table F_m.
  *   nparam       0 .. 8 scalar parameters theta_p of sigma.
  *   dsigma       host, nparam*K*2*P: d sigma / d theta_p, laid out like sl_controls.sigma.
  *   dJ_dtheta    host, nparam out.

@@ -42,11 +42,17 @@ class SlControls(ctypes.Structure):
                 ("b", ctypes.c_void_p), ("c", ctypes.c_void_p), ("sigma_field", ctypes.c_void_p)]
 
 
+# sl_field_cb: void (*)(double t, const sl_grid *grid, int m, double *dev_out, void *user, void *stream)
+FIELD_CB = ctypes.CFUNCTYPE(None, ctypes.c_double, ctypes.POINTER(SlGrid), ctypes.c_int, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_void_p)
+
+
 class SlSource(ctypes.Structure):
     _fields_ = [("nf", ctypes.c_int), ("nq", ctypes.c_int), ("phi", ctypes.c_void_p),
                 ("G_dev", ctypes.c_void_p), ("tau_kind", ctypes.c_void_p),
                 ("tau_rate", ctypes.c_void_p), ("npsi", ctypes.c_int), ("Psi_dev", ctypes.c_void_p),
-                ("psi_kind", ctypes.c_void_p), ("psi_rate", ctypes.c_void_p)]
+                ("psi_kind", ctypes.c_void_p), ("psi_rate", ctypes.c_void_p),
+                ("f_cb", FIELD_CB), ("psi_cb", FIELD_CB), ("cb_user", ctypes.c_void_p)]
 
 
 class SlOpts(ctypes.Structure):
@@ -164,11 +170,50 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+class _DeviceView:
+    """A device array of n x n FP64 values, as the CUDA array interface describes it (lets
+    torch alias library-owned memory without a copy)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n, n), "typestr": "<f8", "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
+class FieldCallback:
+    """Wraps fn(t, m, out) as an sl_field_cb.  `out` is an (n, n) float64 CUDA tensor aliasing
+    the library's buffer; fn runs with the library's stream as torch's current stream, so its
+    torch operations are ordered before the kernels that read the values.  An exception inside
+    fn cannot cross the C ABI: it is kept and re-raised by the Solver method that triggered it."""
+
+    def __init__(self, fn, n: int):
+        self.fn = fn
+        self.n = n
+        self.error = None
+
+        def _cb(t, grid, m, dev_out, user, stream):
+            import torch
+            try:
+                out = torch.as_tensor(_DeviceView(dev_out, self.n))
+                st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+                with torch.cuda.stream(st):
+                    self.fn(t, m, out)
+            except BaseException as e:  # noqa: BLE001 - kept and re-raised on the Python side
+                if self.error is None:
+                    self.error = e
+
+        self.c = FIELD_CB(_cb)
+
+    def raise_pending(self):
+        if self.error is not None:
+            e, self.error = self.error, None
+            raise RuntimeError("a coefficient callback raised") from e
+
+
 def _describe(keep: list, n, lo, hi, sigma, phi, G, tau_kind, tau_rate, Psi=None, psi_kind=None,
-              psi_rate=None, b=None, c=None, sigma_field=None):
+              psi_rate=None, b=None, c=None, sigma_field=None, f_cb=None, psi_cb=None):
     """sl_grid / sl_controls / sl_source for one problem.  Host arrays and the device tensors
     are appended to `keep` (which must outlive the structs); the last two entries are G and
-    Psi (or None)."""
+    Psi (or None).  f_cb / psi_cb: FieldCallback objects or None (G / Psi are then unused)."""
     import torch
 
     def host(a, dtype):
@@ -189,19 +234,28 @@ def _describe(keep: list, n, lo, hi, sigma, phi, G, tau_kind, tau_rate, Psi=None
     ctrl = SlControls(K, P, sig_ptr,
                       host(b, np.float64) if b is not None else None,
                       host(c, np.float64) if c is not None else None, fld_ptr)
-    G = G.contiguous()
-    assert G.is_cuda and G.dtype == torch.float64 and G.shape[2:] == (n, n)
-    nf, nq = G.shape[0], G.shape[1]
+    if f_cb is None:
+        G = G.contiguous()
+        assert G.is_cuda and G.dtype == torch.float64 and G.shape[2:] == (n, n)
+        nf, nq = G.shape[0], G.shape[1]
+        g_ptr = _ptr(G)
+    else:
+        nf, nq, g_ptr = np.atleast_2d(phi).shape[1], 0, None
+        tau_kind, tau_rate = np.zeros(1, dtype=np.int32), np.zeros(1)
     npsi = 0
     psi_ptr = None
-    if Psi is not None:
+    if Psi is not None and psi_cb is None:
         Psi = Psi.contiguous()
         npsi = Psi.shape[0]
         psi_ptr = _ptr(Psi)
-    src = SlSource(nf, nq, host(phi, np.float64), _ptr(G), host(tau_kind, np.int32),
+    src = SlSource(nf, nq, host(phi, np.float64), g_ptr, host(tau_kind, np.int32),
                    host(tau_rate, np.float64), npsi, psi_ptr,
                    host(psi_kind, np.int32) if npsi else None,
-                   host(psi_rate, np.float64) if npsi else None)
+                   host(psi_rate, np.float64) if npsi else None,
+                   f_cb.c if f_cb is not None else FIELD_CB(),
+                   psi_cb.c if psi_cb is not None else FIELD_CB(), None)
+    keep.append(f_cb)
+    keep.append(psi_cb)
     keep.append(G)
     keep.append(Psi)
     return grid, ctrl, src
@@ -212,16 +266,21 @@ class Solver:
 
     G: (nf, nq, n, n) float64 source tables; Psi: (npsi, n, n) float64 or None.  The handle
     keeps references to G and Psi, which must stay alive and unchanged.
+    f_cb / psi_cb: optional coefficient callbacks fn(t, m, out) (sl_field_cb) that write
+    F_m(t, .) or psi(t, .) into the (n, n) float64 CUDA tensor `out` at each step's time; they
+    replace G (then pass G=None) and Psi.
     """
 
     def __init__(self, n: int, lo: float, hi: float, sigma: np.ndarray, phi: np.ndarray, G,
                  tau_kind, tau_rate, Psi=None, psi_kind=None, psi_rate=None, b=None, c=None,
-                 sigma_field=None, opts: Optional[SlOpts] = None, stream=None, **opt_kw):
+                 sigma_field=None, opts: Optional[SlOpts] = None, stream=None, f_cb=None,
+                 psi_cb=None, **opt_kw):
         lib = load()
         self._lib = lib
         self._keep = []
+        self._cbs = [FieldCallback(fn, n) if fn is not None else None for fn in (f_cb, psi_cb)]
         grid, ctrl, src = _describe(self._keep, n, lo, hi, sigma, phi, G, tau_kind, tau_rate, Psi,
-                                    psi_kind, psi_rate, b, c, sigma_field)
+                                    psi_kind, psi_rate, b, c, sigma_field, *self._cbs)
         self.n, self.K, self.P = n, ctrl.K, ctrl.P
         self.general = ctrl.sigma_field is not None
         self._G = self._keep[-2]
@@ -251,6 +310,9 @@ class Solver:
             pass
 
     def _check(self, st):
+        for cb in self._cbs:
+            if cb is not None:
+                cb.raise_pending()
         if st != SL_OK:
             raise SLError(st, self._lib.sl_hjb_last_error(self.h).decode())
 

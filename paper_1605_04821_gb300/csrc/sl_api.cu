@@ -66,6 +66,12 @@ struct sl_hjb {
   std::vector<double> phi, phimax, tau_rate, psi_rate, cvec, sigma;
   std::vector<int> tau_kind, psi_kind;
   const double *G = nullptr, *Psi = nullptr;
+  // coefficient callbacks: they fill Gcb (nf tables, read with nq = 1 and tau = 1) and Psicb
+  // (read as one boundary table with tau = 1) at each step's time
+  sl_field_cb f_cb = nullptr, psi_cb = nullptr;
+  void *cb_user = nullptr;
+  sl_grid grid{};
+  double *Gcb = nullptr, *Psicb = nullptr;
   FineTabHost ft;
   FineTab tab{};
   // device tables
@@ -211,6 +217,11 @@ size_t NN(const sl_hjb *h, int l) { return size_t(h->cl[l].n) * h->cl[l].n; }
 
 // ---------------------------------------------------------------------- per-step tables
 sl_status coef(sl_hjb *h, double t, double *Xext, cudaStream_t s) {
+  const size_t NNc = size_t(h->n) * h->n;
+  if (h->f_cb)
+    for (int mm = 0; mm < h->nf; ++mm) h->f_cb(t, &h->grid, mm, h->Gcb + mm * NNc, h->cb_user, s);
+  if (h->psi_cb) h->psi_cb(t, &h->grid, 0, h->Psicb, h->cb_user, s);
+  if (h->f_cb || h->psi_cb) CK(cudaGetLastError());
   std::vector<double> tv(std::max(1, h->nq) + std::max(1, h->npsi), 0.0);
   for (int q = 0; q < h->nq; ++q) tv[q] = tau_eval(h->tau_kind[q], h->tau_rate[q], t);
   for (int q = 0; q < h->npsi; ++q) tv[h->nq + q] = tau_eval(h->psi_kind[q], h->psi_rate[q], t);
@@ -1133,9 +1144,11 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   if (c->K < 1 || c->K > 255) return fail(h, SL_EINVAL, "K must be in 1..255");
   if (c->P < 1 || c->P > 4 || (!c->sigma && !c->sigma_field))
     return fail(h, SL_EINVAL, "P must be in 1..4 with sigma or sigma_field given");
-  if (src->nf < 1 || src->nf > 4 || src->nq < 1 || !src->phi || !src->G_dev || !src->tau_kind || !src->tau_rate)
-    return fail(h, SL_EINVAL, "source: need 1 <= nf <= 4, nq >= 1, phi, G, tau");
-  if (src->npsi < 0 || (src->npsi > 0 && (!src->Psi_dev || !src->psi_kind || !src->psi_rate)))
+  const bool fcb = src->f_cb != nullptr, pcb = src->psi_cb != nullptr;
+  if (src->nf < 1 || src->nf > 4 || !src->phi ||
+      (!fcb && (src->nq < 1 || !src->G_dev || !src->tau_kind || !src->tau_rate)))
+    return fail(h, SL_EINVAL, "source: need 1 <= nf <= 4, phi, and nq >= 1, G, tau or a source callback");
+  if (!pcb && (src->npsi < 0 || (src->npsi > 0 && (!src->Psi_dev || !src->psi_kind || !src->psi_rate))))
     return fail(h, SL_EINVAL, "boundary data incomplete");
   if (opts) h->o = *opts; else sl_opts_default(&h->o);
   if (h->o.precision != 0 && h->o.precision != 1) return fail(h, SL_EINVAL, "precision must be 0 or 1");
@@ -1154,14 +1167,26 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   h->K = c->K;
   h->P = c->P;
   h->nf = src->nf;
-  h->nq = src->nq;
-  h->npsi = src->npsi;
+  h->nq = fcb ? 1 : src->nq;
+  h->npsi = pcb ? 1 : src->npsi;
   h->G = src->G_dev;
   h->Psi = src->Psi_dev;
+  h->f_cb = src->f_cb;
+  h->psi_cb = src->psi_cb;
+  h->cb_user = src->cb_user;
+  h->grid = *g;
   h->phi.assign(src->phi, src->phi + size_t(c->K) * src->nf);
-  h->tau_kind.assign(src->tau_kind, src->tau_kind + src->nq);
-  h->tau_rate.assign(src->tau_rate, src->tau_rate + src->nq);
-  if (src->npsi > 0) {
+  if (fcb) {
+    h->tau_kind.assign(1, SL_TAU_ONE);
+    h->tau_rate.assign(1, 0.0);
+  } else {
+    h->tau_kind.assign(src->tau_kind, src->tau_kind + src->nq);
+    h->tau_rate.assign(src->tau_rate, src->tau_rate + src->nq);
+  }
+  if (pcb) {
+    h->psi_kind.assign(1, SL_TAU_ONE);
+    h->psi_rate.assign(1, 0.0);
+  } else if (src->npsi > 0) {
     h->psi_kind.assign(src->psi_kind, src->psi_kind + src->npsi);
     h->psi_rate.assign(src->psi_rate, src->psi_rate + src->npsi);
   }
@@ -1346,6 +1371,14 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   AL(h->Fvec, N);
   AL(h->F, N * h->nf);
   AL(h->F32, N * h->nf);
+  if (h->f_cb) {
+    AL(h->Gcb, N * h->nf);
+    h->G = h->Gcb;
+  }
+  if (h->psi_cb) {
+    AL(h->Psicb, N);
+    h->Psi = h->Psicb;
+  }
   AL(h->policy, size_t(h->m) * h->m);
   const bool p64 = h->o.precision == 0;
   KBuf &k = h->kb;
