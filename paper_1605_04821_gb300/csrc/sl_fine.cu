@@ -164,6 +164,10 @@ __device__ __forceinline__ float eval_itap32(const ArgminITaps &it, int k, const
   return acc;
 }
 
+// An opaque register move: the value can no longer be recomputed from its inputs, so it stays
+// in a register across the loop that uses it.
+__device__ __forceinline__ void pin_reg(float &v) { asm volatile("mov.b32 %0, %0;" : "+f"(v)); }
+
 __device__ __forceinline__ void cand_push(unsigned long long &cand, int &ncand, bool &overflow, int k) {
   if (ncand < kMaxCand) cand |= (unsigned long long)k << (8 * ncand++);
   else overflow = true;
@@ -254,14 +258,22 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
     bool overflow = false;
     if (SCREEN) {
       const float u = 5.9604645e-8f;
-      const float xj32 = float(Xj);
+      float xj32 = float(Xj);
       // node-constant part of E_k: f-term, c-term and the centring term 2 u (1 + u) D
       // (Dmax * 1.001 covers D: the staged |x'| are within a factor 1 + u of |X - c|)
-      const float Ef = u * ((nf + 3.0f) * Fabs * 1.001f + 3.0f * float(a.cmax) * fabsf(xj32) * 1.001f);
-      const float eta = 2.0f * u * Dmax * 1.001f + 1e-30f;
+      float Ef = u * ((nf + 3.0f) * Fabs * 1.001f + 3.0f * float(a.cmax) * fabsf(xj32) * 1.001f);
+      float eta = 2.0f * u * Dmax * 1.001f + 1e-30f;
       const float x0 = xs32[sidx];
       const bool itap = TMAX > 0 && it.n > 0 && q1 == tab.B && q2 == tab.B;
-      const float tw_rel = float(a.tie_rel) * 2.0f;
+      float tw_rel = float(a.tie_rel) * 2.0f;
+      // Keep these node constants in registers: left alone, the compiler recomputed the ones
+      // derived from FP64 values (X_j, tie_rel) inside the control loop, and each such
+      // FP64 -> FP32 conversion occupies GB300's narrow FP64 pipe (87 % busy, about two
+      // conversions per control and node, before this).
+      pin_reg(xj32);
+      pin_reg(Ef);
+      pin_reg(eta);
+      pin_reg(tw_rel);
       float Umin = INFINITY, Lmin = INFINITY;
       for (int k = 0; k < tab.K; ++k) {
         const int e = (k * tab.Q + q2) * tab.Q + q1;

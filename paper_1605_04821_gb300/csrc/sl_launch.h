@@ -222,4 +222,73 @@ void launch_init_scalars(BicgScalars *S, double tolrel2, cudaStream_t s);
 void launch_maxabs_diff(const double *a, const double *b, int n, double *out2,
                         unsigned *counter, double *partials, cudaStream_t s);
 
+
+// ---- device-side control of implicit steps (sl_control.cu) ----------------------------------
+// The loops of a step (Howard policy iteration, iterative refinement / restarts, BiCGSTAB) and
+// of a march run on the device as conditional nodes of one CUDA graph.  These single-thread
+// kernels read the loop state below, apply exactly the host loop's tests, and set the
+// conditional handles; every loop's counter is capped, so each while node ends.
+struct DevCtl {
+  int extrap;            // this step's first solve starts from 2 U^{n-1} - U^{n-2}
+  int need_improve;      // this step starts with an improvement on U^{n-1} (no policy yet)
+  int extrap_first, need_improve_first;  // the same for the first step of a march
+  int step, nsteps;      // march: current step (1-based) and its number of steps
+  int status;            // sl_status of the step or march (the first failure)
+  int pi_it;             // Howard iterations of the current step
+  int hier_valid;        // the Galerkin hierarchy belongs to the current policy and step size
+  int round, total;      // refinement round and Krylov iterations of the current solve
+  int kry_it, kry_maxit, kry_res, ls_done;
+  long long changes_since_build;
+  double tolk;           // threshold handed to BiCGSTAB's recurrence
+  double res_final;      // last relative 2-norm residual
+  // counts, accumulated until the host clears them
+  long long c_steps, c_improve0, c_pi, c_rebuild, c_ir, c_enter, c_kry, c_ok, c_changes;
+};
+
+// Kry results (DevCtl::kry_res)
+enum { KRY_RUNNING = 0, KRY_CONVERGED = 1, KRY_BREAKDOWN = 2, KRY_NONFINITE = 3, KRY_CAP = 4 };
+
+// Values the host hands to a single step graph (launched just before it).
+struct StepPrep {
+  double tau[8];         // tau_q(t_n), then tau'_q(t_n): the separable time factors
+  int ntau, extrap, need_improve, hier_valid;
+  long long changes_since_build;
+};
+
+void launch_ctl_step_prep(DevCtl *c, const StepPrep &p, double *d_tau, cudaStream_t s);
+void launch_ctl_march_begin(DevCtl *c, int nsteps, int extrap_first, int need_improve_first,
+                            cudaGraphConditionalHandle march, cudaStream_t s);
+void launch_ctl_step_begin(DevCtl *c, const double *tau_table, int ntau, double *d_tau, int extrap_opt,
+                           cudaGraphConditionalHandle improve0, cudaGraphConditionalHandle pi,
+                           cudaStream_t s);
+void launch_ctl_improved0(DevCtl *c, cudaStream_t s);
+void launch_extrapolate_ctl(double *X, const double *U, const double *V, int n, const DevCtl *c,
+                            cudaStream_t s);
+void launch_ctl_pi_pre(DevCtl *c, long long thresh, cudaGraphConditionalHandle rebuild, cudaStream_t s);
+void launch_ctl_built(DevCtl *c, cudaStream_t s);
+void launch_ctl_ls_begin(DevCtl *c, double tol, cudaGraphConditionalHandle ir, cudaStream_t s);
+void launch_init_scalars_ctl(BicgScalars *S, const DevCtl *c, cudaStream_t s);
+void launch_ctl_ir_decide(DevCtl *c, const BicgScalars *S, double tol, int fp64, int kry_max,
+                          cudaGraphConditionalHandle enter, cudaStream_t s);
+void launch_ctl_kry_begin(DevCtl *c, int fp64, int kry_max, cudaGraphConditionalHandle kry,
+                          cudaStream_t s);
+void launch_ctl_kry_check(DevCtl *c, const BicgScalars *S, cudaGraphConditionalHandle kry, cudaStream_t s);
+void launch_ctl_kry_end(DevCtl *c, int fp64, cudaStream_t s);
+void launch_ctl_ir_end(DevCtl *c, int rounds, cudaGraphConditionalHandle ir, cudaStream_t s);
+void launch_ctl_after_ls(DevCtl *c, cudaGraphConditionalHandle ok, cudaGraphConditionalHandle pi,
+                         cudaStream_t s);
+void launch_ctl_pi_post(DevCtl *c, const unsigned long long *changes, const int *flags,
+                        const double *maxd, double pi_tol, int pi_max, cudaGraphConditionalHandle pi,
+                        cudaStream_t s);
+void launch_ctl_march_end(DevCtl *c, cudaGraphConditionalHandle march, cudaStream_t s);
+
+// Explicit Galerkin rows with their count read from device memory (*count_dev, at most cap):
+// the launch shape does not depend on the classification, so a graph can rebuild the
+// hierarchy without the host.  Same per-row arithmetic as launch_rap_explicit.
+template <typename T>
+cudaError_t launch_rap_explicit_dev(int level, const FineTab &tab, const int32_t *fine_off,
+                                    const uint8_t *policy, T dt, const CoarseLev<T> &prev,
+                                    const int32_t *prev_coff, const CoarseLev<T> &cur,
+                                    const int *count_dev, int cap, T *ewin_out, cudaStream_t s);
+
 }  // namespace sl
