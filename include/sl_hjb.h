@@ -247,6 +247,14 @@ sl_status sl_hjb_adjoint(sl_hjb *h, const double *w_dev, double *dJ_dg_dev, doub
                          int nparam, const double *dsigma, double *dJ_dtheta, sl_stats *stats,
                          void *stream);
 
+/* Copies the policy that defined step `step`'s system A_step in the last sl_hjb_solve_record
+ * (1 <= step <= n_steps; the policy of the step's last linear solve, the one the adjoint
+ * differentiates at) to policy_dev ((n-2)^2 uint8, device).  Marching again with these
+ * policies fixed (sl_hjb_set_policy + sl_hjb_linear_solve per step) evaluates the smooth piece
+ * of the march whose derivative sl_hjb_adjoint returns.  SL_EINVAL without a record or for a
+ * step out of range.  Stream-ordered. */
+sl_status sl_hjb_recorded_policy(sl_hjb *h, int step, uint8_t *policy_dev, void *stream);
+
 const char *sl_hjb_last_error(const sl_hjb *h);
 void sl_hjb_destroy(sl_hjb *h);
 

@@ -29,7 +29,8 @@ EXPORTED = ["sl_opts_default", "sl_hjb_create", "sl_hjb_step", "sl_hjb_solve",
             "sl_hjb_vcycle_noalloc", "sl_hjb_solve_record", "sl_hjb_adjoint", "sl_hjb_reset",
             "sl_batch_create", "sl_batch_run", "sl_batch_worker_of", "sl_batch_plan",
             "sl_batch_last_error", "sl_batch_destroy", "sl_amg_create", "sl_amg_num_levels",
-            "sl_amg_level", "sl_amg_apply", "sl_amg_last_error", "sl_amg_destroy"]
+            "sl_amg_level", "sl_amg_apply", "sl_amg_last_error", "sl_amg_destroy",
+            "sl_hjb_recorded_policy"]
 
 
 class SlGrid(ctypes.Structure):
@@ -117,6 +118,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "sl_hjb_solve_record": (i, [vp, vp, d, d, i, i, ctypes.POINTER(SlStats), vp]),
         "sl_hjb_adjoint": (i, [vp, vp, vp, vp, i, vp, vp, ctypes.POINTER(SlStats), vp]),
         "sl_hjb_reset": (i, [vp]),
+        "sl_hjb_recorded_policy": (i, [vp, i, vp, vp]),
         "sl_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(SlInstance),
                                 ctypes.POINTER(SlOpts), i]),
         "sl_batch_run": (i, [vp, vp, ctypes.POINTER(SlStats)]),
@@ -392,6 +394,10 @@ class Solver:
             self.h, _ptr(w), _ptr(dJ_dg), _ptr(dJ_dG) if dJ_dG is not None else None, np_, ds_ptr,
             out.ctypes.data_as(ctypes.c_void_p) if np_ else None, ctypes.byref(s), _stream(stream)))
         return out, s.as_dict()
+
+    def recorded_policy(self, step: int, policy_out, stream=None):
+        """sl_hjb_recorded_policy: the policy of step `step` (1-based) of the last solve_record."""
+        self._check(self._lib.sl_hjb_recorded_policy(self.h, step, _ptr(policy_out), _stream(stream)))
 
     def num_levels(self) -> int:
         return self._lib.sl_hjb_num_levels(self.h)

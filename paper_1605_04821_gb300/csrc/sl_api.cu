@@ -1677,6 +1677,16 @@ sl_status sl_hjb_adjoint(sl_hjb *h, const double *w, double *dJ_dg, double *dJ_d
   return SL_OK;
 }
 
+sl_status sl_hjb_recorded_policy(sl_hjb *h, int step, uint8_t *policy_dev, void *stream) {
+  if (!h || !policy_dev) return SL_EINVAL;
+  if (!h->rec_valid || step < 1 || step > h->rec_N)
+    return fail(h, SL_EINVAL, "sl_hjb_recorded_policy: no recorded march, or step out of range");
+  const size_t M = size_t(h->m) * h->m;
+  CK(cudaMemcpyAsync(policy_dev, h->rec_pol + size_t(step - 1) * M, M, cudaMemcpyDeviceToDevice,
+                     static_cast<cudaStream_t>(stream)));
+  return SL_OK;
+}
+
 sl_status sl_hjb_level_info(const sl_hjb *h, int level, int *n, long long *explicit_rows, long long *nnz) {
   if (!h || level < 0 || level >= h->L) return SL_EINVAL;
   const CoarseBuf &c = h->cl[level];

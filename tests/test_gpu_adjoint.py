@@ -124,54 +124,80 @@ def test_autograd_function_returns_the_adjoint_gradients():
 
 def test_full_size_gradient_matches_central_differences_of_the_march():
     """1025^2, 33 controls, 64 steps, checkpoints every 8 steps: <dJ/dg, w> and dJ/dtheta
-    against central differences of the library's own FP64 forward march at 1e-6 relative.
-    The perturbed marches must take the base march's policy and Howard count at every step,
-    so that the differences stay on the piece of the piecewise-smooth map whose gradient the
-    adjoint gives: the step of each difference is the largest of a short decreasing list for
-    which that holds.  The marches solve to 1e-14 so that the differences resolve 1e-6."""
+    against central differences of the library's own FP64 march.
+
+    * On the piece (away from policy switches): every perturbed march runs at the recorded
+      per-step policies of the base march (sl_hjb_recorded_policy + sl_hjb_set_policy +
+      sl_hjb_linear_solve), which is the map whose derivative the adjoint is; 1e-6 relative.
+    * The full Howard march, beside it: at this size some of the 6.4e7 node-steps sit within
+      any usable step of a tie between two controls and switch, each moving J only at second
+      order; the switched node-steps are counted (a small fraction) and the difference must
+      agree to 1e-5.
+    The marches solve to 1e-14 so that the differences resolve 1e-6."""
+    import warnings
+
     import torch
     S = _lib()
     p, w = W.adjoint_1025(seed=0)
     dirs = W.sigma_directions(p)
     tol = 1e-14
+    m = p.n - 2
+    N = p.n_steps
+    dt = p.T / N
     sol = S.solver_from_problem(p, precision=0, krylov_tol=tol)
     u = to_dev(p.g)
-    sol.solve_record(u, 0.0, p.T, p.n_steps, 8)
+    sol.solve_record(u, 0.0, p.T, N, 8)
+    rec = torch.empty((N, m * m), dtype=torch.uint8, device=u.device)
+    for i in range(1, N + 1):
+        sol.recorded_policy(i, rec[i - 1])
     wd = to_dev(w)
     dg = torch.zeros_like(u)
     dth, _ = sol.adjoint(wd, dg, None, dirs)
     sol.close()
-    m = p.n - 2
-    dt = p.T / p.n_steps
 
-    def march(sigma=None, g=None):
+    def solver(sigma):
         q = copy.copy(p)
         if sigma is not None:
             q.sigma = sigma
-        s = S.solver_from_problem(q, precision=0, krylov_tol=tol)
+        return S.solver_from_problem(q, precision=0, krylov_tol=tol)
+
+    def march_fixed(sigma=None, g=None):
+        s = solver(sigma)
         uu = to_dev(p.g if g is None else g)
-        pols = torch.empty((p.n_steps, m * m), dtype=torch.uint8, device=uu.device)
-        its = []
-        for i in range(1, p.n_steps + 1):
-            st = s.step(uu, i * dt, dt, policy_out=pols[i - 1])
-            its.append(st["pi_iters"])
+        x = torch.empty_like(uu)
+        for i in range(1, N + 1):
+            s.set_policy(rec[i - 1])
+            x.copy_(uu)
+            s.linear_solve(uu, x, i * dt, dt)
+            uu, x = x, uu
         s.close()
-        return float((wd * uu).sum()), pols, its
+        return float((wd * uu).sum())
 
-    _, pol0, it0 = march()
+    def march_howard(sigma=None, g=None):
+        s = solver(sigma)
+        uu = to_dev(p.g if g is None else g)
+        pols = torch.empty((N, m * m), dtype=torch.uint8, device=uu.device)
+        for i in range(1, N + 1):
+            s.step(uu, i * dt, dt, policy_out=pols[i - 1])
+        s.close()
+        return float((wd * uu).sum()), pols
 
-    def central(make, steps):
-        for eps in steps:
-            Jp, pp, ip = march(**make(eps))
-            Jm, pm, im = march(**make(-eps))
-            if torch.equal(pp, pol0) and torch.equal(pm, pol0) and ip == it0 and im == it0:
-                return (Jp - Jm) / (2 * eps), eps
-        pytest.fail("every step of the list switched a policy")
-
+    _, pol0 = march_howard()
     d = w  # a coherent direction: the bump itself
-    fd_g, eps_g = central(lambda e: {"g": p.g + e * d}, (1e-5, 2e-6, 5e-7))
     ad_g = float((dg.cpu().numpy() * d).sum())
-    assert abs(fd_g - ad_g) <= 1e-6 * abs(fd_g), (fd_g, ad_g, eps_g)
+    cases = [("g", ad_g, 1e-3, 1e-5, lambda e: {"g": p.g + e * d})]
     for i, ds in enumerate(dirs):
-        fd, eps = central(lambda e: {"sigma": p.sigma + e * ds}, (2e-5, 5e-6, 1e-6))
-        assert abs(fd - dth[i]) <= 1e-6 * abs(fd), (i, fd, dth[i], eps)
+        cases.append((f"theta_{i}", float(dth[i]), 2e-5, 2e-5,
+                      lambda e, ds=ds: {"sigma": p.sigma + e * ds}))
+    for name, ad, eps_f, eps_h, make in cases:
+        fd = (march_fixed(**make(eps_f)) - march_fixed(**make(-eps_f))) / (2 * eps_f)
+        assert abs(fd - ad) <= 1e-6 * abs(fd), (name, "fixed policies", fd, ad)
+        Jp, pp = march_howard(**make(eps_h))
+        Jm, pm = march_howard(**make(-eps_h))
+        fdh = (Jp - Jm) / (2 * eps_h)
+        switched = int((pp != pol0).sum()) + int((pm != pol0).sum())
+        warnings.warn(f"{name}: adjoint {ad:.12e}, fixed-policy FD {fd:.12e} "
+                      f"({abs(fd - ad) / abs(fd):.1e}), Howard FD {fdh:.12e} "
+                      f"({abs(fdh - ad) / abs(fdh):.1e}, {switched} switched node-steps)")
+        assert switched <= 1e-3 * 2 * N * m * m, (name, switched)
+        assert abs(fdh - ad) <= 1e-5 * abs(fdh), (name, "Howard", fdh, ad, switched)
