@@ -131,8 +131,8 @@ def test_full_size_gradient_matches_central_differences_of_the_march():
       sl_hjb_linear_solve), which is the map whose derivative the adjoint is; 1e-6 relative.
     * The full Howard march, beside it: at this size some of the 6.4e7 node-steps sit within
       any usable step of a tie between two controls and switch, each moving J only at second
-      order; the switched node-steps are counted (a small fraction) and the difference must
-      agree to 1e-5.
+      order; the switched node-steps are counted (a small fraction: 27 to 364 of 1.3e8 when
+      this was written) and the difference must agree to 1e-6 as well.
     The marches solve to 1e-14 so that the differences resolve 1e-6."""
     import warnings
 
@@ -200,4 +200,4 @@ def test_full_size_gradient_matches_central_differences_of_the_march():
                       f"({abs(fd - ad) / abs(fd):.1e}), Howard FD {fdh:.12e} "
                       f"({abs(fdh - ad) / abs(fdh):.1e}, {switched} switched node-steps)")
         assert switched <= 1e-3 * 2 * N * m * m, (name, switched)
-        assert abs(fdh - ad) <= 1e-5 * abs(fdh), (name, "Howard", fdh, ad, switched)
+        assert abs(fdh - ad) <= 1e-6 * abs(fdh), (name, "Howard", fdh, ad, switched)
