@@ -264,6 +264,9 @@ sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_
   a.tie_rel = h->o.tie_rel;
   a.cmax = 0.0;
   for (double c : h->cvec) a.cmax = std::max(a.cmax, std::fabs(c));
+  a.tie2_32 = float(a.tie_rel) * 2.0f;
+  a.cmax32 = float(a.cmax);
+  for (int mm = 0; mm < 4; ++mm) a.phimax32[mm] = mm < h->nf ? float(h->phimax[mm]) : 0.f;
   a.Wmax_class = h->d_Wmaxc;
   a.policy = h->policy;
   a.changes = h->d_changes;

@@ -164,10 +164,6 @@ __device__ __forceinline__ float eval_itap32(const ArgminITaps &it, int k, const
   return acc;
 }
 
-// An opaque register move: the value can no longer be recomputed from its inputs, so it stays
-// in a register across the loop that uses it.
-__device__ __forceinline__ void pin_reg(float &v) { asm volatile("mov.b32 %0, %0;" : "+f"(v)); }
-
 __device__ __forceinline__ void cand_push(unsigned long long &cand, int &ncand, bool &overflow, int k) {
   if (ncand < kMaxCand) cand |= (unsigned long long)k << (8 * ncand++);
   else overflow = true;
@@ -243,37 +239,34 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
     const int sidx = (threadIdx.y + a.halo) * a.SW + threadIdx.x + a.halo;
     const size_t N = size_t(n) * n;
     const int nf = a.nf;  // 1..4 (checked at create)
-    double Fv[4];
-    float Fv32[4];
-    float Fabs = 0.f;
+    // The node's FP64 values (X_j, F_m(j)) are loaded by the FP64 comparisons that use them
+    // and are not held across the FP32 screen: with them live there, the compiler recomputed
+    // their FP32 copies inside the control loop, about two FP64 -> FP32 conversions per
+    // control and node, which filled GB300's narrow FP64 pipe (87 % busy).
+    auto load_fv = [&](double (&Fv)[4]) {
 #pragma unroll
-    for (int mm = 0; mm < 4; ++mm) {
-      Fv[mm] = mm < nf ? a.F[mm * N + j] : 0.0;
-      Fv32[mm] = mm < nf ? a.F32[mm * N + j] : 0.f;
-      if (mm < nf) Fabs = fmaf(float(a.phimax[mm]), fabsf(Fv32[mm]), Fabs);
-    }
-    const double Xj = a.X[j];
+      for (int mm = 0; mm < 4; ++mm) Fv[mm] = mm < nf ? a.F[mm * N + j] : 0.0;
+    };
     unsigned long long cand = 0ull;
     int ncand = 0;
     bool overflow = false;
     if (SCREEN) {
       const float u = 5.9604645e-8f;
-      float xj32 = float(Xj);
+      float Fv32[4];
+      float Fabs = 0.f;
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        Fv32[mm] = mm < nf ? a.F32[mm * N + j] : 0.f;
+        if (mm < nf) Fabs = fmaf(a.phimax32[mm], fabsf(Fv32[mm]), Fabs);
+      }
+      const float xj32 = float(a.X[j]);
       // node-constant part of E_k: f-term, c-term and the centring term 2 u (1 + u) D
       // (Dmax * 1.001 covers D: the staged |x'| are within a factor 1 + u of |X - c|)
-      float Ef = u * ((nf + 3.0f) * Fabs * 1.001f + 3.0f * float(a.cmax) * fabsf(xj32) * 1.001f);
-      float eta = 2.0f * u * Dmax * 1.001f + 1e-30f;
+      const float Ef = u * ((nf + 3.0f) * Fabs * 1.001f + 3.0f * a.cmax32 * fabsf(xj32) * 1.001f);
+      const float eta = 2.0f * u * Dmax * 1.001f + 1e-30f;
       const float x0 = xs32[sidx];
       const bool itap = TMAX > 0 && it.n > 0 && q1 == tab.B && q2 == tab.B;
-      float tw_rel = float(a.tie_rel) * 2.0f;
-      // Keep these node constants in registers: left alone, the compiler recomputed the ones
-      // derived from FP64 values (X_j, tie_rel) inside the control loop, and each such
-      // FP64 -> FP32 conversion occupies GB300's narrow FP64 pipe (87 % busy, about two
-      // conversions per control and node, before this).
-      pin_reg(xj32);
-      pin_reg(Ef);
-      pin_reg(eta);
-      pin_reg(tw_rel);
+      const float tw_rel = a.tie2_32;
       float Umin = INFINITY, Lmin = INFINITY;
       for (int k = 0; k < tab.K; ++k) {
         const int e = (k * tab.Q + q2) * tab.Q + q1;
@@ -308,6 +301,9 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
         }
       }
     } else {
+      double Fv[4];
+      load_fv(Fv);
+      const double Xj = a.X[j];
       double vmin = INFINITY;
       for (int k = 0; k < tab.K; ++k) {
         const int e = (k * tab.Q + q2) * tab.Q + q1;
@@ -338,6 +334,9 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
     } else if (ncand > 1 || overflow) {
       // pass 2: exact FP64 decision among the candidates (all controls on overflow)
       const int cnt = overflow ? tab.K : ncand;
+      double Fv[4];
+      load_fv(Fv);
+      const double Xj = a.X[j];
       double vm = INFINITY;
       double vals[kMaxCand];
       for (int c = 0; c < cnt; ++c) {

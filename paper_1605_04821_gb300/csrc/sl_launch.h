@@ -38,6 +38,9 @@ struct ArgminArgs {
   int nf;
   double tie_rel;
   double cmax;             // max_k |c_k|
+  float tie2_32;           // 2 fp32(tie_rel), cmax and phimax in FP32 for the screen's bound
+  float cmax32;            // (converted on the host: no FP64 value enters the FP32 loop)
+  float phimax32[4];
   const double *Wmax_class;  // [Q*Q]
   uint8_t *policy;         // in: current, out: improved
   unsigned long long *changes;
