@@ -50,7 +50,8 @@ typedef enum {
   SL_ECFL = 4,            /* dt * c^k > 1 for some control (Proposition 2.4, theta = 1) */
   SL_ENOCONV_PI = 5,      /* Howard iteration reached pi_max */
   SL_ENOCONV_KRYLOV = 6,  /* BiCGSTAB / refinement reached its iteration cap */
-  SL_EBREAKDOWN = 7,      /* BiCGSTAB breakdown (rho or omega vanished) */
+  SL_EBREAKDOWN = 7,      /* BiCGSTAB breakdown (rho or omega vanished); handled inside the
+                             solves by a restart, not returned by the step entry points */
   SL_ENAN = 8,            /* a NaN or Inf appeared in a residual or control value */
   SL_ETIMEOUT = 9         /* reserved: a bounded device-side wait gave up */
 } sl_status;
@@ -145,8 +146,14 @@ typedef struct {
                            Default 0.01: at 2049^2 fewer than 0.1 % of the rows change per
                            step, and rebuilding every step cost about 1.3 ms of a 19 ms step
                            for the same iteration count. */
-  int use_graphs;       /* 1: each BiCGSTAB iteration is one CUDA-graph launch (captured once
-                           per precision and step size); 0: plain stream launches */
+  int use_graphs;       /* 2: each implicit step is one CUDA-graph launch: its Howard,
+                           refinement / restart and BiCGSTAB loops are conditional graph nodes
+                           whose tests run on the device (captured once per step size), so a step
+                           reads the host only once at its end; used with the geometric V-cycle
+                           and x-independent sigma outside sl_hjb_solve_record, otherwise as 1.
+                           1: each BiCGSTAB iteration is one CUDA-graph launch (captured once per
+                           precision and step size); 0: plain stream launches.  All three run the
+                           same kernels in the same order and give the same result bit for bit. */
   int coarse_tail_rows; /* levels with at most this many rows run, from the first such level
                            down, in one thread block per V-cycle; 0: never; -1: default
                            (1024 rows in mixed precision, 0 in FP64, whose per-SM rate is low) */
@@ -172,12 +179,14 @@ typedef struct {
   long long policy_changes;   /* rows whose control changed, summed over improvements */
   long long explicit_rows;    /* coarse rows stored explicitly in the last build */
   double res_final;           /* last relative residual ||F - A X||_2 / ||F||_2 */
-  double t_argmin_ms, t_hier_ms, t_solve_ms;  /* host-timed phases (sync points) */
+  double t_argmin_ms, t_hier_ms, t_solve_ms;  /* host-timed phases (sync points; 0 for steps
+                                                 that ran as one graph launch) */
+  int graph_steps;            /* steps that ran as one graph launch (use_graphs 2) */
 } sl_stats;
 
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
- * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 1, coarse_tail_rows -1,
+ * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
  * extrapolate 1, precond 0, amg_k_levels 2. */
 void sl_opts_default(sl_opts *o);
 
@@ -194,8 +203,9 @@ sl_status sl_hjb_create(sl_hjb **h, const sl_grid *grid, const sl_controls *ctrl
  * The policy of the previous step is the starting policy; the first step starts from an
  * improvement on U^{n-1}.  policy_out_dev ((n-2)^2 uint8) receives the final policy if not
  * NULL.  stats (host, may be NULL) is overwritten with this step's counts.  Returns
- * SL_ECFL if dt * c^k > 1, SL_ENOCONV_PI / SL_ENOCONV_KRYLOV / SL_EBREAKDOWN / SL_ENAN on
- * failure of an iteration (u_dev then holds the last iterate). */
+ * SL_ECFL if dt * c^k > 1, SL_ENOCONV_PI / SL_ENOCONV_KRYLOV / SL_ENAN on failure of an
+ * iteration.  A BiCGSTAB breakdown is not an error of the step: the solve restarts from the
+ * true residual, and only when the restarts run out does the step end with SL_ENOCONV_KRYLOV. */
 sl_status sl_hjb_step(sl_hjb *h, double *u_dev, double t_n, double dt, uint8_t *policy_out_dev,
                       sl_stats *stats, void *stream);
 

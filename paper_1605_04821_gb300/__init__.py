@@ -77,7 +77,8 @@ class SlStats(ctypes.Structure):
                 ("ir_iters", ctypes.c_int), ("rebuilds", ctypes.c_int),
                 ("policy_changes", ctypes.c_longlong), ("explicit_rows", ctypes.c_longlong),
                 ("res_final", ctypes.c_double), ("t_argmin_ms", ctypes.c_double),
-                ("t_hier_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double)]
+                ("t_hier_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
+                ("graph_steps", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -17,8 +17,8 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libslhjb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-SOURCES = ["sl_api.cu", "sl_fine.cu", "sl_coarse.cu", "sl_krylov.cu", "sl_adjoint.cu", "sl_general.cu", "sl_amg.cu", "sl_geometry.cpp",
-           "sl_batch.cpp"]
+SOURCES = ["sl_api.cu", "sl_fine.cu", "sl_coarse.cu", "sl_krylov.cu", "sl_adjoint.cu", "sl_general.cu",
+           "sl_amg.cu", "sl_control.cu", "sl_geometry.cpp", "sl_batch.cpp"]
 
 
 def nvcc() -> str:

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
@@ -48,6 +49,16 @@ struct IterGraph {  // one captured BiCGSTAB iteration
   double dt = -1.0;
   long long kernels = 0;
   long long gen = -1;  // AMG hierarchy generation it was captured with
+};
+
+// One captured implicit step (use_graphs 2): the Howard, refinement and BiCGSTAB loops are
+// conditional nodes of the graph, so a step is one graph launch.  The counts are the kernels
+// captured directly in each loop body (the host adds them up from the device's loop counts).
+struct DevStepGraph {
+  cudaGraphExec_t exec = nullptr;
+  double dt = -1.0;
+  long long k_step = 0, k_imp0 = 0, k_pi = 0, k_rebuild = 0, k_ir = 0, k_enter = 0, k_kry = 0,
+            k_ok = 0;
 };
 
 struct KBuf {  // BiCGSTAB vectors on the finest level
@@ -146,6 +157,12 @@ struct sl_hjb {
   int rec_N = 0, rec_k = 0;
   double rec_t0 = 0.0, rec_dt = 0.0;
   bool rec_valid = false;
+  // device-driven steps (use_graphs 2): loop state on the device and its pinned host mirror,
+  // the streams that capture nested conditional bodies, and the captured step
+  DevCtl *ctl = nullptr, *h_ctl = nullptr;
+  cudaStream_t cap_pool[8] = {};
+  DevStepGraph sgraph;
+  bool dev_off = false;                        // a capture failed: host-driven steps from then on
   AmgEngine amg;                               // precond 1
   ArgminITaps *itaps = nullptr;                // interior-class taps for the argmin's parameter
   long long amg_gen = 0;                       // bumped by every AMG setup (its sizes change)
@@ -235,21 +252,8 @@ sl_status coef(sl_hjb *h, double t, double *Xext, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------- argmin
-sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_t s) {
-  if (h->general) {
-    CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
-    CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
-    launch_argmin_general(h->gen, h->dtab, h->dtab.c64, Xext, h->F, h->d_phi, h->nf, h->o.tie_rel,
-                          h->policy, h->d_changes, h->d_flags, s);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(h->h_changes, h->d_changes, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (*h->h_flags & 1) return fail(h, SL_ENAN, "non-finite control value in the policy improvement");
-    if (changes) *changes = (long long)*h->h_changes;
-    h->have_policy = true;
-    return SL_OK;
-  }
+// Arguments of the policy improvement on Xext (psi on the boundary) for the handle's tables.
+ArgminArgs argmin_args(sl_hjb *h, const double *Xext) {
   ArgminArgs a{};
   a.tab = h->tab;
   a.slin = h->d_slin;
@@ -275,6 +279,25 @@ sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_
   a.SW = h->SW;
   a.SH = h->SH;
   a.screen = h->o.argmin_screen;
+  return a;
+}
+
+sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_t s) {
+  if (h->general) {
+    CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+    launch_argmin_general(h->gen, h->dtab, h->dtab.c64, Xext, h->F, h->d_phi, h->nf, h->o.tie_rel,
+                          h->policy, h->d_changes, h->d_flags, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_changes, h->d_changes, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*h->h_flags & 1) return fail(h, SL_ENAN, "non-finite control value in the policy improvement");
+    if (changes) *changes = (long long)*h->h_changes;
+    h->have_policy = true;
+    return SL_OK;
+  }
+  const ArgminArgs a = argmin_args(h, Xext);
   CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
   CK(launch_argmin(a, *h->itaps, s));
@@ -439,6 +462,16 @@ sl_status build_hierarchy_T(sl_hjb *h, double dt, cudaStream_t s) {
   return SL_OK;
 }
 
+// Host-built class stencils and the fine Jacobi scales for step size dt (when dt changes).
+sl_status ensure_class_tables(sl_hjb *h, double dt, cudaStream_t s) {
+  if (h->class_valid && h->class_dt == dt) return SL_OK;
+  sl_status st = build_class_tables(h, dt);
+  if (st != SL_OK) return st;
+  if (!h->general) launch_fine_od(h->tab, dt, h->o.omega, h->d_od64, h->d_od32, h->d_iod64, h->d_iod32, s);
+  CK(cudaGetLastError());
+  return SL_OK;
+}
+
 sl_status build_hierarchy(sl_hjb *h, double dt, cudaStream_t s) {
   if (h->general) {  // the fine rows of the current policy and step size
     launch_assemble_general(h->gen, h->dtab, h->policy, h->dtab.c64, dt, h->o.omega, h->SW, h->gout, s);
@@ -457,13 +490,9 @@ sl_status build_hierarchy(sl_hjb *h, double dt, cudaStream_t s) {
     ++h->amg_gen;
     return SL_OK;
   }
-  if (!h->class_valid || h->class_dt != dt) {
-    sl_status st = build_class_tables(h, dt);
-    if (st != SL_OK) return st;
-    if (!h->general) launch_fine_od(h->tab, dt, h->o.omega, h->d_od64, h->d_od32, h->d_iod64, h->d_iod32, s);
-    CK(cudaGetLastError());
-  }
-  sl_status st = (h->o.precision == 0) ? build_hierarchy_T<double>(h, dt, s)
+  sl_status st = ensure_class_tables(h, dt, s);
+  if (st != SL_OK) return st;
+  st = (h->o.precision == 0) ? build_hierarchy_T<double>(h, dt, s)
                                        : build_hierarchy_T<float>(h, dt, s);
   if (st != SL_OK) return st;
   h->hier_valid = true;
@@ -849,6 +878,399 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
   return fail(h, SL_ENOCONV_PI, "Howard iteration reached pi_max");
 }
 
+// ---------------------------------------------------------------------- device-driven steps
+// use_graphs 2: a step is captured once per step size as one CUDA graph whose Howard,
+// refinement and BiCGSTAB loops are conditional nodes.  The graph runs the kernels of
+// step_impl / linear_solve / bicgstab in the same order on the same buffers; the single-thread
+// control kernels of sl_control.cu take the host loop's decisions on the device, so a step
+// costs one graph launch and one read of the loop state.
+
+cudaError_t cap_stream_at(sl_hjb *h, int depth, cudaStream_t *out) {
+  if (depth < 0 || depth >= 8) return cudaErrorInvalidValue;
+  if (!h->cap_pool[depth]) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap_pool[depth], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  *out = h->cap_pool[depth];
+  return cudaSuccess;
+}
+
+// A conditional handle of the graph that stream s is capturing into.
+cudaError_t new_cond_handle(cudaStream_t s, cudaGraphConditionalHandle *hd) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureInvalidated;
+  return cudaGraphConditionalHandleCreate(hd, g, 0, 0);
+}
+
+// Captures body(stream, depth, &nested) into a new graph body; nested collects the kernels of
+// deeper conditionals so that each body's own kernel count stays separate.
+using BodyFn = std::function<sl_status(cudaStream_t, int, long long *)>;
+
+// Adds a conditional node (while / if on handle hd) after the work captured so far on s,
+// captures the body on the capture stream of the next depth, and orders the next work on s
+// after the node.  *direct: kernels captured in the body itself; *total: with deeper bodies.
+sl_status add_cond(sl_hjb *h, cudaStream_t s, int depth, cudaGraphConditionalHandle hd,
+                   cudaGraphConditionalNodeType type, long long *direct, long long *total,
+                   const BodyFn &body) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *ed = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &ed, &nd));
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hd;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  CK(cudaGraphAddNode(&node, g, deps, ed, nd, &p));
+  cudaStream_t sb = nullptr;
+  CK(cap_stream_at(h, depth + 1, &sb));
+  CK(cudaStreamBeginCaptureToGraph(sb, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  const long long before = thread_launch_count();
+  long long nested = 0;
+  const sl_status st = body(sb, depth + 1, &nested);
+  cudaGraph_t og = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(sb, &og);
+  if (st != SL_OK) return st;
+  CK(e);
+  *total = thread_launch_count() - before;
+  *direct = *total - nested;
+  CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return SL_OK;
+}
+
+// Ends any capture left open on the handle's capture streams (after a failed capture).
+void abandon_captures(sl_hjb *h) {
+  for (int d = 7; d >= 0; --d) {
+    cudaStream_t cs = h->cap_pool[d];
+    if (!cs) continue;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(cs, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(cs, &g);
+      if (g) cudaGraphDestroy(g);
+    }
+  }
+  cudaGetLastError();
+}
+
+// Galerkin hierarchy for the current policy with every launch shape fixed: the explicit-row
+// counts stay on the device (build_hierarchy_T reads them back to size its launches).
+template <typename T>
+sl_status cap_hierarchy_T(sl_hjb *h, double dt, cudaStream_t s) {
+  for (int l = 1; l < h->L; ++l) {
+    CoarseBuf &c = h->cl[l];
+    CoarseBuf &p = h->cl[l - 1];
+    launch_classify(l, h->tab, h->policy, p.cls, p.n, c.cls, c.n, c.erow, c.d_nexpl, h->chunk_scratch, s);
+    CoarseLev<T> prevv = lev_view<T>(h, l - 1), curv = lev_view<T>(h, l);
+    CK(launch_rap_explicit_dev<T>(l, h->tab, h->d_off, h->policy, T(dt), prevv, p.coff, curv, c.d_nexpl,
+                                  c.cap, pick<T>(c.ewin64, c.ewin32), s));
+  }
+  const int lc = h->L - 1;
+  CoarseLev<T> cv = lev_view<T>(h, lc);
+  launch_coarsest_setup<T>(lc, h->tab, h->policy, T(dt), cv, lc == 0 ? h->d_off : h->cl[lc].coff,
+                           h->cwork, pick<T>(h->Ainv64, h->Ainv32), s);
+  CK(cudaGetLastError());
+  return SL_OK;
+}
+
+// BiCGSTAB on the Krylov vectors of precision T (x accumulated in TX), the iterations a while
+// node: the prologue of bicgstab(), then issue_iteration() and the device stop test.
+template <typename T, typename TX>
+sl_status cap_bicgstab(sl_hjb *h, double dt, TX *x, T *r, T *rh, T *p, T *v, T *sv, T *t, T *ph,
+                       T *sh, BicgScalars *S, cudaStream_t s, int depth, long long *nested,
+                       DevStepGraph &G) {
+  const size_t N = NN(h, 0);
+  const int fp64 = sizeof(T) == 8 ? 1 : 0;
+  cudaGraphConditionalHandle hk;
+  CK(new_cond_handle(s, &hk));
+  CK(cudaMemcpyAsync(rh, r, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  launch_dot2<T>(r, r, r, r, N, POST_RHO_INIT, S, h->partials, h->counter, s);
+  launch_ctl_kry_begin(h->ctl, fp64, h->o.kry_max, hk, s);
+  long long tot = 0;
+  const sl_status st = add_cond(h, s, depth, hk, cudaGraphCondTypeWhile, &G.k_kry, &tot,
+                                [&](cudaStream_t sb, int, long long *) -> sl_status {
+                                  sl_status r2 = issue_iteration<T, TX>(h, dt, x, r, rh, p, v, sv, t, ph, sh, S, sb);
+                                  if (r2 != SL_OK) return r2;
+                                  launch_ctl_kry_check(h->ctl, S, hk, sb);
+                                  CK(cudaGetLastError());
+                                  return SL_OK;
+                                });
+  *nested += tot;
+  return st;
+}
+
+// linear_solve() with its refinement / restart rounds a while node and the Krylov part of a
+// round an if node.
+sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long long *nested,
+                           DevStepGraph &G) {
+  const size_t N = NN(h, 0);
+  const bool fp64 = h->o.precision == 0;
+  KBuf &k = h->kb;
+  launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, h->halo,
+                   h->SW, s, std::max(1, h->cl[0].R));
+  cudaGraphConditionalHandle hir;
+  CK(new_cond_handle(s, &hir));
+  launch_ctl_ls_begin(h->ctl, h->o.krylov_tol, hir, s);
+  const int rounds = fp64 ? 12 : h->o.ir_max + 1;
+  long long tot = 0;
+  const sl_status st = add_cond(
+      h, s, depth, hir, cudaGraphCondTypeWhile, &G.k_ir, &tot,
+      [&](cudaStream_t sb, int d, long long *nest) -> sl_status {
+        double *r64 = fp64 ? k.r64 : h->R;
+        launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r64, h->halo, h->SW, sb);
+        launch_init_scalars_ctl(h->S, h->ctl, sb);
+        launch_norms(h->Fvec, N, 0, h->S, h->partials, h->counter, sb);
+        launch_norms(r64, N, 1, h->S, h->partials, h->counter, sb);
+        cudaGraphConditionalHandle hen;
+        CK(new_cond_handle(sb, &hen));
+        launch_ctl_ir_decide(h->ctl, h->S, h->o.krylov_tol, fp64 ? 1 : 0, h->o.kry_max, hen, sb);
+        long long t2 = 0;
+        const sl_status s2 = add_cond(
+            h, sb, d, hen, cudaGraphCondTypeIf, &G.k_enter, &t2,
+            [&](cudaStream_t sc, int d2, long long *nest2) -> sl_status {
+              sl_status s3;
+              if (fp64) {
+                s3 = cap_bicgstab<double, double>(h, dt, h->X, k.r64, k.rh64, k.p64, k.v64, k.s64, k.t64,
+                                                  k.ph64, k.sh64, h->S, sc, d2, nest2, G);
+              } else {
+                launch_convert<double, float>(h->R, k.r32, N, sc);
+                launch_fill<float>(k.e32, N, 0.0f, sc);
+                launch_init_scalars(h->S32, h->o.inner_tol * h->o.inner_tol, sc);
+                launch_dot2<float>(k.r32, k.r32, nullptr, nullptr, N, POST_BNORM, h->S32, h->partials,
+                                   h->counter, sc);
+                s3 = cap_bicgstab<float, float>(h, dt, k.e32, k.r32, k.rh32, k.p32, k.v32, k.s32, k.t32,
+                                                k.ph32, k.sh32, h->S32, sc, d2, nest2, G);
+                if (s3 == SL_OK) launch_add_f32_to_f64(h->X, k.e32, N, sc);
+              }
+              if (s3 != SL_OK) return s3;
+              launch_ctl_kry_end(h->ctl, fp64 ? 1 : 0, sc);
+              CK(cudaGetLastError());
+              return SL_OK;
+            });
+        *nest += t2;
+        if (s2 != SL_OK) return s2;
+        launch_ctl_ir_end(h->ctl, rounds, hir, sb);
+        CK(cudaGetLastError());
+        return SL_OK;
+      });
+  *nested += tot;
+  return st;
+}
+
+// The argmin with its change counter and flags cleared first (improve() without the host read).
+sl_status cap_improve(sl_hjb *h, cudaStream_t s) {
+  CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+  CK(launch_argmin(argmin_args(h, h->X), *h->itaps, s));
+  return SL_OK;
+}
+
+// One Howard iteration: rebuild (if node), linear solve, then improvement and stop test (if
+// node, taken when the solve succeeded).
+sl_status cap_pi_body(sl_hjb *h, double dt, cudaStream_t s, int depth, long long *nested,
+                      DevStepGraph &G, cudaGraphConditionalHandle hpi) {
+  const size_t N = NN(h, 0);
+  cudaGraphConditionalHandle hrb, hok;
+  CK(new_cond_handle(s, &hrb));
+  CK(new_cond_handle(s, &hok));
+  const long long thresh = (long long)(h->o.rebuild_frac * double(h->m) * h->m);
+  launch_ctl_pi_pre(h->ctl, thresh, hrb, s);
+  long long t = 0;
+  sl_status st = add_cond(h, s, depth, hrb, cudaGraphCondTypeIf, &G.k_rebuild, &t,
+                          [&](cudaStream_t sb, int, long long *) -> sl_status {
+                            const sl_status r = h->o.precision == 0 ? cap_hierarchy_T<double>(h, dt, sb)
+                                                                    : cap_hierarchy_T<float>(h, dt, sb);
+                            if (r != SL_OK) return r;
+                            launch_ctl_built(h->ctl, sb);
+                            return SL_OK;
+                          });
+  *nested += t;
+  if (st != SL_OK) return st;
+  st = cap_linear_solve(h, dt, s, depth, nested, G);
+  if (st != SL_OK) return st;
+  launch_ctl_after_ls(h->ctl, hok, hpi, s);
+  st = add_cond(h, s, depth, hok, cudaGraphCondTypeIf, &G.k_ok, &t,
+                [&](cudaStream_t sb, int, long long *) -> sl_status {
+                  const sl_status r = cap_improve(h, sb);
+                  if (r != SL_OK) return r;
+                  launch_maxabs_diff(h->X, h->Xpi, h->n, h->d_maxd, h->counter, h->partials, sb);
+                  launch_ctl_pi_post(h->ctl, h->d_changes, h->d_flags, h->d_maxd, h->o.pi_tol,
+                                     h->o.pi_max, hpi, sb);
+                  CK(cudaMemcpyAsync(h->Xpi, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, sb));
+                  CK(cudaGetLastError());
+                  return SL_OK;
+                });
+  *nested += t;
+  return st;
+}
+
+// The work of one step after U^{n-1} is in Uprev (and U^{n-2} in Uprev2): tables, the first
+// improvement of a march (if node), extrapolation, and the Howard loop (while node).
+// tau_table: per-step time factors of a march (nullptr: d_tau is set before each launch).
+sl_status cap_step_body(sl_hjb *h, double dt, cudaStream_t s, int depth, long long *nested,
+                        DevStepGraph &G, const double *tau_table) {
+  const size_t N = NN(h, 0);
+  cudaGraphConditionalHandle him, hpi;
+  CK(new_cond_handle(s, &him));
+  CK(new_cond_handle(s, &hpi));
+  launch_ctl_step_begin(h->ctl, tau_table, h->nq + h->npsi, h->d_tau, h->o.extrapolate, him, hpi, s);
+  CK(cudaMemcpyAsync(h->X, h->Uprev, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  launch_coef(h->G, h->nf, h->nq, h->d_tau, h->Psi, h->npsi, h->d_tau + h->nq, h->n, h->F, h->F32,
+              h->X, h->Xb, s);
+  long long t = 0;
+  sl_status st = add_cond(h, s, depth, him, cudaGraphCondTypeIf, &G.k_imp0, &t,
+                          [&](cudaStream_t sb, int, long long *) -> sl_status {
+                            const sl_status r = cap_improve(h, sb);
+                            if (r != SL_OK) return r;
+                            launch_ctl_improved0(h->ctl, sb);
+                            return SL_OK;
+                          });
+  *nested += t;
+  if (st != SL_OK) return st;
+  CK(cudaMemcpyAsync(h->Xpi, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  launch_extrapolate_ctl(h->X, h->Uprev, h->Uprev2, h->n, h->ctl, s);
+  st = add_cond(h, s, depth, hpi, cudaGraphCondTypeWhile, &G.k_pi, &t,
+                [&](cudaStream_t sb, int d, long long *nest) -> sl_status {
+                  return cap_pi_body(h, dt, sb, d, nest, G, hpi);
+                });
+  *nested += t;
+  CK(cudaGetLastError());
+  return st;
+}
+
+// Steps run on the device when nothing in the middle of a step needs the host: the geometric
+// V-cycle, the class-table fine level, no recording for the adjoint.
+bool dev_step_ok(const sl_hjb *h) {
+  return h->o.use_graphs == 2 && !h->dev_off && !h->general && h->o.precond == 0 && !h->rec_slot &&
+         !h->transposed && h->nq + h->npsi <= 8;
+}
+
+// Kernels one step graph launch ran, from the device's loop counts.
+long long dev_kernels(const DevStepGraph &G, const DevCtl &c) {
+  return G.k_step * c.c_steps + G.k_imp0 * c.c_improve0 + G.k_pi * c.c_pibody + G.k_rebuild * c.c_rebuild +
+         G.k_ir * c.c_ir + G.k_enter * c.c_enter + G.k_kry * c.c_kry + G.k_ok * c.c_ok;
+}
+
+// Captures the step graph for step size dt (after the host-side tables for dt).
+sl_status ensure_step_graph(sl_hjb *h, double dt, cudaStream_t s) {
+  DevStepGraph &G = h->sgraph;
+  if (G.exec && G.dt == dt) return SL_OK;
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G = DevStepGraph{};
+  sl_status st = ensure_class_tables(h, dt, s);
+  if (st != SL_OK) return st;
+  CK(cudaStreamSynchronize(s));
+  cudaStream_t cs = nullptr;
+  CK(cap_stream_at(h, 0, &cs));
+  const long long before = thread_launch_count();
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  long long nested = 0;
+  st = cap_step_body(h, dt, cs, 0, &nested, G, nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  const long long captured = thread_launch_count() - before;
+  note_launch(int(-captured));  // captured, not executed
+  G.k_step = captured - nested;
+  if (st == SL_OK && e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (st != SL_OK || e != cudaSuccess) {
+    abandon_captures(h);
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G = DevStepGraph{};
+    return st != SL_OK ? st : fail(h, SL_ECUDA, std::string("step graph: ") + cudaGetErrorString(e));
+  }
+  G.dt = dt;
+  return SL_OK;
+}
+
+sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out, sl_stats *st,
+                    cudaStream_t s);
+
+// One implicit step as one graph launch (the same kernels and results as step_impl).
+sl_status step_device(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out, sl_stats *st,
+                      cudaStream_t s) {
+  if (!(dt > 0)) return fail(h, SL_EINVAL, "dt must be positive");
+  for (double c : h->cvec)
+    if (dt * c > 1.0) return fail(h, SL_ECFL, "dt * c > 1 violates the positivity condition");
+  if (ensure_step_graph(h, dt, s) != SL_OK) {
+    h->dev_off = true;
+    std::fprintf(stderr, "sl_hjb: step graph unavailable (%s); steps are host-driven\n", h->err.c_str());
+    return step_impl(h, u, t, dt, pol_out, st, s);
+  }
+  const size_t N = NN(h, 0);
+  const bool extrap = h->o.extrapolate && h->have_prev2 && h->prev_dt == dt &&
+                      std::fabs(h->prev_t + dt - t) <= 1e-12 * std::max(1.0, std::fabs(t));
+  if (h->o.extrapolate) CK(cudaMemcpyAsync(h->Uprev2, h->Uprev, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->Uprev, u, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (h->f_cb)
+    for (int mm = 0; mm < h->nf; ++mm) h->f_cb(t, &h->grid, mm, h->Gcb + mm * N, h->cb_user, s);
+  if (h->psi_cb) h->psi_cb(t, &h->grid, 0, h->Psicb, h->cb_user, s);
+  StepPrep p{};
+  p.ntau = h->nq + h->npsi;
+  for (int q = 0; q < h->nq; ++q) p.tau[q] = tau_eval(h->tau_kind[q], h->tau_rate[q], t);
+  for (int q = 0; q < h->npsi; ++q) p.tau[h->nq + q] = tau_eval(h->psi_kind[q], h->psi_rate[q], t);
+  p.extrap = extrap ? 1 : 0;
+  p.need_improve = h->have_policy ? 0 : 1;
+  p.hier_valid = (h->hier_valid && h->hier_dt == dt) ? 1 : 0;
+  p.changes_since_build = h->changes_since_build;
+  CK(cudaMemsetAsync(h->ctl, 0, sizeof(DevCtl), s));
+  launch_ctl_step_prep(h->ctl, p, h->d_tau, s);
+  CK(cudaGraphLaunch(h->sgraph.exec, s));
+  CK(cudaMemcpyAsync(u, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (pol_out) CK(cudaMemcpyAsync(pol_out, h->policy, size_t(h->m) * h->m, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const DevCtl &c = *h->h_ctl;
+  note_launch(int(dev_kernels(h->sgraph, c)));
+  h->have_policy = true;
+  h->have_prev2 = h->o.extrapolate != 0;
+  h->prev_t = t;
+  h->prev_dt = dt;
+  h->hier_valid = c.hier_valid != 0;
+  if (c.c_rebuild) h->hier_dt = dt;
+  h->changes_since_build = c.changes_since_build;
+  if (c.c_rebuild)
+    for (int l = 1; l < h->L; ++l)
+      CK(cudaMemcpy(&h->cl[l].nexpl, h->cl[l].d_nexpl, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    st->steps += 1;
+    st->graph_steps += 1;
+    st->pi_iters += int(c.c_pi);
+    st->krylov_iters += int(c.c_kry);
+    if (h->o.precision != 0) st->ir_iters += int(c.c_enter);
+    st->rebuilds += int(c.c_rebuild);
+    st->policy_changes += c.c_changes;
+    st->res_final = c.res_final;
+    if (c.c_rebuild) {
+      long long ex = 0;
+      for (int l = 1; l < h->L; ++l) ex += h->cl[l].nexpl;
+      st->explicit_rows = ex;
+    }
+  }
+  switch (c.status) {
+    case SL_OK: return SL_OK;
+    case SL_ENAN: return fail(h, SL_ENAN, "non-finite value in the step (control value, residual or iterate)");
+    case SL_ENOCONV_PI: return fail(h, SL_ENOCONV_PI, "Howard iteration reached pi_max");
+    case SL_ENOCONV_KRYLOV:
+      return fail(h, SL_ENOCONV_KRYLOV, h->o.precision == 0 ? "BiCGSTAB reached its iteration cap"
+                                                             : "iterative refinement reached ir_max");
+    default: return fail(h, sl_status(c.status), "step failed on the device");
+  }
+}
+
+// The step of the public entry points.
+sl_status step_any(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out, sl_stats *st,
+                   cudaStream_t s) {
+  return dev_step_ok(h) ? step_device(h, u, t, dt, pol_out, st, s) : step_impl(h, u, t, dt, pol_out, st, s);
+}
+
 // ---------------------------------------------------------------------- adjoint
 // Grows a device buffer (contents are not kept).
 template <typename T>
@@ -1110,7 +1532,7 @@ void sl_opts_default(sl_opts *o) {
   o->tie_rel = 1e-12;
   o->argmin_screen = 0;
   o->rebuild_frac = 0.01;
-  o->use_graphs = 1;
+  o->use_graphs = 2;
   o->coarse_tail_rows = -1;
   o->extrapolate = 1;
   o->precond = 0;
@@ -1127,6 +1549,10 @@ void sl_hjb_destroy(sl_hjb *h) {
   for (auto &g : h->graphT)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->sgraph.exec) cudaGraphExecDestroy(h->sgraph.exec);
+  for (cudaStream_t cs : h->cap_pool)
+    if (cs) cudaStreamDestroy(cs);
+  if (h->h_ctl) cudaFreeHost(h->h_ctl);
   amg_free(h->amg);
   for (void *p : h->allocs) cudaFree(p);
   if (h->hS) cudaFreeHost(h->hS);
@@ -1431,6 +1857,9 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   AL(h->d_changes, 1);
   AL(h->d_flags, 1);
   AL(h->d_count, 1);
+  AL(h->ctl, 1);
+  CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_ctl), sizeof(DevCtl)));
+  std::memset(h->h_ctl, 0, sizeof(DevCtl));
   CK(cudaMallocHost(reinterpret_cast<void **>(&h->hS), sizeof(BicgScalars)));
   CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_maxd), 2 * sizeof(double)));
   CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_changes), sizeof(unsigned long long)));
@@ -1461,7 +1890,7 @@ sl_status sl_hjb_step(sl_hjb *h, double *u, double t_n, double dt, uint8_t *pol_
                       void *stream) {
   if (!h || !u) return SL_EINVAL;
   if (st) std::memset(st, 0, sizeof(*st));
-  return step_impl(h, u, t_n, dt, pol_out, st, static_cast<cudaStream_t>(stream));
+  return step_any(h, u, t_n, dt, pol_out, st, static_cast<cudaStream_t>(stream));
 }
 
 sl_status sl_hjb_solve(sl_hjb *h, double *u, double t0, double T, int n_steps, uint8_t *pol_out,
@@ -1470,7 +1899,7 @@ sl_status sl_hjb_solve(sl_hjb *h, double *u, double t0, double T, int n_steps, u
   if (st) std::memset(st, 0, sizeof(*st));
   const double dt = T / n_steps;
   for (int i = 1; i <= n_steps; ++i) {
-    sl_status r = step_impl(h, u, t0 + i * dt, dt, pol_out, st, static_cast<cudaStream_t>(stream));
+    sl_status r = step_any(h, u, t0 + i * dt, dt, pol_out, st, static_cast<cudaStream_t>(stream));
     if (r != SL_OK) return r;
   }
   return SL_OK;

@@ -118,6 +118,13 @@ void launch_classify(int level, const FineTab &tab, const uint8_t *policy, const
 // ----------------------------------------------------------------------------- explicit RAP
 // Thread per explicit coarse row; the (2R+1)^2 window accumulates in shared memory.  Row
 // 2I + a of the previous level contributes R_a * (its coefficient at column j) * P_{jJ}.
+// The window of one explicit coarse row (slot), accumulated in `win` (cur.win entries).
+template <typename T>
+__device__ void rap_explicit_row(int level, const FineTab &tab, const int32_t *__restrict__ fine_off,
+                                 const uint8_t *__restrict__ policy, T dt, const CoarseLev<T> &prev,
+                                 const int32_t *__restrict__ prev_coff, const CoarseLev<T> &cur,
+                                 int slot, T *win, T *__restrict__ ewin_out);
+
 template <typename T>
 __global__ void k_rap_explicit(int level, FineTab tab, const int32_t *__restrict__ fine_off,
                                const uint8_t *__restrict__ policy, T dt, CoarseLev<T> prev,
@@ -127,6 +134,28 @@ __global__ void k_rap_explicit(int level, FineTab tab, const int32_t *__restrict
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= count) return;
   T *win = reinterpret_cast<T *>(smem_raw) + size_t(threadIdx.x) * cur.win;
+  rap_explicit_row<T>(level, tab, fine_off, policy, dt, prev, prev_coff, cur, slot, win, ewin_out);
+}
+
+// The same rows with their number read from device memory, over a grid-stride loop: the launch
+// shape depends only on the capacity, so a CUDA graph can rebuild the hierarchy on the device.
+template <typename T>
+__global__ void k_rap_explicit_dev(int level, FineTab tab, const int32_t *__restrict__ fine_off,
+                                   const uint8_t *__restrict__ policy, T dt, CoarseLev<T> prev,
+                                   const int32_t *__restrict__ prev_coff, CoarseLev<T> cur,
+                                   const int *__restrict__ count_dev, T *__restrict__ ewin_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int count = *count_dev;
+  T *win = reinterpret_cast<T *>(smem_raw) + size_t(threadIdx.x) * cur.win;
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < count; slot += gridDim.x * blockDim.x)
+    rap_explicit_row<T>(level, tab, fine_off, policy, dt, prev, prev_coff, cur, slot, win, ewin_out);
+}
+
+template <typename T>
+__device__ void rap_explicit_row(int level, const FineTab &tab, const int32_t *__restrict__ fine_off,
+                                 const uint8_t *__restrict__ policy, T dt, const CoarseLev<T> &prev,
+                                 const int32_t *__restrict__ prev_coff, const CoarseLev<T> &cur,
+                                 int slot, T *win, T *__restrict__ ewin_out) {
   for (int e = 0; e < cur.win; ++e) win[e] = T(0);
   const int jr = cur.erow[slot];
   const int I1 = jr % cur.n, I2 = jr / cur.n;
@@ -169,6 +198,35 @@ __global__ void k_rap_explicit(int level, FineTab tab, const int32_t *__restrict
     }
   for (int e = 0; e < cur.win; ++e) ewin_out[size_t(e) * cur.cap + slot] = win[e];
 }
+
+template <typename T>
+cudaError_t launch_rap_explicit_dev(int level, const FineTab &tab, const int32_t *fine_off,
+                                    const uint8_t *policy, T dt, const CoarseLev<T> &prev,
+                                    const int32_t *prev_coff, const CoarseLev<T> &cur,
+                                    const int *count_dev, int cap, T *ewin_out, cudaStream_t s) {
+  if (cap <= 0) return cudaSuccess;
+  const size_t per = size_t(cur.win) * sizeof(T);
+  int threads = int((200 * 1024) / per);
+  threads = threads > 128 ? 128 : threads;
+  if (threads < 1) return cudaErrorInvalidValue;
+  const size_t bytes = per * threads;
+  // two resident blocks per SM at most (the windows take up to 200 KB); a grid of that size
+  // strides over the rows, and blocks beyond the row count exit at once
+  int blocks = (cap + threads - 1) / threads;
+  blocks = blocks > 2 * 152 ? 2 * 152 : blocks;
+  note_launch();
+  k_rap_explicit_dev<T><<<blocks, threads, bytes, s>>>(level, tab, fine_off, policy, dt, prev,
+                                                       prev_coff, cur, count_dev, ewin_out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_rap_explicit_dev<double>(int, const FineTab &, const int32_t *,
+                                                     const uint8_t *, double, const CoarseLev<double> &,
+                                                     const int32_t *, const CoarseLev<double> &,
+                                                     const int *, int, double *, cudaStream_t);
+template cudaError_t launch_rap_explicit_dev<float>(int, const FineTab &, const int32_t *,
+                                                    const uint8_t *, float, const CoarseLev<float> &,
+                                                    const int32_t *, const CoarseLev<float> &,
+                                                    const int *, int, float *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_rap_explicit(int level, const FineTab &tab, const int32_t *fine_off,
@@ -656,6 +714,7 @@ template void launch_coarsest_apply<float>(const float *, int, const float *, fl
 template <typename T>
 static cudaError_t prepare_coarse_T() {
   const void *fs[] = {reinterpret_cast<const void *>(k_rap_explicit<T>),
+                      reinterpret_cast<const void *>(k_rap_explicit_dev<T>),
                       reinterpret_cast<const void *>(k_coarse_op<T, OP_APPLY, 0>),
                       reinterpret_cast<const void *>(k_coarse_op<T, OP_RESID, 0>),
                       reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI, 0>),

@@ -100,6 +100,7 @@ void launch_extrapolate_ctl(double *X, const double *U, const double *V, int n, 
 // than `thresh` rows changed control since it was built.
 __global__ void k_ctl_pi_pre(DevCtl *c, long long thresh, cudaGraphConditionalHandle rebuild) {
   const bool rb = !c->hier_valid || c->changes_since_build > thresh;
+  c->c_pibody += 1;
   if (rb) c->c_rebuild += 1;
   cudaGraphSetConditional(rebuild, rb ? 1u : 0u);
 }

@@ -245,7 +245,7 @@ struct DevCtl {
   double tolk;           // threshold handed to BiCGSTAB's recurrence
   double res_final;      // last relative 2-norm residual
   // counts, accumulated until the host clears them
-  long long c_steps, c_improve0, c_pi, c_rebuild, c_ir, c_enter, c_kry, c_ok, c_changes;
+  long long c_steps, c_improve0, c_pibody, c_pi, c_rebuild, c_ir, c_enter, c_kry, c_ok, c_changes;
 };
 
 // Kry results (DevCtl::kry_res)
