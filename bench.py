@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--amg-steps", type=int, default=8)
     p.add_argument("--batched-instances", type=int, default=256)
     p.add_argument("--batched-workers", type=int, default=16)
+    p.add_argument("--batched-one-worker", action="store_true",
+                   help="also time the batch with a single worker thread (about 25 s)")
     p.add_argument("--adjoint-steps", type=int, default=64,
                    help="steps of 1/64 in the adjoint workload's march (64: T = 1)")
     p.add_argument("--opt", action="append", default=[],
@@ -514,9 +516,12 @@ def amg_record(slp, prob, dev, stream, args, extra, g):
 
 
 def batched_record(slp, W, dev, args, extra, rank, world, barrier, dist):
-    """The batched workload (independent instances of the same PDE family) with W worker
-    threads and, for comparison, with one; each run is timed on the host around
-    sl_batch_run, which returns when every instance's stream is idle."""
+    """The batched workload (independent instances of the same PDE family), LPT-sharded over the
+    ranks and over W worker threads per rank, each with its own stream, every BiCGSTAB iteration
+    one graph launch (use_graphs 1: these overlap across streams better than the device-driven
+    steps).  Timed on the host around sl_batch_run, which returns when every instance's stream
+    is idle: once with the default launch configuration, then with the one sl_batch_autotune
+    chooses per grid size (the V-cycle tail, by probe runs of the whole batch)."""
     import torch
     probs = W.batched(n_inst=args.batched_instances, seed=0)
     mine = slp.shard(probs, world, rank)
@@ -524,14 +529,15 @@ def batched_record(slp, W, dev, args, extra, rank, world, barrier, dist):
     us = [torch.as_tensor(p.g, dtype=torch.float64, device=dev) for p in sub]
     kw = dict(precision=1, argmin_screen=1)
     kw.update(extra)
+    kw["use_graphs"] = 1
     out = {"workload": f"{len(probs)} instances of the uncertain-correlation family: n uniform in "
                        "{65,129,257,513}, (s1,s2) ~ U[0.15,0.4]^2, K ~ U{17..65}, rho in "
                        "[-0.9,0.9], 32 steps of 1/32 (seed 0); mixed precision",
            "unit": UNIT, "instances": len(probs), "scaling": "weak" if world > 1 else None,
            "sharding": "LPT over ranks by n^2 * steps * (K + 32), no collective" if world > 1 else None}
     gp = sum(p.n * p.n * p.n_steps for p in sub)
-    for workers, key in ((args.batched_workers, "concurrent"), (1, "one_worker")):
-        b = slp.Batch(sub, us, workers=workers, device=dev, **kw)
+
+    def timed_run(b, key, workers):
         for u, p in zip(us, sub):
             u.copy_(torch.as_tensor(p.g, device=dev))
         b.run()   # warm-up: graphs and class tables of every handle
@@ -558,11 +564,26 @@ def batched_record(slp, W, dev, args, extra, rank, world, barrier, dist):
                     "failed": int(sum(1 for x in st if x != 0)), "gpu_launches": launches,
                     "pi_iters": int(sum(s["pi_iters"] for s in stats)),
                     "krylov_iters": int(sum(s["krylov_iters"] for s in stats))}
+
+    b = slp.Batch(sub, us, workers=args.batched_workers, device=dev, **kw)
+    timed_run(b, "default_launch", args.batched_workers)
+    t0 = time.perf_counter()
+    choices = b.autotune(probe_steps=3)
+    out["autotune"] = {"seconds": time.perf_counter() - t0, "probe_steps": 3,
+                       "choices": choices, "tunable": "single-block V-cycle tail (coarse_tail_rows) "
+                                                      "per grid size"}
+    timed_run(b, "concurrent", args.batched_workers)
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    if args.batched_one_worker:
+        b = slp.Batch(sub, us, workers=1, device=dev, **kw)
+        timed_run(b, "one_worker", 1)
         b.close()
         del b
         torch.cuda.empty_cache()
+        out["speedup_vs_one_worker"] = out["concurrent"]["value"] / out["one_worker"]["value"]
     out["value"] = out["concurrent"]["value"]
-    out["speedup_vs_one_worker"] = out["concurrent"]["value"] / out["one_worker"]["value"]
     return out
 
 

@@ -257,6 +257,13 @@ sl_status sl_hjb_adjoint(sl_hjb *h, const double *w_dev, double *dJ_dg_dev, doub
                          int nparam, const double *dsigma, double *dJ_dtheta, sl_stats *stats,
                          void *stream);
 
+/* Changes the launch configuration of a handle: use_graphs and coarse_tail_rows as in sl_opts
+ * (the same steps, launched differently; the single-block tail adds its coarse-level sums in
+ * another order, so moving levels into or out of it changes results at rounding level).
+ * Captured graphs are dropped and captured again by the next step.  Synchronises the device.
+ * SL_EINVAL for use_graphs outside 0..2. */
+sl_status sl_hjb_set_launch(sl_hjb *h, int use_graphs, int coarse_tail_rows);
+
 /* Copies the policy that defined step `step`'s system A_step in the last sl_hjb_solve_record
  * (1 <= step <= n_steps; the policy of the step's last linear solve, the one the adjoint
  * differentiates at) to policy_dev ((n-2)^2 uint8, device).  Marching again with these
@@ -334,6 +341,30 @@ int sl_batch_worker_of(const sl_batch *b, int i);
  * items taken in decreasing cost (ties by index) and each placed in the least-loaded bin
  * (ties by the lowest bin).  Returns SL_OK or SL_EINVAL. */
 int sl_batch_plan(int n_items, const double *cost, int n_bins, int *bin_of);
+
+/* One grid size's launch configuration, as chosen by sl_batch_autotune. */
+typedef struct {
+  int n;                  /* nodes per dimension of the instances it applies to */
+  int instances;          /* instances of the batch with that size */
+  int coarse_tail_rows;   /* chosen single-block V-cycle tail (sl_opts.coarse_tail_rows; 0 = none) */
+  double probe_seconds;   /* wall time of the fastest probe run of the whole batch */
+} sl_tune_choice;
+
+/* Autotuner of the batch's launch configuration; the paper has no counterpart.  Once many small
+ * grids run concurrently, a batch is limited by kernel launches more than by arithmetic, and the
+ * single-block V-cycle tail trades grid-wide launches on the coarse levels for the work of one
+ * thread block.  For each grid size of the batch, in decreasing order of its share of the work,
+ * every tail size that moves the tail to another level (levels of at most max_tail_rows rows,
+ * and none) is timed by a probe run of the whole batch -- every instance, probe_steps implicit
+ * steps after one untimed step that captures the graphs, from its current state -- with the
+ * other sizes at their current choice, and the fastest is kept (coordinate descent, one pass).
+ * The instances' state vectors are restored afterwards, so sl_batch_run starts from the same
+ * data, and each handle keeps its chosen configuration (sl_hjb_set_launch).  The choices go to
+ * out (capacity max_out; *n_out receives their number).  The tail only changes the order of the
+ * coarse levels' sums: every instance still equals, bit for bit, a single solve with the same
+ * configuration.  Allocates one state copy per instance for the duration of the call. */
+sl_status sl_batch_autotune(sl_batch *b, int probe_steps, int max_tail_rows, sl_tune_choice *out,
+                            int max_out, int *n_out);
 
 const char *sl_batch_last_error(const sl_batch *b);
 void sl_batch_destroy(sl_batch *b);

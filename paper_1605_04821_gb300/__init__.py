@@ -30,7 +30,7 @@ EXPORTED = ["sl_opts_default", "sl_hjb_create", "sl_hjb_step", "sl_hjb_solve",
             "sl_batch_create", "sl_batch_run", "sl_batch_worker_of", "sl_batch_plan",
             "sl_batch_last_error", "sl_batch_destroy", "sl_amg_create", "sl_amg_num_levels",
             "sl_amg_level", "sl_amg_apply", "sl_amg_last_error", "sl_amg_destroy",
-            "sl_hjb_recorded_policy"]
+            "sl_hjb_recorded_policy", "sl_hjb_set_launch", "sl_batch_autotune"]
 
 
 class SlGrid(ctypes.Structure):
@@ -70,6 +70,11 @@ class SlInstance(ctypes.Structure):
     _fields_ = [("grid", SlGrid), ("ctrl", SlControls), ("src", SlSource),
                 ("u_dev", ctypes.c_void_p), ("t0", ctypes.c_double), ("T", ctypes.c_double),
                 ("n_steps", ctypes.c_int)]
+
+
+class SlTuneChoice(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("instances", ctypes.c_int), ("coarse_tail_rows", ctypes.c_int),
+                ("probe_seconds", ctypes.c_double)]
 
 
 class SlStats(ctypes.Structure):
@@ -120,6 +125,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "sl_hjb_adjoint": (i, [vp, vp, vp, vp, i, vp, vp, ctypes.POINTER(SlStats), vp]),
         "sl_hjb_reset": (i, [vp]),
         "sl_hjb_recorded_policy": (i, [vp, i, vp, vp]),
+        "sl_hjb_set_launch": (i, [vp, i, i]),
+        "sl_batch_autotune": (i, [vp, i, i, vp, i, ctypes.POINTER(i)]),
         "sl_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(SlInstance),
                                 ctypes.POINTER(SlOpts), i]),
         "sl_batch_run": (i, [vp, vp, ctypes.POINTER(SlStats)]),
@@ -396,6 +403,12 @@ class Solver:
             out.ctypes.data_as(ctypes.c_void_p) if np_ else None, ctypes.byref(s), _stream(stream)))
         return out, s.as_dict()
 
+    def set_launch(self, use_graphs: int, coarse_tail_rows: int):
+        """sl_hjb_set_launch: graph mode and single-block V-cycle tail of this handle."""
+        self._check(self._lib.sl_hjb_set_launch(self.h, use_graphs, coarse_tail_rows))
+        self.opts.use_graphs = use_graphs
+        self.opts.coarse_tail_rows = coarse_tail_rows
+
     def recorded_policy(self, step: int, policy_out, stream=None):
         """sl_hjb_recorded_policy: the policy of step `step` (1-based) of the last solve_record."""
         self._check(self._lib.sl_hjb_recorded_policy(self.h, step, _ptr(policy_out), _stream(stream)))
@@ -486,6 +499,16 @@ class Batch:
         stats = (SlStats * self.n)()
         self._lib.sl_batch_run(self.b, st, stats)
         return [int(x) for x in st], [s.as_dict() for s in stats]
+
+    def autotune(self, probe_steps: int = 3, max_tail_rows: int = 16384):
+        """sl_batch_autotune: per grid size, the V-cycle tail that gave the fastest probe run of
+        the whole batch; returns [{n, instances, coarse_tail_rows, probe_seconds}, ...]."""
+        out = (SlTuneChoice * 64)()
+        k = ctypes.c_int(0)
+        st = self._lib.sl_batch_autotune(self.b, probe_steps, max_tail_rows, out, 64, ctypes.byref(k))
+        if st != SL_OK:
+            raise SLError(st, self.last_error())
+        return [{f: getattr(out[j], f) for f, _ in SlTuneChoice._fields_} for j in range(min(k.value, 64))]
 
     def worker_of(self, i: int) -> int:
         return int(self._lib.sl_batch_worker_of(self.b, i))

@@ -232,6 +232,27 @@ double now_ms() {
 
 size_t NN(const sl_hjb *h, int l) { return size_t(h->cl[l].n) * h->cl[l].n; }
 
+// First level run by the single-block V-cycle tail (0: none), from opts.coarse_tail_rows.
+void set_tail(sl_hjb *h) {
+  h->tail_l0 = 0;
+  const int tail_rows = h->o.coarse_tail_rows >= 0 ? h->o.coarse_tail_rows : (h->o.precision == 0 ? 0 : 1024);
+  for (int l = 1; l < h->L - 1 && tail_rows > 0; ++l)
+    if (h->cl[l].m * h->cl[l].m <= tail_rows) {
+      h->tail_l0 = l;
+      break;
+    }
+}
+
+// Drops every captured graph (they hold launch shapes and the V-cycle's structure).
+void drop_graphs(sl_hjb *h) {
+  for (auto &g : h->graph)
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g = IterGraph{}; }
+  for (auto &g : h->graphT)
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g = IterGraph{}; }
+  if (h->sgraph.exec) cudaGraphExecDestroy(h->sgraph.exec);
+  h->sgraph = DevStepGraph{};
+}
+
 // ---------------------------------------------------------------------- per-step tables
 sl_status coef(sl_hjb *h, double t, double *Xext, cudaStream_t s) {
   const size_t NNc = size_t(h->n) * h->n;
@@ -1088,7 +1109,10 @@ sl_status cap_pi_body(sl_hjb *h, double dt, cudaStream_t s, int depth, long long
                             const sl_status r = h->o.precision == 0 ? cap_hierarchy_T<double>(h, dt, sb)
                                                                     : cap_hierarchy_T<float>(h, dt, sb);
                             if (r != SL_OK) return r;
-                            launch_ctl_built(h->ctl, sb);
+                            NexplPtrs np{};
+                            np.L = h->L;
+                            for (int l = 1; l < h->L && l < 16; ++l) np.p[l] = h->cl[l].d_nexpl;
+                            launch_ctl_built(h->ctl, np, sb);
                             return SL_OK;
                           });
   *nested += t;
@@ -1237,8 +1261,7 @@ sl_status step_device(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_ou
   if (c.c_rebuild) h->hier_dt = dt;
   h->changes_since_build = c.changes_since_build;
   if (c.c_rebuild)
-    for (int l = 1; l < h->L; ++l)
-      CK(cudaMemcpy(&h->cl[l].nexpl, h->cl[l].d_nexpl, sizeof(int), cudaMemcpyDeviceToHost));
+    for (int l = 1; l < h->L && l < 16; ++l) h->cl[l].nexpl = c.nexpl[l];
   if (st) {
     st->steps += 1;
     st->graph_steps += 1;
@@ -1840,10 +1863,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
     const size_t m1 = size_t(h->cl[1].m);
     AL(h->chunk_scratch, 2 * ((m1 * m1 + 255) / 256) + 2);
   }
-  h->tail_l0 = 0;
-  const int tail_rows = h->o.coarse_tail_rows >= 0 ? h->o.coarse_tail_rows : (p64 ? 0 : 1024);
-  for (int l = 1; l < h->L - 1 && tail_rows > 0; ++l)
-    if (h->cl[l].m * h->cl[l].m <= tail_rows) { h->tail_l0 = l; break; }
+  set_tail(h);
   const int mc = h->cl[h->L - 1].m;
   AL(h->cwork, size_t(2) * mc * mc * mc * mc);
   if (p64) AL(h->Ainv64, size_t(mc) * mc * mc * mc);
@@ -2106,6 +2126,16 @@ sl_status sl_hjb_adjoint(sl_hjb *h, const double *w, double *dJ_dg, double *dJ_d
   // the handle's policy and hierarchy now belong to step 1; the next march starts afresh
   h->hier_valid = false;
   h->have_prev2 = false;
+  return SL_OK;
+}
+
+sl_status sl_hjb_set_launch(sl_hjb *h, int use_graphs, int coarse_tail_rows) {
+  if (!h || use_graphs < 0 || use_graphs > 2) return SL_EINVAL;
+  CK(cudaDeviceSynchronize());
+  h->o.use_graphs = use_graphs;
+  h->o.coarse_tail_rows = coarse_tail_rows;
+  set_tail(h);
+  drop_graphs(h);
   return SL_OK;
 }
 

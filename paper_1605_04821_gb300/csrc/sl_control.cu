@@ -109,13 +109,14 @@ void launch_ctl_pi_pre(DevCtl *c, long long thresh, cudaGraphConditionalHandle r
   k_ctl_pi_pre<<<1, 1, 0, s>>>(c, thresh, rebuild);
 }
 
-__global__ void k_ctl_built(DevCtl *c) {
+__global__ void k_ctl_built(DevCtl *c, NexplPtrs np) {
   c->hier_valid = 1;
   c->changes_since_build = 0;
+  for (int l = 1; l < np.L && l < 16; ++l) c->nexpl[l] = *np.p[l];
 }
-void launch_ctl_built(DevCtl *c, cudaStream_t s) {
+void launch_ctl_built(DevCtl *c, const NexplPtrs &np, cudaStream_t s) {
   note_launch();
-  k_ctl_built<<<1, 1, 0, s>>>(c);
+  k_ctl_built<<<1, 1, 0, s>>>(c, np);
 }
 
 // Start of a linear solve.

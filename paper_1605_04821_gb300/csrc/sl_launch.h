@@ -246,6 +246,13 @@ struct DevCtl {
   double res_final;      // last relative 2-norm residual
   // counts, accumulated until the host clears them
   long long c_steps, c_improve0, c_pibody, c_pi, c_rebuild, c_ir, c_enter, c_kry, c_ok, c_changes;
+  int nexpl[16];         // explicit rows of each level after the last rebuild in the graph
+};
+
+// Explicit-row counts of the coarse levels, gathered into DevCtl::nexpl (levels 1 .. L-1).
+struct NexplPtrs {
+  const int *p[16];
+  int L;
 };
 
 // Kry results (DevCtl::kry_res)
@@ -268,7 +275,7 @@ void launch_ctl_improved0(DevCtl *c, cudaStream_t s);
 void launch_extrapolate_ctl(double *X, const double *U, const double *V, int n, const DevCtl *c,
                             cudaStream_t s);
 void launch_ctl_pi_pre(DevCtl *c, long long thresh, cudaGraphConditionalHandle rebuild, cudaStream_t s);
-void launch_ctl_built(DevCtl *c, cudaStream_t s);
+void launch_ctl_built(DevCtl *c, const NexplPtrs &np, cudaStream_t s);
 void launch_ctl_ls_begin(DevCtl *c, double tol, cudaGraphConditionalHandle ir, cudaStream_t s);
 void launch_init_scalars_ctl(BicgScalars *S, const DevCtl *c, cudaStream_t s);
 void launch_ctl_ir_decide(DevCtl *c, const BicgScalars *S, double tol, int fp64, int kry_max,

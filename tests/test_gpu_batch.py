@@ -124,3 +124,38 @@ def test_many_workers_on_uneven_instances_never_fail():
         else:
             assert all(torch.equal(a, u) for a, u in zip(first, us))
     b.close()
+
+
+def test_autotuned_batch_equals_single_solves_with_the_chosen_launch():
+    """sl_batch_autotune picks a V-cycle tail per grid size from probe runs of the whole batch,
+    restores the state vectors, and every instance then equals, bit for bit, a single solve with
+    the chosen configuration (and the oracle within the mixed tolerance)."""
+    import torch
+    from oracle import lisl
+    from tests._gpu_util import TOL_MIXED
+    S = _lib()
+    probs = W.batched(n_inst=10, seed=5, sizes=(65, 129), k_range=(5, 17), n_steps=4, T=0.25)
+    us = [to_dev(p.g) for p in probs]
+    b = S.Batch(probs, us, workers=4, precision=1, argmin_screen=1, nu1=1, nu2=1, use_graphs=1)
+    choices = b.autotune(probe_steps=1, max_tail_rows=4096)
+    assert sorted(c["n"] for c in choices) == sorted(set(p.n for p in probs))
+    level_rows = {65: {0, 31 * 31, 15 * 15, 7 * 7}, 129: {0, 63 * 63, 31 * 31, 15 * 15, 7 * 7}}
+    for c in choices:
+        assert c["coarse_tail_rows"] in level_rows[c["n"]], c
+        assert c["probe_seconds"] > 0
+    for p, u in zip(probs, us):
+        assert torch.equal(u, to_dev(p.g))
+    st, _ = b.run()
+    torch.cuda.synchronize()
+    assert st == [0] * len(probs), b.last_error()
+    tail = {c["n"]: c["coarse_tail_rows"] for c in choices}
+    for p, u in zip(probs, us):
+        sol = S.solver_from_problem(p, precision=1, argmin_screen=1, nu1=1, nu2=1, use_graphs=1,
+                                    coarse_tail_rows=tail[p.n])
+        v = to_dev(p.g)
+        sol.solve(v, 0.0, p.T, p.n_steps)
+        sol.close()
+        assert torch.equal(u, v)
+    p, u = probs[0], us[0]
+    assert rel_maxnorm(u.cpu().numpy(), lisl.solve(p).U) <= TOL_MIXED
+    b.close()
