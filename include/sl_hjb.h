@@ -53,7 +53,8 @@ typedef enum {
   SL_EBREAKDOWN = 7,      /* BiCGSTAB breakdown (rho or omega vanished); handled inside the
                              solves by a restart, not returned by the step entry points */
   SL_ENAN = 8,            /* a NaN or Inf appeared in a residual or control value */
-  SL_ETIMEOUT = 9         /* reserved: a bounded device-side wait gave up */
+  SL_ETIMEOUT = 9         /* a bounded device-side wait gave up (the TMA tile copies of the
+                             fine operator did not arrive) */
 } sl_status;
 
 /* Grid of Eq. 1.1 (Section 2.4: "N_x x N_x equispaced nodes"). */
@@ -168,6 +169,11 @@ typedef struct {
                            solve.  The V-cycle entry points and sl_hjb_adjoint need precond 0. */
   int amg_k_levels;     /* precond 1: coarse levels 1..amg_k_levels take two GCR steps, deeper
                            levels one */
+  int fine_tma;         /* 1: the FP32 fine-level operator (apply, residual, Jacobi sweep) runs as
+                           a persistent kernel whose interior tiles are copied into shared memory
+                           by the TMA unit (cp.async.bulk, double-buffered: the next tile is in
+                           flight while the current one is computed); 0: the threads stage every
+                           tile.  Same arithmetic per row, same result bit for bit. */
 } sl_opts;
 
 typedef struct {
@@ -187,7 +193,7 @@ typedef struct {
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
  * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
- * extrapolate 1, precond 0, amg_k_levels 2. */
+ * extrapolate 1, precond 0, amg_k_levels 2, fine_tma 1. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every

@@ -63,7 +63,8 @@ class SlOpts(ctypes.Structure):
                 ("pi_tol", ctypes.c_double), ("pi_max", ctypes.c_int), ("tie_rel", ctypes.c_double),
                 ("argmin_screen", ctypes.c_int), ("rebuild_frac", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("coarse_tail_rows", ctypes.c_int),
-                ("extrapolate", ctypes.c_int), ("precond", ctypes.c_int), ("amg_k_levels", ctypes.c_int)]
+                ("extrapolate", ctypes.c_int), ("precond", ctypes.c_int), ("amg_k_levels", ctypes.c_int),
+                ("fine_tma", ctypes.c_int)]
 
 
 class SlInstance(ctypes.Structure):

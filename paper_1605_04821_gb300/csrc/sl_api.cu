@@ -891,6 +891,14 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
       if (pol_out)
         CK(cudaMemcpyAsync(pol_out, h->policy, size_t(h->m) * h->m, cudaMemcpyDeviceToDevice, s));
       (void)t0;
+      if (h->tab.tma) {  // a bounded wait of the TMA fine operator that gave up
+        CK(cudaMemcpyAsync(&h->h_ctl->tma_err, &h->ctl->tma_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->h_ctl->tma_err) {
+          CK(cudaMemsetAsync(&h->ctl->tma_err, 0, sizeof(int), s));
+          return fail(h, SL_ETIMEOUT, "a bounded wait for the TMA tile copies of the fine operator gave up");
+        }
+      }
       return SL_OK;
     }
     CK(cudaMemcpyAsync(h->Xpi, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1277,6 +1285,7 @@ sl_status step_device(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_ou
       st->explicit_rows = ex;
     }
   }
+  if (c.tma_err) return fail(h, SL_ETIMEOUT, "a bounded wait for the TMA tile copies of the fine operator gave up");
   switch (c.status) {
     case SL_OK: return SL_OK;
     case SL_ENAN: return fail(h, SL_ENAN, "non-finite value in the step (control value, residual or iterate)");
@@ -1560,6 +1569,7 @@ void sl_opts_default(sl_opts *o) {
   o->extrapolate = 1;
   o->precond = 0;
   o->amg_k_levels = 2;
+  o->fine_tma = 1;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -1686,7 +1696,12 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   const FineTabHost &ft = h->ft;
   const int R0 = h->general ? std::max(ft.R0, h->nd.R0) : ft.R0;
   h->halo = std::max(1, R0);
-  h->SW = 32 + 2 * h->halo;
+  // Row pitch of the staged fine tiles: at least 3 columns beyond the 32 + 2 halo staged ones,
+  // and congruent to n mod 4, so that each tile row and its global row have the same offset
+  // within 16 bytes: a row can then be copied by the TMA unit (cp.async.bulk) from its
+  // 16-byte-aligned start, the extra columns taking the rounding at either end.
+  h->SW = 32 + 2 * h->halo + 3;
+  while ((h->SW - h->n) % 4 != 0) ++h->SW;
   h->SH = 8 + 2 * h->halo;
   if (size_t(h->SW) * (32 + 2 * h->halo) * sizeof(double) > 200 * 1024)
     return fail(h, SL_EINVAL, "stencil too wide for the shared-memory tiles");
@@ -1782,6 +1797,8 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   AL(h->d_od32, size_t(h->K) * ft.Q * ft.Q);
   t.od64 = h->d_od64; t.od32 = h->d_od32;
   t.general = 0;
+  t.tma = 0;
+  t.tma_err = nullptr;
   if (h->general) {
     // the tables above hold the drift part; the fine level reads per-row entries
     h->dtab = t;
@@ -1878,6 +1895,8 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   AL(h->d_flags, 1);
   AL(h->d_count, 1);
   AL(h->ctl, 1);
+  h->tab.tma = (h->o.fine_tma && !h->general) ? 1 : 0;
+  h->tab.tma_err = &h->ctl->tma_err;
   CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_ctl), sizeof(DevCtl)));
   std::memset(h->h_ctl, 0, sizeof(DevCtl));
   CK(cudaMallocHost(reinterpret_cast<void **>(&h->hS), sizeof(BicgScalars)));

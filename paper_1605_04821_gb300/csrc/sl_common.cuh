@@ -78,6 +78,10 @@ struct FineTab {
   const float *iWc32;     // [k] the same difference taken in FP32 (W32[e] - c32[k])
   const double *iod64;    // [k] od of the interior entry
   const float *iod32;
+  // FP32 operator with TMA-staged tiles (k_fine_op_tma): 1 to use it where it applies; err is
+  // set to 1 by a bounded wait that gave up
+  int tma;
+  int *tma_err;
 };
 
 // Table entry of row (i1, i2) whose control is k: the (control, boundary class) entry, or, on
@@ -151,9 +155,12 @@ template <> struct PackedTap<double> {
 // latency serves the whole pass.  (A loop that stores each value right after loading it makes
 // every load wait for the previous one, since the store waits for its data and instructions
 // issue in order; on a level with one block per SM nothing hides that.)  Columns from 64 on,
-// for wide halos, are copied one by one.
+// for wide halos, are copied one by one.  SW is the row pitch of xs; the first `width` columns
+// of each row are staged (width < 0: all SW).
 template <int NR, typename T, typename Load>
-__device__ __forceinline__ void stage_window(T *xs, int SW, int SH, int tx, int ty, Load load) {
+__device__ __forceinline__ void stage_window(T *xs, int SW, int SH, int tx, int ty, Load load,
+                                             int width = -1) {
+  const int WD = width < 0 ? SW : width;
   for (int r0 = 0; r0 < SH; r0 += 8 * NR) {
     T v[NR][2];
 #pragma unroll
@@ -161,18 +168,18 @@ __device__ __forceinline__ void stage_window(T *xs, int SW, int SH, int tx, int 
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int r = r0 + ty + 8 * i, c = tx + 32 * q;
-        v[i][q] = (r < SH && c < SW) ? load(r, c) : T(0);
+        v[i][q] = (r < SH && c < WD) ? load(r, c) : T(0);
       }
 #pragma unroll
     for (int i = 0; i < NR; ++i)
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int r = r0 + ty + 8 * i, c = tx + 32 * q;
-        if (r < SH && c < SW) xs[r * SW + c] = v[i][q];
+        if (r < SH && c < WD) xs[r * SW + c] = v[i][q];
       }
   }
   for (int r = ty; r < SH; r += 8)
-    for (int c = tx + 64; c < SW; c += 32) xs[r * SW + c] = load(r, c);
+    for (int c = tx + 64; c < WD; c += 32) xs[r * SW + c] = load(r, c);
 }
 
 template <typename T> struct ClassTap;

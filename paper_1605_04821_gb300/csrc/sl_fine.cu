@@ -1,7 +1,10 @@
 // sl_fine.cu - fine-level kernels: source tables, policy improvement, matrix-free operator,
 // FP64 HJB residual and grid transfers.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstdint>
+#include <type_traits>
 
 #include "sl_launch.h"
 
@@ -204,12 +207,12 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
       const float xd = float((in ? a.X[size_t(g2) * n + g1] : 0.0) - xc);
       if (in) dmax = fmaxf(dmax, fabsf(xd));
       return xd;
-    });
+    }, 32 + 2 * a.halo);
   } else {
     stage_window<4, double>(xs64, a.SW, a.SH, threadIdx.x, threadIdx.y, [&](int r, int cc) {
       const int g2 = o2 + r, g1 = o1 + cc;
       return (g1 >= 0 && g1 < n && g2 >= 0 && g2 < n) ? a.X[size_t(g2) * n + g1] : 0.0;
-    });
+    }, 32 + 2 * a.halo);
   }
   if (SCREEN) {
     for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -434,17 +437,18 @@ __device__ __forceinline__ void fine_finish(T *y, const T *b, int j, T xj, T ax,
 
 // Stages rows [o2, o2 + SH) x columns [o1, o1 + SW) of a full-grid vector into shared memory,
 // with zeros outside the grid; tiles whose halo lies inside the grid skip the bounds checks.
+// SW is the pitch of xs; WD columns are staged.
 template <typename T>
 __device__ __forceinline__ void stage_tile(T *xs, const T *__restrict__ x, int n, int o1, int o2, int SW,
-                                           int SH, int tx, int ty) {
-  if (o1 >= 0 && o2 >= 0 && o1 + SW <= n && o2 + SH <= n) {
+                                           int WD, int SH, int tx, int ty) {
+  if (o1 >= 0 && o2 >= 0 && o1 + WD <= n && o2 + SH <= n) {
     const T *src = x + size_t(o2) * n + o1;
-    stage_window<4, T>(xs, SW, SH, tx, ty, [&](int r, int c) { return src[size_t(r) * n + c]; });
+    stage_window<4, T>(xs, SW, SH, tx, ty, [&](int r, int c) { return src[size_t(r) * n + c]; }, WD);
   } else {
     stage_window<4, T>(xs, SW, SH, tx, ty, [&](int r, int c) {
       const int g2 = o2 + r, g1 = o1 + c;
       return (g2 >= 0 && g2 < n && g1 >= 0 && g1 < n) ? x[size_t(g2) * n + g1] : T(0);
-    });
+    }, WD);
   }
 }
 
@@ -481,37 +485,26 @@ template <int TMAX> struct InnerTaps<double, TMAX> {
   static __device__ __forceinline__ double od(const FineTab &tab, int k) { return tab.iod64[k]; }
 };
 
-template <typename T, int OP, int TMAX, int RPT = kFineRPT>
-__global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__restrict__ policy, T dt, T omega,
-                                                 const T *__restrict__ x, const T *__restrict__ b,
-                                                 T *__restrict__ y, int halo, int SW) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *xs = reinterpret_cast<T *>(smem_raw);
+// The rows of tile (bx, by) (32 columns x 8 RPT rows) from the staged tile xs (pitch SW; the
+// tile's column 0 is grid column 1 + 32 bx - halo); kr: the rows' controls.  Every fine
+// operator kernel calls this, so all of them compute each row the same way.
+template <typename T, int OP, int TMAX, int RPT>
+__device__ __forceinline__ void fine_tile_rows(const FineTab &tab, T dt, T omega, const T *xs,
+                                               const T *__restrict__ b, T *__restrict__ y, int halo,
+                                               int SW, int bx, int by, const int (&kr)[RPT]) {
   const int n = tab.n, m = tab.m;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i1 = 1 + blockIdx.x * 32 + tx;
-  // the rows' controls are read before the tile is staged, so that both loads are in flight
-  int kr[RPT];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    const int i2 = 1 + blockIdx.y * (8 * RPT) + ty + 8 * r;
-    kr[r] = i1 <= m && i2 <= m ? int(policy[(i2 - 1) * m + (i1 - 1)]) : 0;
-  }
-  if (OP != OP_JACOBI0) {
-    stage_tile<T>(xs, x, n, 1 + blockIdx.x * 32 - halo, 1 + blockIdx.y * (8 * RPT) - halo, SW,
-                  (8 * RPT) + 2 * halo, tx, ty);
-    __syncthreads();
-  }
+  const int i1 = 1 + bx * 32 + tx;
   if (i1 > m) return;
   // a block whose rows all lie in the interior class (q1 = q2 = B) reads the tap-major
   // interior table, indexed by the control alone
   const int B = tab.B;
-  const int r1 = blockIdx.x * 32, r2 = blockIdx.y * (8 * RPT);
+  const int r1 = bx * 32, r2 = by * (8 * RPT);
   const bool inner = TMAX > 0 && tab.ipk32 != nullptr && !tab.general && n - 1 >= 2 * B &&
                      1 + r1 >= B && r1 + 32 <= n - 1 - B && 1 + r2 >= B && r2 + 8 * RPT <= n - 1 - B;
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const int i2 = 1 + blockIdx.y * (8 * RPT) + ty + 8 * r;
+    const int i2 = 1 + by * (8 * RPT) + ty + 8 * r;
     if (i2 > m) continue;
     const int k = kr[r];
     const int j = i2 * n + i1;
@@ -558,9 +551,225 @@ __global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__r
   }
 }
 
+
+template <typename T, int OP, int TMAX, int RPT = kFineRPT>
+__global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__restrict__ policy, T dt, T omega,
+                                                 const T *__restrict__ x, const T *__restrict__ b,
+                                                 T *__restrict__ y, int halo, int SW) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  const int n = tab.n, m = tab.m;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i1 = 1 + blockIdx.x * 32 + tx;
+  // the rows' controls are read before the tile is staged, so that both loads are in flight
+  int kr[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int i2 = 1 + blockIdx.y * (8 * RPT) + ty + 8 * r;
+    kr[r] = i1 <= m && i2 <= m ? int(policy[(i2 - 1) * m + (i1 - 1)]) : 0;
+  }
+  if (OP != OP_JACOBI0) {
+    stage_tile<T>(xs, x, n, 1 + blockIdx.x * 32 - halo, 1 + blockIdx.y * (8 * RPT) - halo, SW,
+                  32 + 2 * halo, (8 * RPT) + 2 * halo, tx, ty);
+    __syncthreads();
+  }
+  fine_tile_rows<T, OP, TMAX, RPT>(tab, dt, omega, xs, b, y, halo, SW, blockIdx.x, blockIdx.y, kr);
+}
+
+// ----------------------------------------------------------------------------- TMA fine operator
+// The FP32 fine operator (apply, residual, Jacobi sweep) as a persistent kernel whose tiles are
+// moved by the TMA unit.  Each block walks the 32 x 32-row tiles t = blockIdx.x, + gridDim.x,
+// ...; while it computes one tile, the rows of its next interior tile are in flight into the
+// other of two shared buffers, one cp.async.bulk global -> shared copy per tile row, completing
+// on that buffer's mbarrier.  A bulk copy needs 16-byte-aligned addresses and a length that is
+// a multiple of 16 bytes; a grid row of n = 2^j + 1 values is not, so each row is copied from
+// its 16-byte-aligned start with its length rounded up, and the tile pitch SW is congruent to n
+// mod 4 (and at least 3 columns wider than the 32 + 2 halo staged ones) so that every row keeps
+// the same offset a0 (0..3 values) inside its 16 bytes in shared memory as in global memory;
+// the tile then starts at buffer + a0.  The extra values at both ends of a row land in columns
+// the taps never read.  Tiles at the boundary, whose halo leaves the grid, are staged by the
+// threads with zeros outside the grid, as in k_fine_op.  A wait that does not complete within
+// kTmaSpin polls sets *err (reported by the solver as SL_ETIMEOUT) and the tile is computed
+// from whatever arrived; no wait is unbounded.
+constexpr unsigned kTmaSpin = 1u << 20;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
+                                              unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// orders this thread's earlier generic shared accesses before later async-proxy (TMA) ones
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+struct TmaTiles {
+  int tiles_x, ntiles;  // tiles per grid row, total
+  int buf_floats;       // floats per shared buffer (multiple of 32)
+  int *err;             // set to 1 when a wait gave up
+};
+
+// Issues (warp 0) the bulk copies of the interior tile with origin (o1, o2) into bf; one copy
+// per row, all completing on bar, whose expected byte count lane 0 raises first.
+__device__ __forceinline__ void tma_issue_tile(const float *__restrict__ x, int n, int o1, int o2, int WD,
+                                               int SH, int SW, float *bf, unsigned long long *bar) {
+  const int lane = threadIdx.x;
+  unsigned bytes = 0;
+  for (int r = lane; r < SH; r += 32) {
+    const int ar = int((size_t(o2 + r) * n + o1) & 3);
+    bytes += unsigned(((ar + WD + 3) & ~3) * 4);
+  }
+  for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+  if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
+  __syncwarp();
+  const int a0 = int((size_t(o2) * n + o1) & 3);
+  for (int r = lane; r < SH; r += 32) {
+    const size_t g = size_t(o2 + r) * n + o1;
+    const int ar = int(g & 3);
+    bulk_copy_g2s(bf + (a0 + r * SW - ar), x + (g - ar), unsigned(((ar + WD + 3) & ~3) * 4), bar);
+  }
+}
+
+template <int OP, int TMAX>
+__global__ void __launch_bounds__(256) k_fine_op_tma(FineTab tab, const uint8_t *__restrict__ policy, float dt,
+                                                     float omega, const float *__restrict__ x,
+                                                     const float *__restrict__ b, float *__restrict__ y,
+                                                     int halo, int SW, TmaTiles tt) {
+  constexpr int RPT = kFineRPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  float *buf[2] = {reinterpret_cast<float *>(smem_raw), reinterpret_cast<float *>(smem_raw) + tt.buf_floats};
+  const int n = tab.n, m = tab.m;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int WD = 32 + 2 * halo, SH = 8 * RPT + 2 * halo;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto origin = [&](int t, int &o1, int &o2) {
+    o1 = 1 + (t % tt.tiles_x) * 32 - halo;
+    o2 = 1 + (t / tt.tiles_x) * (8 * RPT) - halo;
+  };
+  // the row copies stay inside the array: 3 values of rounding at either end of each row
+  // (and a bulk copy needs a 16-byte-aligned shared address: otherwise every tile is staged
+  // by the threads)
+  const bool smem16 = (smem_addr(smem_raw) & 15u) == 0u;
+  auto interior = [&](int o1, int o2) {
+    return smem16 && o1 >= 3 && o2 >= 0 && o1 + WD + 3 <= n && o2 + SH <= n;
+  };
+  unsigned parity[2] = {0u, 0u};
+  int cur = 0;
+  int t = blockIdx.x;
+  if (t < tt.ntiles && ty == 0) {
+    int o1, o2;
+    origin(t, o1, o2);
+    if (interior(o1, o2)) tma_issue_tile(x, n, o1, o2, WD, SH, SW, buf[0], &bar[0]);
+  }
+  bool failed = false;
+  for (; t < tt.ntiles; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    // prefetch the next tile into the other buffer (its readers finished before the last
+    // __syncthreads of the previous iteration)
+    if (tn < tt.ntiles && ty == 0) {
+      int p1, p2;
+      origin(tn, p1, p2);
+      if (interior(p1, p2)) {
+        fence_proxy_async_smem();
+        tma_issue_tile(x, n, p1, p2, WD, SH, SW, buf[cur ^ 1], &bar[cur ^ 1]);
+      }
+    }
+    const int bx = t % tt.tiles_x, by = t / tt.tiles_x;
+    const int i1 = 1 + bx * 32 + tx;
+    int kr[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int i2 = 1 + by * (8 * RPT) + ty + 8 * r;
+      kr[r] = i1 <= m && i2 <= m ? int(policy[(i2 - 1) * m + (i1 - 1)]) : 0;
+    }
+    int o1, o2;
+    origin(t, o1, o2);
+    const float *xs;
+    if (interior(o1, o2)) {
+      unsigned spins = 0;
+      while (!mbar_try_wait(&bar[cur], parity[cur])) {
+        if (++spins >= kTmaSpin) {
+          failed = true;
+          break;
+        }
+      }
+      parity[cur] ^= 1u;
+      xs = buf[cur] + int((size_t(o2) * n + o1) & 3);
+    } else {
+      stage_tile<float>(buf[cur], x, n, o1, o2, SW, WD, SH, tx, ty);
+      __syncthreads();
+      xs = buf[cur];
+    }
+    fine_tile_rows<float, OP, TMAX, RPT>(tab, dt, omega, xs, b, y, halo, SW, bx, by, kr);
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (failed) atomicExch(tt.err, 1);
+}
+
+// The TMA kernel for the FP32 ops that stage x, on the common tap stride 12, when x is
+// 16-byte aligned and the grid has interior tiles; false: the caller launches k_fine_op.
+template <typename T, int OP>
+bool fine_op_tma(const FineTab &tab, const uint8_t *policy, T dt, T omega, const T *x, const T *b, T *y,
+                 int halo, int SW, cudaStream_t s) {
+  if constexpr (!std::is_same<T, float>::value || OP == OP_JACOBI0) {
+    return false;
+  } else {
+    if (!tab.tma || !tab.tma_err || tab.tmax != 12 || (reinterpret_cast<uintptr_t>(x) & 15) != 0 ||
+        tab.n < 64 + 2 * halo + 8)
+      return false;
+    TmaTiles tt{};
+    tt.tiles_x = (tab.m + 31) / 32;
+    tt.ntiles = tt.tiles_x * ((tab.m + 8 * kFineRPT - 1) / (8 * kFineRPT));
+    const int SH = 8 * kFineRPT + 2 * halo;
+    tt.buf_floats = (SW * SH + 8 + 31) / 32 * 32;
+    tt.err = tab.tma_err;
+    const size_t bytes = 2 * size_t(tt.buf_floats) * sizeof(float);
+    // persistent: four blocks per SM of the 152, or one per tile when there are fewer
+    const int grid = std::min(tt.ntiles, 4 * 152);
+    note_launch();
+    k_fine_op_tma<OP, 12><<<grid, dim3(32, 8), bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, tt);
+    return true;
+  }
+}
+
 template <typename T, int OP>
 void fine_op_dispatch(const FineTab &tab, const uint8_t *policy, T dt, T omega, const T *x, const T *b,
                       T *y, int halo, int SW, cudaStream_t s) {
+  if (fine_op_tma<T, OP>(tab, policy, dt, omega, x, b, y, halo, SW, s)) return;
   dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + 8 * kFineRPT - 1) / (8 * kFineRPT));
   const size_t bytes = OP == OP_JACOBI0 ? 0 : size_t(SW) * (8 * kFineRPT + 2 * halo) * sizeof(T);
   note_launch();
@@ -653,7 +862,7 @@ __global__ void __launch_bounds__(256) k_hjb_resid(FineTab tab, const uint8_t *_
     stage_window<4, double>(xs, SW, SH, tx, ty, [&](int rr, int cc) {
       const int g2 = o2 + rr, g1 = o1 + cc;
       return (g2 >= 0 && g2 < n && g1 >= 0 && g1 < n) ? X[size_t(g2) * n + g1] - xc : 0.0;
-    });
+    }, 32 + 2 * halo);
   }
   __syncthreads();
   if (i1 > m) return;
@@ -774,6 +983,13 @@ cudaError_t prepare_fine_kernels() {
                       reinterpret_cast<const void *>(k_argmin<1, 20>),
                       reinterpret_cast<const void *>(k_argmin<1, 0>)};
   for (const void *f : fs) {
+    cudaError_t e = allow_dynamic_smem(f);
+    if (e != cudaSuccess) return e;
+  }
+  const void *tma[] = {reinterpret_cast<const void *>(k_fine_op_tma<OP_APPLY, 12>),
+                       reinterpret_cast<const void *>(k_fine_op_tma<OP_RESID, 12>),
+                       reinterpret_cast<const void *>(k_fine_op_tma<OP_JACOBI, 12>)};
+  for (const void *f : tma) {
     cudaError_t e = allow_dynamic_smem(f);
     if (e != cudaSuccess) return e;
   }

@@ -247,6 +247,7 @@ struct DevCtl {
   // counts, accumulated until the host clears them
   long long c_steps, c_improve0, c_pibody, c_pi, c_rebuild, c_ir, c_enter, c_kry, c_ok, c_changes;
   int nexpl[16];         // explicit rows of each level after the last rebuild in the graph
+  int tma_err;           // a bounded wait of the TMA fine operator gave up (FineTab::tma_err)
 };
 
 // Explicit-row counts of the coarse levels, gathered into DevCtl::nexpl (levels 1 .. L-1).
