@@ -169,11 +169,13 @@ typedef struct {
                            solve.  The V-cycle entry points and sl_hjb_adjoint need precond 0. */
   int amg_k_levels;     /* precond 1: coarse levels 1..amg_k_levels take two GCR steps, deeper
                            levels one */
-  int fine_tma;         /* 1: the FP32 fine-level operator (apply, residual, Jacobi sweep) runs as
-                           a persistent kernel whose interior tiles are copied into shared memory
-                           by the TMA unit (cp.async.bulk, double-buffered: the next tile is in
-                           flight while the current one is computed); 0: the threads stage every
-                           tile.  Same arithmetic per row, same result bit for bit. */
+  int fine_tma;         /* staging of the FP32 fine-level operator's tiles (apply, residual, Jacobi
+                           sweep; tap stride 12): 1 (default): the interior tiles' rows are copied
+                           into shared memory by the TMA unit (cp.async.bulk completing on an
+                           mbarrier), one tile per block; 2: a persistent kernel that keeps the
+                           next tile's copies in flight while it computes the current one (two
+                           buffers); 0: the threads stage every tile.  All three compute each row
+                           the same way and give the same result bit for bit. */
 } sl_opts;
 
 typedef struct {

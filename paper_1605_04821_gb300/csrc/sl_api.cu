@@ -1895,7 +1895,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   AL(h->d_flags, 1);
   AL(h->d_count, 1);
   AL(h->ctl, 1);
-  h->tab.tma = (h->o.fine_tma && !h->general) ? 1 : 0;
+  h->tab.tma = h->general ? 0 : std::max(0, std::min(2, h->o.fine_tma));
   h->tab.tma_err = &h->ctl->tma_err;
   CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_ctl), sizeof(DevCtl)));
   std::memset(h->h_ctl, 0, sizeof(DevCtl));

@@ -742,6 +742,59 @@ __global__ void __launch_bounds__(256) k_fine_op_tma(FineTab tab, const uint8_t 
 
 // The TMA kernel for the FP32 ops that stage x, on the common tap stride 12, when x is
 // 16-byte aligned and the grid has interior tiles; false: the caller launches k_fine_op.
+// One tile per block, as k_fine_op, with the interior tile's rows copied by the TMA unit
+// instead of the threads (warp 0 issues them; every thread loads its rows' controls meanwhile).
+template <int OP, int TMAX>
+__global__ void __launch_bounds__(256) k_fine_op_tma1(FineTab tab, const uint8_t *__restrict__ policy,
+                                                      float dt, float omega, const float *__restrict__ x,
+                                                      const float *__restrict__ b, float *__restrict__ y,
+                                                      int halo, int SW, TmaTiles tt) {
+  constexpr int RPT = kFineRPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar;
+  float *buf = reinterpret_cast<float *>(smem_raw);
+  const int n = tab.n, m = tab.m;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int WD = 32 + 2 * halo, SH = 8 * RPT + 2 * halo;
+  const int o1 = 1 + blockIdx.x * 32 - halo, o2 = 1 + blockIdx.y * (8 * RPT) - halo;
+  const bool tma = (smem_addr(smem_raw) & 15u) == 0u && o1 >= 3 && o2 >= 0 && o1 + WD + 3 <= n && o2 + SH <= n;
+  if (tma) {
+    if (ty == 0) {
+      if (tx == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+      }
+      __syncwarp();
+      tma_issue_tile(x, n, o1, o2, WD, SH, SW, buf, &bar);
+    }
+  }
+  const int i1 = 1 + blockIdx.x * 32 + tx;
+  int kr[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int i2 = 1 + blockIdx.y * (8 * RPT) + ty + 8 * r;
+    kr[r] = i1 <= m && i2 <= m ? int(policy[(i2 - 1) * m + (i1 - 1)]) : 0;
+  }
+  const float *xs = buf;
+  if (tma) {
+    __syncthreads();  // the barrier is initialised before anyone polls it
+    unsigned spins = 0;
+    bool failed = false;
+    while (!mbar_try_wait(&bar, 0u)) {
+      if (++spins >= kTmaSpin) {
+        failed = true;
+        break;
+      }
+    }
+    if (failed && tx == 0 && ty == 0) atomicExch(tt.err, 1);
+    xs = buf + int((size_t(o2) * n + o1) & 3);
+  } else {
+    stage_tile<float>(buf, x, n, o1, o2, SW, WD, SH, tx, ty);
+    __syncthreads();
+  }
+  fine_tile_rows<float, OP, TMAX, RPT>(tab, dt, omega, xs, b, y, halo, SW, blockIdx.x, blockIdx.y, kr);
+}
+
 template <typename T, int OP>
 bool fine_op_tma(const FineTab &tab, const uint8_t *policy, T dt, T omega, const T *x, const T *b, T *y,
                  int halo, int SW, cudaStream_t s) {
@@ -757,11 +810,17 @@ bool fine_op_tma(const FineTab &tab, const uint8_t *policy, T dt, T omega, const
     const int SH = 8 * kFineRPT + 2 * halo;
     tt.buf_floats = (SW * SH + 8 + 31) / 32 * 32;
     tt.err = tab.tma_err;
-    const size_t bytes = 2 * size_t(tt.buf_floats) * sizeof(float);
-    // persistent: four blocks per SM of the 152, or one per tile when there are fewer
-    const int grid = std::min(tt.ntiles, 4 * 152);
     note_launch();
-    k_fine_op_tma<OP, 12><<<grid, dim3(32, 8), bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, tt);
+    if (tab.tma == 2) {
+      // persistent: four blocks per SM of the 152, or one per tile when there are fewer
+      const size_t bytes = 2 * size_t(tt.buf_floats) * sizeof(float);
+      const int grid = std::min(tt.ntiles, 4 * 152);
+      k_fine_op_tma<OP, 12><<<grid, dim3(32, 8), bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, tt);
+    } else {
+      const size_t bytes = size_t(tt.buf_floats) * sizeof(float);
+      dim3 grd(tt.tiles_x, tt.ntiles / tt.tiles_x);
+      k_fine_op_tma1<OP, 12><<<grd, dim3(32, 8), bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, tt);
+    }
     return true;
   }
 }
@@ -988,7 +1047,10 @@ cudaError_t prepare_fine_kernels() {
   }
   const void *tma[] = {reinterpret_cast<const void *>(k_fine_op_tma<OP_APPLY, 12>),
                        reinterpret_cast<const void *>(k_fine_op_tma<OP_RESID, 12>),
-                       reinterpret_cast<const void *>(k_fine_op_tma<OP_JACOBI, 12>)};
+                       reinterpret_cast<const void *>(k_fine_op_tma<OP_JACOBI, 12>),
+                       reinterpret_cast<const void *>(k_fine_op_tma1<OP_APPLY, 12>),
+                       reinterpret_cast<const void *>(k_fine_op_tma1<OP_RESID, 12>),
+                       reinterpret_cast<const void *>(k_fine_op_tma1<OP_JACOBI, 12>)};
   for (const void *f : tma) {
     cudaError_t e = allow_dynamic_smem(f);
     if (e != cudaSuccess) return e;
