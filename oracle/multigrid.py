@@ -9,6 +9,13 @@ A_{l+1} = R A_l P.  Restriction is full weighting, R = P^T / 4; the precondition
 P (R A P)^{-1} R does not depend on the scale of R, so this is the paper's R = P^T up to a
 factor.  The smoother is damped Jacobi x <- x + omega D^{-1} (b - A x), and the coarsest
 level is solved directly.  Grid and algebraic complexities follow Definitions 3.1 and 3.2.
+
+The paper's geometric multigrid smooths with Gauss-Seidel (Section 3.3).  Its data-parallel
+form here is the two-colour (red-black) Gauss-Seidel sweep: the interior nodes with i1 + i2
+even, then those with i1 + i2 odd, each colour updated at once from the current values of all
+nodes, x_c <- x_c + omega D_c^{-1} (b - A x)_c.  For the 5-point Laplacian, whose nodes of one
+colour do not couple, this is Gauss-Seidel in red-black order exactly; the wide LISL stencils
+couple nodes of one colour too, which the simultaneous update of a colour treats as Jacobi does.
 """
 from __future__ import annotations
 
@@ -85,17 +92,43 @@ def jacobi(A, b, x, omega, sweeps):
     return x
 
 
+def colours(n: int) -> np.ndarray:
+    """(i1 + i2) mod 2 of the interior nodes of an n x n grid, in the unknowns' row-major order."""
+    i2, i1 = np.meshgrid(np.arange(1, n - 1), np.arange(1, n - 1), indexing="ij")
+    return ((i1 + i2) % 2).ravel()
+
+
+def rbgs(A, b, x, omega, sweeps, n):
+    """Two-colour Gauss-Seidel sweeps: colour 0 (i1 + i2 even), then colour 1, each updated at once."""
+    d = A.diagonal()
+    col = colours(n)
+    for _ in range(sweeps):
+        for c in (0, 1):
+            sel = col == c
+            r = b - A @ x
+            x = x.copy()
+            x[sel] += omega * r[sel] / d[sel]
+    return x
+
+
 def vcycle(H: Hierarchy, b: np.ndarray, nu1: int = 2, nu2: int = 2, omega: float = 0.8,
-           level: int = 0) -> np.ndarray:
-    """One V(nu1, nu2) cycle for A_level x = b from x = 0; exact solve on the coarsest level."""
+           level: int = 0, smoother: str = "jacobi") -> np.ndarray:
+    """One V(nu1, nu2) cycle for A_level x = b from x = 0; exact solve on the coarsest level.
+    smoother: "jacobi" (damped Jacobi) or "rbgs" (two-colour Gauss-Seidel, relaxation omega)."""
     A = H.A[level]
     if level == len(H.A) - 1:
         return spla.spsolve(A.tocsc(), b)
-    x = jacobi(A, b, np.zeros_like(b), omega, nu1)
+
+    def smooth(x, sweeps):
+        if smoother == "rbgs":
+            return rbgs(A, b, x, omega, sweeps, H.n[level])
+        return jacobi(A, b, x, omega, sweeps)
+
+    x = smooth(np.zeros_like(b), nu1)
     r = b - A @ x
-    ec = vcycle(H, H.R[level] @ r, nu1, nu2, omega, level + 1)
+    ec = vcycle(H, H.R[level] @ r, nu1, nu2, omega, level + 1, smoother)
     x = x + H.P[level] @ ec
-    return jacobi(A, b, x, omega, nu2)
+    return smooth(x, nu2)
 
 
 def complexities(H: Hierarchy):
