@@ -169,6 +169,15 @@ typedef struct {
                            solve.  The V-cycle entry points and sl_hjb_adjoint need precond 0. */
   int amg_k_levels;     /* precond 1: coarse levels 1..amg_k_levels take two GCR steps, deeper
                            levels one */
+  int smoother;         /* smoother of the geometric V-cycle (nu1 / nu2 sweeps, relaxation weight
+                           omega): 0 damped Jacobi; 1 two-colour (red-black) Gauss-Seidel, the
+                           data-parallel form of the paper's Gauss-Seidel smoother (Section 3.3):
+                           the nodes with i1 + i2 even, then the odd ones, each colour updated at
+                           once from the current values of all nodes.  The wide stencils couple
+                           nodes of one colour, which a colour's simultaneous update treats as
+                           Jacobi does; for grid-aligned stencils of even reach all couplings are
+                           within a colour (see the design notes), and omega = 1 can then diverge.
+                           The aggregation K-cycle and the adjoint's transposed cycle use Jacobi. */
   int fine_tma;         /* staging of the FP32 fine-level operator's tiles (apply, residual, Jacobi
                            sweep; tap stride 12): 1 (default): the interior tiles' rows are copied
                            into shared memory by the TMA unit (cp.async.bulk completing on an
@@ -195,7 +204,7 @@ typedef struct {
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
  * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
- * extrapolate 1, precond 0, amg_k_levels 2, fine_tma 1. */
+ * extrapolate 1, precond 0, amg_k_levels 2, smoother 0, fine_tma 1. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every

@@ -536,7 +536,8 @@ CsrTView<T> csrT_view(sl_hjb *h) {
 }
 
 template <typename T>
-void level_op(sl_hjb *h, int l, int op, double dt, const T *x, const T *b, T *y, cudaStream_t s) {
+void level_op(sl_hjb *h, int l, int op, double dt, const T *x, const T *b, T *y, cudaStream_t s,
+              int color = -1) {
   if (h->transposed) {
     if (l == 0)
       launch_fineT_op<T>(op, csrT_view<T>(h), T(h->o.omega), x, b, y, s);
@@ -546,9 +547,38 @@ void level_op(sl_hjb *h, int l, int op, double dt, const T *x, const T *b, T *y,
     return;
   }
   if (l == 0)
-    launch_fine_op<T>(op, h->tab, h->d_slin, h->policy, T(dt), T(h->o.omega), x, b, y, h->halo, h->SW, s);
+    launch_fine_op<T>(op, h->tab, h->d_slin, h->policy, T(dt), T(h->o.omega), x, b, y, h->halo, h->SW, s,
+                      color);
   else
-    launch_coarse_op<T>(op, lev_view<T>(h, l), h->cl[l].d_nexpl, T(h->o.omega), x, b, y, s);
+    launch_coarse_op<T>(op, lev_view<T>(h, l), h->cl[l].d_nexpl, T(h->o.omega), x, b, y, s, color);
+}
+
+// `sweeps` sweeps of the level-l smoother on A_l x = b, ping-ponging between cur and other
+// (from_zero: the first sweep starts at x = 0 and writes cur).  Damped Jacobi, or with
+// smoother 1 the two-colour Gauss-Seidel sweep (Section 3.3's Gauss-Seidel in data-parallel
+// form): rows with i1 + i2 even, then odd, each half updated from the current values.  The
+// transposed solves of the adjoint smooth with Jacobi.
+template <typename T>
+void smooth(sl_hjb *h, int l, double dt, const T *b, T *&cur, T *&other, int sweeps, bool from_zero,
+            cudaStream_t s) {
+  const bool gs = h->o.smoother == 1 && !h->transposed;
+  for (int it = 0; it < sweeps; ++it) {
+    if (gs) {
+      for (int c = 0; c < 2; ++c) {
+        if (from_zero && it == 0 && c == 0) {
+          level_op<T>(h, l, OP_JACOBI0, dt, nullptr, b, cur, s, 0);
+        } else {
+          level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s, c);
+          std::swap(cur, other);
+        }
+      }
+    } else if (from_zero && it == 0) {
+      level_op<T>(h, l, OP_JACOBI0, dt, nullptr, b, cur, s);
+    } else {
+      level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s);
+      std::swap(cur, other);
+    }
+  }
 }
 
 template <typename T>
@@ -573,6 +603,7 @@ sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) 
     a.L = h->L;
     a.nu1 = h->o.nu1;
     a.nu2 = h->o.nu2;
+    a.rbgs = h->o.smoother == 1 ? 1 : 0;
     a.omega = T(h->o.omega);
     for (int q = l; q < h->L; ++q) {
       a.lev[q] = lev_view<T>(h, q);
@@ -591,15 +622,8 @@ sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) 
   T *bx, *bt, *br, *bb;
   vbufs<T>(h->vb[l], &bx, &bt, &br, &bb);
   T *cur = x, *other = bt;
-  if (h->o.nu1 == 0) {
-    launch_fill<T>(x, N, T(0), s);
-  } else {
-    level_op<T>(h, l, OP_JACOBI0, dt, nullptr, b, cur, s);
-    for (int it = 1; it < h->o.nu1; ++it) {
-      level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s);
-      std::swap(cur, other);
-    }
-  }
+  if (h->o.nu1 == 0) launch_fill<T>(x, N, T(0), s);
+  else smooth<T>(h, l, dt, b, cur, other, h->o.nu1, true, s);
   level_op<T>(h, l, OP_RESID, dt, cur, b, br, s);
   T *cx, *ct, *cr, *cb;
   vbufs<T>(h->vb[l + 1], &cx, &ct, &cr, &cb);
@@ -607,10 +631,7 @@ sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) 
   sl_status st = vcycle<T>(h, l + 1, dt, cb, cx, s);
   if (st != SL_OK) return st;
   launch_prolong_add<T>(cx, h->cl[l + 1].n, cur, h->cl[l].n, s);
-  for (int it = 0; it < h->o.nu2; ++it) {
-    level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s);
-    std::swap(cur, other);
-  }
+  smooth<T>(h, l, dt, b, cur, other, h->o.nu2, false, s);
   if (cur != x) CK(cudaMemcpyAsync(x, cur, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CK(cudaGetLastError());
   return SL_OK;
@@ -1479,24 +1500,14 @@ sl_status vcycle_into(sl_hjb *h, int l, double dt, const T *b, T *x, T *const *t
     return SL_OK;
   }
   T *cur = x, *other = t[l];
-  if (h->o.nu1 == 0) {
-    launch_fill<T>(x, N, T(0), s);
-  } else {
-    level_op<T>(h, l, OP_JACOBI0, dt, nullptr, b, cur, s);
-    for (int it = 1; it < h->o.nu1; ++it) {
-      level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s);
-      std::swap(cur, other);
-    }
-  }
+  if (h->o.nu1 == 0) launch_fill<T>(x, N, T(0), s);
+  else smooth<T>(h, l, dt, b, cur, other, h->o.nu1, true, s);
   level_op<T>(h, l, OP_RESID, dt, cur, b, r[l], s);
   launch_restrict<T>(r[l], h->cl[l].n, cb[l + 1], h->cl[l + 1].n, s);
   sl_status st = vcycle_into<T>(h, l + 1, dt, cb[l + 1], cx[l + 1], t, r, cb, cx, s);
   if (st != SL_OK) return st;
   launch_prolong_add<T>(cx[l + 1], h->cl[l + 1].n, cur, h->cl[l].n, s);
-  for (int it = 0; it < h->o.nu2; ++it) {
-    level_op<T>(h, l, OP_JACOBI, dt, cur, b, other, s);
-    std::swap(cur, other);
-  }
+  smooth<T>(h, l, dt, b, cur, other, h->o.nu2, false, s);
   if (cur != x) CK(cudaMemcpyAsync(x, cur, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CK(cudaGetLastError());
   return SL_OK;
@@ -1570,6 +1581,7 @@ void sl_opts_default(sl_opts *o) {
   o->precond = 0;
   o->amg_k_levels = 2;
   o->fine_tma = 1;
+  o->smoother = 0;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -1617,6 +1629,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   if (h->o.nu1 < 0 || h->o.nu2 < 0 || h->o.kry_max < 1 || h->o.pi_max < 1 || !(h->o.omega > 0))
     return fail(h, SL_EINVAL, "bad iteration options");
   if (h->o.precond != 0 && h->o.precond != 1) return fail(h, SL_EINVAL, "precond must be 0 or 1");
+  if (h->o.smoother != 0 && h->o.smoother != 1) return fail(h, SL_EINVAL, "smoother must be 0 or 1");
   if (h->o.precond == 1 && (h->o.nu1 < 1 || h->o.amg_k_levels < 0))
     return fail(h, SL_EINVAL, "the aggregation K-cycle needs nu1 >= 1 and amg_k_levels >= 0");
   h->amg.nu1 = h->o.nu1;

@@ -266,7 +266,11 @@ __device__ __forceinline__ void coarse_finish(T *y, const T *x, const T *b, int 
 template <typename T, int OP>
 __device__ __forceinline__ void coarse_class_row(const CoarseLev<T> &L, int k, int j, T omega,
                                                  const T *__restrict__ x, const T *__restrict__ b,
-                                                 T *__restrict__ y) {
+                                                 T *__restrict__ y, int color = -1) {
+  if ((OP == OP_JACOBI || OP == OP_JACOBI0) && color >= 0 && (((j % L.n) + (j / L.n)) & 1) != color) {
+    y[j] = OP == OP_JACOBI ? x[j] : T(0);
+    return;
+  }
   const T d = L.cdiag[k];
   if (OP == OP_JACOBI0) {
     y[j] = omega * b[j] / d;
@@ -327,9 +331,13 @@ __device__ __forceinline__ T expl_window_sum_any(const CoarseLev<T> &L, int slot
 template <typename T, int OP>
 __device__ __forceinline__ void coarse_expl_row(const CoarseLev<T> &L, int slot, T omega,
                                                 const T *__restrict__ x, const T *__restrict__ b,
-                                                T *__restrict__ y) {
+                                                T *__restrict__ y, int color = -1) {
   const int j = L.erow[slot];
   const int I1 = j % L.n, I2 = j / L.n;
+  if ((OP == OP_JACOBI || OP == OP_JACOBI0) && color >= 0 && ((I1 + I2) & 1) != color) {
+    y[j] = OP == OP_JACOBI ? x[j] : T(0);
+    return;
+  }
   const int R = L.R, Wd = 2 * R + 1;
   const T d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
   if (OP == OP_JACOBI0) {
@@ -361,7 +369,7 @@ __host__ __device__ inline size_t coarse_tile_bytes(int R) {
 template <typename T, int OP, int STAB>
 __global__ void __launch_bounds__(256, 6) k_coarse_op(CoarseLev<T> L, const int *__restrict__ nexpl_dev,
                                                    int tiles_x, int tiles, T omega, const T *__restrict__ x,
-                                                   const T *__restrict__ b, T *__restrict__ y) {
+                                                   const T *__restrict__ b, T *__restrict__ y, int color) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (int(blockIdx.x) < tiles) {
     using PK = typename ClassTap<T>::Packed;
@@ -404,12 +412,16 @@ __global__ void __launch_bounds__(256, 6) k_coarse_op(CoarseLev<T> L, const int 
       const int k = L.cls[(I2 - 1) * L.m + (I1 - 1)];
       if (k < 0) continue;
       const int j = I2 * L.n + I1;
+      const int sidx = (ty + 8 * r + R) * SW + tx + R;
+      if ((OP == OP_JACOBI || OP == OP_JACOBI0) && color >= 0 && ((I1 + I2) & 1) != color) {
+        y[j] = OP == OP_JACOBI ? xs[sidx] : T(0);
+        continue;
+      }
       const T d = L.cdiag[k];
       if (OP == OP_JACOBI0) {
         y[j] = omega * b[j] / d;
         continue;
       }
-      const int sidx = (ty + 8 * r + R) * SW + tx + R;
       T acc = T(0);
       const int nt = L.cnt[k];
       if (STAB) {
@@ -449,17 +461,20 @@ __global__ void __launch_bounds__(256, 6) k_coarse_op(CoarseLev<T> L, const int 
     const bool act = slot < nexpl;
     T acc = T(0), d = T(1);
     int j = 0;
+    bool pass = false;  // a row of the other colour in a Gauss-Seidel half-sweep
     if (act) {
       j = L.erow[slot];
       const int I1 = j % L.n, I2 = j / L.n;
+      pass = (OP == OP_JACOBI || OP == OP_JACOBI0) && color >= 0 && ((I1 + I2) & 1) != color;
       const int R = L.R, Wd = 2 * R + 1;
       d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
-      if (OP != OP_JACOBI0) acc = expl_window_sum_any<T>(L, slot, j, I1, I2, x, part, 4);
+      if (OP != OP_JACOBI0 && !pass) acc = expl_window_sum_any<T>(L, slot, j, I1, I2, x, part, 4);
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
     if (act && part == 0) {
-      if (OP == OP_JACOBI0) y[j] = omega * b[j] / d;
+      if (pass) y[j] = OP == OP_JACOBI ? x[j] : T(0);
+      else if (OP == OP_JACOBI0) y[j] = omega * b[j] / d;
       else coarse_finish<T, OP>(y, x, b, j, acc, d, omega);
     }
   }
@@ -467,7 +482,7 @@ __global__ void __launch_bounds__(256, 6) k_coarse_op(CoarseLev<T> L, const int 
 
 template <typename T>
 void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T omega, const T *x,
-                      const T *b, T *y, cudaStream_t s) {
+                      const T *b, T *y, cudaStream_t s, int color) {
   const int tx = (L.m + 31) / 32, tiles = tx * ((L.m + kCRowsY - 1) / kCRowsY);
   const int eg = std::max(1, std::min(2 * kRedBlocks, (4 * L.cap + 255) / 256));  // 4 threads per explicit row
   const int grid = tiles + eg;
@@ -476,7 +491,7 @@ void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T ome
   const size_t bytes = op == OP_JACOBI0 ? 0 : coarse_tile_bytes<T>(L.R) + (stab ? tab_bytes : 0);
   note_launch();
 #define SL_COARSE_LAUNCH(OPV, ST) \
-  k_coarse_op<T, OPV, ST><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y)
+  k_coarse_op<T, OPV, ST><<<grid, 256, bytes, s>>>(L, nexpl_dev, tx, tiles, omega, x, b, y, color)
   switch (op) {
     case OP_APPLY: if (stab) SL_COARSE_LAUNCH(OP_APPLY, 1); else SL_COARSE_LAUNCH(OP_APPLY, 0); break;
     case OP_RESID: if (stab) SL_COARSE_LAUNCH(OP_RESID, 1); else SL_COARSE_LAUNCH(OP_RESID, 0); break;
@@ -486,9 +501,9 @@ void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T ome
 #undef SL_COARSE_LAUNCH
 }
 template void launch_coarse_op<double>(int, const CoarseLev<double> &, const int *, double,
-                                       const double *, const double *, double *, cudaStream_t);
+                                       const double *, const double *, double *, cudaStream_t, int);
 template void launch_coarse_op<float>(int, const CoarseLev<float> &, const int *, float, const float *,
-                                      const float *, float *, cudaStream_t);
+                                      const float *, float *, cudaStream_t, int);
 
 // ----------------------------------------------------------------------------- V-cycle tail
 // The coarse end of the V-cycle (every level from l0 down, each with at most a few thousand
@@ -496,7 +511,7 @@ template void launch_coarse_op<float>(int, const CoarseLev<float> &, const int *
 // than the work, so one CTA walks the levels with __syncthreads between phases.  Each row
 // uses the same device functions as the grid-wide kernels.
 template <typename T>
-__device__ void tail_op(const CoarseLev<T> &L, int op, T omega, const T *x, const T *b, T *y) {
+__device__ void tail_op(const CoarseLev<T> &L, int op, T omega, const T *x, const T *b, T *y, int color = -1) {
   const int rows = L.m * L.m;
   for (int I = threadIdx.x; I < rows; I += blockDim.x) {
     const int j = (1 + I / L.m) * L.n + 1 + I % L.m;
@@ -504,18 +519,43 @@ __device__ void tail_op(const CoarseLev<T> &L, int op, T omega, const T *x, cons
     if (c >= 0) {
       switch (op) {
         case OP_RESID: coarse_class_row<T, OP_RESID>(L, c, j, omega, x, b, y); break;
-        case OP_JACOBI: coarse_class_row<T, OP_JACOBI>(L, c, j, omega, x, b, y); break;
-        default: coarse_class_row<T, OP_JACOBI0>(L, c, j, omega, x, b, y); break;
+        case OP_JACOBI: coarse_class_row<T, OP_JACOBI>(L, c, j, omega, x, b, y, color); break;
+        default: coarse_class_row<T, OP_JACOBI0>(L, c, j, omega, x, b, y, color); break;
       }
     } else {
       switch (op) {
         case OP_RESID: coarse_expl_row<T, OP_RESID>(L, -c - 1, omega, x, b, y); break;
-        case OP_JACOBI: coarse_expl_row<T, OP_JACOBI>(L, -c - 1, omega, x, b, y); break;
-        default: coarse_expl_row<T, OP_JACOBI0>(L, -c - 1, omega, x, b, y); break;
+        case OP_JACOBI: coarse_expl_row<T, OP_JACOBI>(L, -c - 1, omega, x, b, y, color); break;
+        default: coarse_expl_row<T, OP_JACOBI0>(L, -c - 1, omega, x, b, y, color); break;
       }
     }
   }
   __syncthreads();
+}
+
+// nu sweeps of the tail's smoother on level L from *c (from_zero: the first sweep starts at
+// x = 0 and writes *c), ping-ponging between *c and *o; the order of kernels of the grid-wide
+// path (sl_api.cu's smooth()).
+template <typename T>
+__device__ void tail_smooth(const CoarseLev<T> &L, const TailArgs<T> &a, const T *b, T *&c, T *&o,
+                            int sweeps, bool from_zero) {
+  for (int it = 0; it < sweeps; ++it) {
+    if (a.rbgs) {
+      for (int col = 0; col < 2; ++col) {
+        if (from_zero && it == 0 && col == 0) {
+          tail_op<T>(L, OP_JACOBI0, a.omega, nullptr, b, c, 0);
+        } else {
+          tail_op<T>(L, OP_JACOBI, a.omega, c, b, o, col);
+          T *sw = c; c = o; o = sw;
+        }
+      }
+    } else if (from_zero && it == 0) {
+      tail_op<T>(L, OP_JACOBI0, a.omega, nullptr, b, c);
+    } else {
+      tail_op<T>(L, OP_JACOBI, a.omega, c, b, o);
+      T *sw = c; c = o; o = sw;
+    }
+  }
 }
 
 template <typename T>
@@ -528,11 +568,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a) {
       for (int I = threadIdx.x; I < L.m * L.m; I += blockDim.x) c[(1 + I / L.m) * L.n + 1 + I % L.m] = T(0);
       __syncthreads();
     } else {
-      tail_op<T>(L, OP_JACOBI0, a.omega, nullptr, a.b[l], c);
-      for (int it = 1; it < a.nu1; ++it) {
-        tail_op<T>(L, OP_JACOBI, a.omega, c, a.b[l], o);
-        T *sw = c; c = o; o = sw;
-      }
+      tail_smooth<T>(L, a, a.b[l], c, o, a.nu1, true);
     }
     tail_op<T>(L, OP_RESID, a.omega, c, a.b[l], a.r[l]);
     const CoarseLev<T> &C = a.lev[l + 1];
@@ -563,10 +599,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a) {
       c[i2 * L.n + i1] += prolong_point<T>(cur[l + 1], C.n, i1, i2);
     }
     __syncthreads();
-    for (int it = 0; it < a.nu2; ++it) {
-      tail_op<T>(L, OP_JACOBI, a.omega, c, a.b[l], o);
-      T *sw = c; c = o; o = sw;
-    }
+    tail_smooth<T>(L, a, a.b[l], c, o, a.nu2, false);
     cur[l] = c;
   }
   if (cur[a.l0] != a.x[a.l0]) {

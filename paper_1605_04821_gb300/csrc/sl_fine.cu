@@ -488,10 +488,13 @@ template <int TMAX> struct InnerTaps<double, TMAX> {
 // The rows of tile (bx, by) (32 columns x 8 RPT rows) from the staged tile xs (pitch SW; the
 // tile's column 0 is grid column 1 + 32 bx - halo); kr: the rows' controls.  Every fine
 // operator kernel calls this, so all of them compute each row the same way.
+// color: -1 for every row; 0 or 1 for a half-sweep of the two-colour Gauss-Seidel smoother, in
+// which the Jacobi ops update only the rows with (i1 + i2) mod 2 == color and pass the others
+// through (x for OP_JACOBI, 0 for OP_JACOBI0, whose start is x = 0).
 template <typename T, int OP, int TMAX, int RPT>
 __device__ __forceinline__ void fine_tile_rows(const FineTab &tab, T dt, T omega, const T *xs,
                                                const T *__restrict__ b, T *__restrict__ y, int halo,
-                                               int SW, int bx, int by, const int (&kr)[RPT]) {
+                                               int SW, int bx, int by, const int (&kr)[RPT], int color) {
   const int n = tab.n, m = tab.m;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i1 = 1 + bx * 32 + tx;
@@ -508,6 +511,10 @@ __device__ __forceinline__ void fine_tile_rows(const FineTab &tab, T dt, T omega
     if (i2 > m) continue;
     const int k = kr[r];
     const int j = i2 * n + i1;
+    if ((OP == OP_JACOBI || OP == OP_JACOBI0) && color >= 0 && ((i1 + i2) & 1) != color) {
+      y[j] = OP == OP_JACOBI ? xs[(ty + 8 * r + halo) * SW + tx + halo] : T(0);
+      continue;
+    }
     if (inner) {
       if (OP == OP_JACOBI0) {
         y[j] = InnerTaps<T, TMAX>::od(tab, k) * b[j];
@@ -555,7 +562,7 @@ __device__ __forceinline__ void fine_tile_rows(const FineTab &tab, T dt, T omega
 template <typename T, int OP, int TMAX, int RPT = kFineRPT>
 __global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__restrict__ policy, T dt, T omega,
                                                  const T *__restrict__ x, const T *__restrict__ b,
-                                                 T *__restrict__ y, int halo, int SW) {
+                                                 T *__restrict__ y, int halo, int SW, int color) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
   const int n = tab.n, m = tab.m;
@@ -573,7 +580,7 @@ __global__ void __launch_bounds__(256) k_fine_op(FineTab tab, const uint8_t *__r
                   32 + 2 * halo, (8 * RPT) + 2 * halo, tx, ty);
     __syncthreads();
   }
-  fine_tile_rows<T, OP, TMAX, RPT>(tab, dt, omega, xs, b, y, halo, SW, blockIdx.x, blockIdx.y, kr);
+  fine_tile_rows<T, OP, TMAX, RPT>(tab, dt, omega, xs, b, y, halo, SW, blockIdx.x, blockIdx.y, kr, color);
 }
 
 // ----------------------------------------------------------------------------- TMA fine operator
@@ -661,7 +668,7 @@ template <int OP, int TMAX>
 __global__ void __launch_bounds__(256) k_fine_op_tma(FineTab tab, const uint8_t *__restrict__ policy, float dt,
                                                      float omega, const float *__restrict__ x,
                                                      const float *__restrict__ b, float *__restrict__ y,
-                                                     int halo, int SW, TmaTiles tt) {
+                                                     int halo, int SW, TmaTiles tt, int color) {
   constexpr int RPT = kFineRPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long bar[2];
@@ -733,7 +740,7 @@ __global__ void __launch_bounds__(256) k_fine_op_tma(FineTab tab, const uint8_t 
       __syncthreads();
       xs = buf[cur];
     }
-    fine_tile_rows<float, OP, TMAX, RPT>(tab, dt, omega, xs, b, y, halo, SW, bx, by, kr);
+    fine_tile_rows<float, OP, TMAX, RPT>(tab, dt, omega, xs, b, y, halo, SW, bx, by, kr, color);
     __syncthreads();
     cur ^= 1;
   }
@@ -748,7 +755,7 @@ template <int OP, int TMAX>
 __global__ void __launch_bounds__(256) k_fine_op_tma1(FineTab tab, const uint8_t *__restrict__ policy,
                                                       float dt, float omega, const float *__restrict__ x,
                                                       const float *__restrict__ b, float *__restrict__ y,
-                                                      int halo, int SW, TmaTiles tt) {
+                                                      int halo, int SW, TmaTiles tt, int color) {
   constexpr int RPT = kFineRPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long bar;
@@ -792,12 +799,12 @@ __global__ void __launch_bounds__(256) k_fine_op_tma1(FineTab tab, const uint8_t
     stage_tile<float>(buf, x, n, o1, o2, SW, WD, SH, tx, ty);
     __syncthreads();
   }
-  fine_tile_rows<float, OP, TMAX, RPT>(tab, dt, omega, xs, b, y, halo, SW, blockIdx.x, blockIdx.y, kr);
+  fine_tile_rows<float, OP, TMAX, RPT>(tab, dt, omega, xs, b, y, halo, SW, blockIdx.x, blockIdx.y, kr, color);
 }
 
 template <typename T, int OP>
 bool fine_op_tma(const FineTab &tab, const uint8_t *policy, T dt, T omega, const T *x, const T *b, T *y,
-                 int halo, int SW, cudaStream_t s) {
+                 int halo, int SW, int color, cudaStream_t s) {
   if constexpr (!std::is_same<T, float>::value || OP == OP_JACOBI0) {
     return false;
   } else {
@@ -815,11 +822,12 @@ bool fine_op_tma(const FineTab &tab, const uint8_t *policy, T dt, T omega, const
       // persistent: four blocks per SM of the 152, or one per tile when there are fewer
       const size_t bytes = 2 * size_t(tt.buf_floats) * sizeof(float);
       const int grid = std::min(tt.ntiles, 4 * 152);
-      k_fine_op_tma<OP, 12><<<grid, dim3(32, 8), bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, tt);
+      k_fine_op_tma<OP, 12><<<grid, dim3(32, 8), bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, tt, color);
     } else {
       const size_t bytes = size_t(tt.buf_floats) * sizeof(float);
       dim3 grd(tt.tiles_x, tt.ntiles / tt.tiles_x);
-      k_fine_op_tma1<OP, 12><<<grd, dim3(32, 8), bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, tt);
+      k_fine_op_tma1<OP, 12><<<grd, dim3(32, 8), bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, tt,
+                                                             color);
     }
     return true;
   }
@@ -827,37 +835,37 @@ bool fine_op_tma(const FineTab &tab, const uint8_t *policy, T dt, T omega, const
 
 template <typename T, int OP>
 void fine_op_dispatch(const FineTab &tab, const uint8_t *policy, T dt, T omega, const T *x, const T *b,
-                      T *y, int halo, int SW, cudaStream_t s) {
-  if (fine_op_tma<T, OP>(tab, policy, dt, omega, x, b, y, halo, SW, s)) return;
+                      T *y, int halo, int SW, int color, cudaStream_t s) {
+  if (fine_op_tma<T, OP>(tab, policy, dt, omega, x, b, y, halo, SW, color, s)) return;
   dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + 8 * kFineRPT - 1) / (8 * kFineRPT));
   const size_t bytes = OP == OP_JACOBI0 ? 0 : size_t(SW) * (8 * kFineRPT + 2 * halo) * sizeof(T);
   note_launch();
   switch (tab.tmax) {
-    case 8: k_fine_op<T, OP, 8><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
-    case 12: k_fine_op<T, OP, 12><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
-    case 16: k_fine_op<T, OP, 16><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
-    case 20: k_fine_op<T, OP, 20><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
-    default: k_fine_op<T, OP, 0><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW); break;
+    case 8: k_fine_op<T, OP, 8><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, color); break;
+    case 12: k_fine_op<T, OP, 12><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, color); break;
+    case 16: k_fine_op<T, OP, 16><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, color); break;
+    case 20: k_fine_op<T, OP, 20><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, color); break;
+    default: k_fine_op<T, OP, 0><<<grd, blk, bytes, s>>>(tab, policy, dt, omega, x, b, y, halo, SW, color); break;
   }
 }
 
 template <typename T>
 void launch_fine_op(int op, const FineTab &tab, const int32_t *slin, const uint8_t *policy, T dt,
-                    T omega, const T *x, const T *b, T *y, int halo, int SW, cudaStream_t s) {
+                    T omega, const T *x, const T *b, T *y, int halo, int SW, cudaStream_t s, int color) {
   (void)slin;
   switch (op) {
-    case OP_APPLY: fine_op_dispatch<T, OP_APPLY>(tab, policy, dt, omega, x, b, y, halo, SW, s); break;
-    case OP_RESID: fine_op_dispatch<T, OP_RESID>(tab, policy, dt, omega, x, b, y, halo, SW, s); break;
-    case OP_JACOBI: fine_op_dispatch<T, OP_JACOBI>(tab, policy, dt, omega, x, b, y, halo, SW, s); break;
-    default: fine_op_dispatch<T, OP_JACOBI0>(tab, policy, dt, omega, x, b, y, halo, SW, s); break;
+    case OP_APPLY: fine_op_dispatch<T, OP_APPLY>(tab, policy, dt, omega, x, b, y, halo, SW, -1, s); break;
+    case OP_RESID: fine_op_dispatch<T, OP_RESID>(tab, policy, dt, omega, x, b, y, halo, SW, -1, s); break;
+    case OP_JACOBI: fine_op_dispatch<T, OP_JACOBI>(tab, policy, dt, omega, x, b, y, halo, SW, color, s); break;
+    default: fine_op_dispatch<T, OP_JACOBI0>(tab, policy, dt, omega, x, b, y, halo, SW, color, s); break;
   }
 }
 template void launch_fine_op<double>(int, const FineTab &, const int32_t *, const uint8_t *, double,
                                      double, const double *, const double *, double *, int, int,
-                                     cudaStream_t);
+                                     cudaStream_t, int);
 template void launch_fine_op<float>(int, const FineTab &, const int32_t *, const uint8_t *, float,
                                     float, const float *, const float *, float *, int, int,
-                                    cudaStream_t);
+                                    cudaStream_t, int);
 
 // omega / d_e for every fine table entry, d_e = 1 + dt (W_e - c_k - w_self,e) (the Jacobi scale).
 // The interior entry of each control (q1 = q2 = B) also goes to iod[k] when iod64 is given.

@@ -66,10 +66,12 @@ void launch_coef(const double *G, int nf, int nq, const double *tau, const doubl
                  cudaStream_t s);
 cudaError_t launch_argmin(const ArgminArgs &a, const ArgminITaps &it, cudaStream_t s);
 
-// slin: staged-tile tap offsets (pitch SW = 32 + 2 halo), the same table as the argmin's.
+// slin: staged-tile tap offsets (pitch SW), the same table as the argmin's.
+// color (OP_JACOBI / OP_JACOBI0): -1 every row; 0 / 1 a half-sweep of the two-colour
+// Gauss-Seidel smoother (rows with (i1 + i2) mod 2 == color updated, the others passed through).
 template <typename T>
 void launch_fine_op(int op, const FineTab &tab, const int32_t *slin, const uint8_t *policy, T dt,
-                    T omega, const T *x, const T *b, T *y, int halo, int SW, cudaStream_t s);
+                    T omega, const T *x, const T *b, T *y, int halo, int SW, cudaStream_t s, int color = -1);
 
 // Jacobi scale omega / d_e of every fine table entry for step size dt (into od64 / od32).
 void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, float *od32,
@@ -99,11 +101,12 @@ cudaError_t launch_rap_explicit(int level, const FineTab &tab, const int32_t *fi
                                 T *ewin_out, cudaStream_t s);
 template <typename T>
 void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T omega, const T *x,
-                      const T *b, T *y, cudaStream_t s);
+                      const T *b, T *y, cudaStream_t s, int color = -1);
 // Levels l0 .. L-1 of one V-cycle in a single thread block (x[l0] = M_l0^{-1} b[l0]).
 template <typename T>
 struct TailArgs {
   int l0, L, nu1, nu2;
+  int rbgs;  // 1: two-colour Gauss-Seidel sweeps (relaxation omega); 0: damped Jacobi
   T omega;
   CoarseLev<T> lev[kMaxLevels];
   T *x[kMaxLevels], *t[kMaxLevels], *r[kMaxLevels], *b[kMaxLevels];
