@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-amg", action="store_true")
+    p.add_argument("--no-smoother", action="store_true")
     p.add_argument("--amg-steps", type=int, default=8)
     p.add_argument("--batched-instances", type=int, default=256)
     p.add_argument("--batched-workers", type=int, default=16)
@@ -380,6 +381,13 @@ def run_ours(args):
         amg = amg_record(slp, prob, dev, stream, args, extra, g)
         torch.cuda.nvtx.range_pop()
 
+    # ---- two-colour Gauss-Seidel against damped Jacobi on the same steps
+    smoother = None
+    if not args.no_smoother:
+        torch.cuda.nvtx.range_push("smoother")
+        smoother = smoother_record(slp, prob, dev, stream, args, extra, g)
+        torch.cuda.nvtx.range_pop()
+
     # ---- batched: many independent instances, LPT-sharded over the ranks
     batched = None
     if not args.no_batched:
@@ -417,6 +425,7 @@ def run_ours(args):
             "adjoint": adjoint,
             "batched": batched,
             "amg": amg,
+            "smoother": smoother,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -512,6 +521,41 @@ def amg_record(slp, prob, dev, stream, args, extra, g):
         del s
         torch.cuda.empty_cache()
     out["value"] = out["aggregation_kcycle"]["value"]
+    return out
+
+
+def smoother_record(slp, prob, dev, stream, args, extra, g):
+    """Mixed-precision steps W+1 .. W+K of the headline workload with two-colour Gauss-Seidel
+    smoothing (relaxation 1) and with damped Jacobi (omega 0.8), each timed with CUDA events."""
+    import torch
+    n = prob.n
+    dt = 1.0 / 128
+    k = args.amg_steps
+    out = {"workload": f"steps {args.warmup + 1}..{args.warmup + k} of the headline workload, mixed precision",
+           "unit": UNIT}
+    for sm, om, key in ((1, 1.0, "red_black_gauss_seidel"), (0, 0.8, "damped_jacobi")):
+        kw = dict(precision=1, argmin_screen=1)
+        kw.update(extra)
+        kw.update(smoother=sm, omega=om)
+        s = slp.solver_from_problem(prob, device=dev, **kw)
+        u = g.clone()
+        for i in range(1, args.warmup + 1):
+            s.step(u, i * dt, dt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = {"pi_iters": 0, "krylov_iters": 0, "ir_iters": 0}
+        e0.record(stream)
+        for i in range(1, k + 1):
+            r = s.step(u, (args.warmup + i) * dt, dt)
+            for kk in st:
+                st[kk] += r[kk]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[key] = {"value": n * n * k / (ms / 1e3), "ms_per_step": ms / k, "omega": om, **st}
+        del s
+        torch.cuda.empty_cache()
+    out["value"] = out["red_black_gauss_seidel"]["value"]
     return out
 
 
