@@ -392,6 +392,269 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin(const __grid_constant__ Arg
   }
 }
 
+// ----------------------------------------------------------------------------- argmin, two nodes
+// The FP32 screen of k_argmin<1, TMAX> with two nodes per thread: rows ty and ty + 8 of a 32 x 16
+// tile.  The nodes of the interior class share each tap's {offset, weight} (a uniform load) and
+// keep their accumulators as FP32 pairs (__ffma2_rn / __fadd2_rn: per lane the rounding of a
+// scalar FMA / add), so a tap costs two shared loads and four paired operations for both nodes.
+// The screen's bound is the one of k_argmin, evaluated as
+//   E_k = A_k S + 8 u |v| + (2 E_f + 2 eta W_k),   A_k = 2 u (n_t + 4) 1.001  (per control),
+// the same sum of positive terms; its own rounding (a few u relative) is far inside the factor 2
+// and the 1.001 margins of the derivation, so the screen stays rigorous and the FP64 decision
+// among the survivors gives the same policy.  Nodes outside the interior class, and threads
+// whose two nodes are not both interior, run k_argmin's per-node screen.
+constexpr int kTY2 = 16;  // node rows per block
+
+struct NodeScreen {
+  int j, q1, q2, sidx;
+  bool valid, itap;
+  float Fv32[4], xj32, Ef, x0;
+  unsigned long long cand;
+  int ncand;
+  bool overflow;
+};
+
+// k_argmin's screen of one node over every control (any table entry).
+template <int TMAX>
+__device__ __forceinline__ void screen_one(const ArgminArgs &a, const ArgminITaps &it, const float *xs32,
+                                           const float4 *ctl_phi, const float4 *ctl_cw, float eta,
+                                           NodeScreen &ns) {
+  const FineTab &tab = a.tab;
+  const float u = 5.9604645e-8f;
+  const int nf = a.nf;
+  float Umin = INFINITY, Lmin = INFINITY;
+  for (int k = 0; k < tab.K; ++k) {
+    const int e = (k * tab.Q + ns.q2) * tab.Q + ns.q1;
+    float S;
+    const float acc = ns.itap ? eval_itap32<TMAX>(it, k, xs32, ns.sidx, ns.x0, S)
+                              : eval_smem32<TMAX>(tab, e, xs32, ns.sidx, ns.x0, S);
+    const float4 ph = ctl_phi[k], cw = ctl_cw[k];
+    float f = fmaf(ph.x, ns.Fv32[0], 0.f);
+    f = fmaf(ph.y, ns.Fv32[1], f);
+    f = fmaf(ph.z, ns.Fv32[2], f);
+    if (nf > 3) f = fmaf(ph.w, ns.Fv32[3], f);
+    const float v = acc + fmaf(cw.x, ns.xj32, f);
+    if (!(v == v)) continue;
+    const float ntf = ns.itap ? cw.z : __int_as_float(0x4B000000 | int(tab.nt[e])) - 8388608.0f;
+    const float We = ns.itap ? cw.y : __ldg(tab.W32 + e);
+    const float E = 2.0f * (u * ((ntf + 4.0f) * S * 1.001f + 2.0f * fabsf(v)) + ns.Ef + eta * We) +
+                    4.0f * u * fabsf(v);
+    const float lb = v - E, ub = v + E;
+    const float tw = a.tie2_32 * fmaxf(1.0f, fabsf(v)) + 4.0f * u * fabsf(v);
+    Umin = fminf(Umin, ub);
+    if (ub + tw < Lmin) {
+      ns.cand = (unsigned long long)k;
+      ns.ncand = 1;
+      ns.overflow = false;
+      Lmin = lb;
+    } else if (lb <= Umin + tw) {
+      cand_push(ns.cand, ns.ncand, ns.overflow, k);
+      Lmin = fminf(Lmin, lb);
+    }
+  }
+}
+
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// The paired screen of two interior-class nodes (the taps from the kernel parameter).
+template <int TMAX>
+__device__ __forceinline__ void screen_pair(const ArgminArgs &a, const ArgminITaps &it, const float *xs32,
+                                            const float4 *ctl_phi, const float4 *ctl_cw, float eta,
+                                            NodeScreen &n0, NodeScreen &n1) {
+  const int K = a.tab.K, nf = a.nf;
+  const float u = 5.9604645e-8f;
+  const char *xb0 = reinterpret_cast<const char *>(xs32 + n0.sidx);
+  const char *xb1 = reinterpret_cast<const char *>(xs32 + n1.sidx);
+  const float2 nx0 = make_float2(-n0.x0, -n1.x0);
+  const float2 xj = make_float2(n0.xj32, n1.xj32);
+  const float2 F0 = make_float2(n0.Fv32[0], n1.Fv32[0]), F1 = make_float2(n0.Fv32[1], n1.Fv32[1]);
+  const float2 F2 = make_float2(n0.Fv32[2], n1.Fv32[2]), F3 = make_float2(n0.Fv32[3], n1.Fv32[3]);
+  const float2 Ef2 = make_float2(2.0f * n0.Ef, 2.0f * n1.Ef);
+  const float eta2 = 2.0f * eta, tw_rel = a.tie2_32;
+  float Umin[2] = {INFINITY, INFINITY}, Lmin[2] = {INFINITY, INFINITY};
+  NodeScreen *ns[2] = {&n0, &n1};
+  for (int k = 0; k < K; ++k) {
+    float2 acc = f2(0.f), sa = f2(0.f);
+#pragma unroll
+    for (int t = 0; t < TMAX; ++t) {
+      const int2 p = it.t[k * TMAX + t];
+      const float2 w = f2(__int_as_float(p.y));
+      const float2 d = make_float2(*reinterpret_cast<const float *>(xb0 + p.x),
+                                   *reinterpret_cast<const float *>(xb1 + p.x));
+      const float2 dd = __fadd2_rn(d, nx0);
+      acc = __ffma2_rn(w, dd, acc);
+      sa = __ffma2_rn(w, make_float2(fabsf(dd.x), fabsf(dd.y)), sa);
+    }
+    const float4 ph = ctl_phi[k], cw = ctl_cw[k];
+    float2 f = __ffma2_rn(f2(ph.x), F0, f2(0.f));
+    f = __ffma2_rn(f2(ph.y), F1, f);
+    f = __ffma2_rn(f2(ph.z), F2, f);
+    if (nf > 3) f = __ffma2_rn(f2(ph.w), F3, f);
+    const float2 v = __fadd2_rn(acc, __ffma2_rn(f2(cw.x), xj, f));
+    const float2 av = make_float2(fabsf(v.x), fabsf(v.y));
+    // E = A_k S + 8 u |v| + 2 E_f + 2 eta W_k  (cw.w = A_k, cw.y = W_k)
+    const float2 E = __ffma2_rn(f2(cw.w), sa, __ffma2_rn(f2(8.0f * u), av, __ffma2_rn(f2(eta2), f2(cw.y), Ef2)));
+    const float2 lb = __fadd2_rn(v, make_float2(-E.x, -E.y)), ub = __fadd2_rn(v, E);
+    const float2 tw = __ffma2_rn(f2(4.0f * u), av,
+                                 __fmul2_rn(f2(tw_rel), make_float2(fmaxf(1.0f, av.x), fmaxf(1.0f, av.y))));
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float vq = q ? v.y : v.x;
+      if (!(vq == vq)) continue;
+      const float lbq = q ? lb.y : lb.x, ubq = q ? ub.y : ub.x, twq = q ? tw.y : tw.x;
+      Umin[q] = fminf(Umin[q], ubq);
+      if (ubq + twq < Lmin[q]) {
+        ns[q]->cand = (unsigned long long)k;
+        ns[q]->ncand = 1;
+        ns[q]->overflow = false;
+        Lmin[q] = lbq;
+      } else if (lbq <= Umin[q] + twq) {
+        cand_push(ns[q]->cand, ns[q]->ncand, ns[q]->overflow, k);
+        Lmin[q] = fminf(Lmin[q], lbq);
+      }
+    }
+  }
+}
+
+// The exact FP64 decision among a node's screened candidates (all controls on overflow), as in
+// k_argmin's pass 2: the lowest index within the tie window of the FP64 minimum; -1 if none.
+__device__ __forceinline__ int decide_fp64(const ArgminArgs &a, const NodeScreen &ns) {
+  if (ns.ncand == 1 && !ns.overflow) return int(ns.cand & 0xffull);
+  if (ns.ncand == 0 && !ns.overflow) return -1;
+  const FineTab &tab = a.tab;
+  const int nf = a.nf, j = ns.j;
+  const size_t N = size_t(tab.n) * tab.n;
+  double Fv[4];
+#pragma unroll
+  for (int mm = 0; mm < 4; ++mm) Fv[mm] = mm < nf ? a.F[mm * N + j] : 0.0;
+  const double Xj = a.X[j];
+  const int cnt = ns.overflow ? tab.K : ns.ncand;
+  auto value = [&](int k) {
+    const int e = (k * tab.Q + ns.q2) * tab.Q + ns.q1;
+    double f = 0.0;
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm)
+      if (mm < nf) f = fma(__ldg(a.phi + k * nf + mm), Fv[mm], f);
+    return eval_global64(tab, e, a.X, j) + fma(tab.c64[k], Xj, f);
+  };
+  double vm = INFINITY;
+  double vals[kMaxCand];
+  for (int c = 0; c < cnt; ++c) {
+    const int k = ns.overflow ? c : int((ns.cand >> (8 * c)) & 0xffull);
+    const double v = value(k);
+    if (c < kMaxCand) vals[c] = v;
+    vm = fmin(vm, v);
+  }
+  const double thr = vm + a.tie_rel * fmax(1.0, fabs(vm));
+  for (int c = 0; c < cnt; ++c) {
+    const int k = ns.overflow ? c : int((ns.cand >> (8 * c)) & 0xffull);
+    const double v = c < kMaxCand ? vals[c] : value(k);
+    if (v <= thr) return k;
+  }
+  return -1;
+}
+
+template <int TMAX>
+__global__ void __launch_bounds__(kTX *kTY) k_argmin2(const __grid_constant__ ArgminArgs a,
+                                                      const __grid_constant__ ArgminITaps it) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned red_cnt[kTX * kTY / 32];
+  __shared__ float red_max[kTX * kTY / 32];
+  const int SH = kTY2 + 2 * a.halo;
+  float *xs32 = reinterpret_cast<float *>(smem_raw);
+  float4 *ctl_phi = reinterpret_cast<float4 *>(smem_raw + argmin_tile_bytes(a.SW, SH, true));
+  float4 *ctl_cw = ctl_phi + a.tab.K;
+  const FineTab &tab = a.tab;
+  const int n = tab.n, m = tab.m;
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  const int o1 = 1 + blockIdx.x * kTX - a.halo, o2 = 1 + blockIdx.y * kTY2 - a.halo;
+  const int c1 = min(1 + blockIdx.x * kTX + kTX / 2, n - 2), c2 = min(1 + blockIdx.y * kTY2 + kTY2 / 2, n - 2);
+  const double xc = a.X[size_t(c2) * n + c1];
+  const float u = 5.9604645e-8f;
+  float dmax = 0.f;
+  stage_window<4, float>(xs32, a.SW, SH, threadIdx.x, threadIdx.y, [&](int r, int cc) {
+    const int g2 = o2 + r, g1 = o1 + cc;
+    const bool in = g1 >= 0 && g1 < n && g2 >= 0 && g2 < n;
+    const float xd = float((in ? a.X[size_t(g2) * n + g1] : 0.0) - xc);
+    if (in) dmax = fmaxf(dmax, fabsf(xd));
+    return xd;
+  }, 32 + 2 * a.halo);
+  for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  if ((tid & 31) == 0) red_max[tid >> 5] = dmax;
+  const bool inner_exists = n - 1 >= 2 * tab.B;
+  for (int k = tid; k < tab.K; k += kTX * kTY) {
+    float p[4];
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) p[mm] = mm < a.nf ? __ldg(a.phi32 + k * a.nf + mm) : 0.f;
+    ctl_phi[k] = make_float4(p[0], p[1], p[2], p[3]);
+    const int ei = (k * tab.Q + tab.B) * tab.Q + tab.B;
+    const float ntf = inner_exists ? float(tab.nt[ei]) : 0.f;
+    ctl_cw[k] = make_float4(tab.c32[k], inner_exists ? tab.W32[ei] : 0.f, ntf, 2.0f * u * (ntf + 4.0f) * 1.001f);
+  }
+  __syncthreads();
+  float Dmax = 0.f;
+  for (int w = 0; w < kTX * kTY / 32; ++w) Dmax = fmaxf(Dmax, red_max[w]);
+  const float eta = 2.0f * u * Dmax * 1.001f + 1e-30f;
+
+  const int i1 = 1 + blockIdx.x * kTX + threadIdx.x;
+  NodeScreen ns[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    NodeScreen &s = ns[q];
+    const int i2 = 1 + blockIdx.y * kTY2 + threadIdx.y + 8 * q;
+    s.valid = i1 <= m && i2 <= m;
+    s.cand = 0ull;
+    s.ncand = 0;
+    s.overflow = false;
+    s.itap = false;
+    if (!s.valid) continue;
+    s.j = i2 * n + i1;
+    s.q1 = class_q(i1, n, tab.B);
+    s.q2 = class_q(i2, n, tab.B);
+    s.sidx = (threadIdx.y + 8 * q + a.halo) * a.SW + threadIdx.x + a.halo;
+    const size_t N = size_t(n) * n;
+    float Fabs = 0.f;
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) {
+      s.Fv32[mm] = mm < a.nf ? a.F32[mm * N + s.j] : 0.f;
+      if (mm < a.nf) Fabs = fmaf(a.phimax32[mm], fabsf(s.Fv32[mm]), Fabs);
+    }
+    s.xj32 = float(a.X[s.j]);
+    s.Ef = u * ((a.nf + 3.0f) * Fabs * 1.001f + 3.0f * a.cmax32 * fabsf(s.xj32) * 1.001f);
+    s.x0 = xs32[s.sidx];
+    s.itap = TMAX > 0 && it.n > 0 && s.q1 == tab.B && s.q2 == tab.B;
+  }
+  if (ns[0].valid && ns[1].valid && ns[0].itap && ns[1].itap) {
+    screen_pair<TMAX>(a, it, xs32, ctl_phi, ctl_cw, eta, ns[0], ns[1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (ns[q].valid) screen_one<TMAX>(a, it, xs32, ctl_phi, ctl_cw, eta, ns[q]);
+  }
+  unsigned changed = 0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (!ns[q].valid) continue;
+    const int best = decide_fp64(a, ns[q]);
+    const int i2 = 1 + blockIdx.y * kTY2 + threadIdx.y + 8 * q;
+    const int pidx = (i2 - 1) * m + (i1 - 1);
+    if (best < 0) {
+      atomicOr(a.flags, 1);
+    } else if (a.policy[pidx] != uint8_t(best)) {
+      changed += 1;
+      a.policy[pidx] = uint8_t(best);
+    }
+  }
+  const unsigned c = __reduce_add_sync(0xffffffffu, changed);
+  if ((tid & 31) == 0) red_cnt[tid >> 5] = c;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < kTX * kTY / 32; ++w) tot += red_cnt[w];
+    if (tot) atomicAdd(a.changes, (unsigned long long)tot);
+  }
+}
+
 template <int SCREEN, int TMAX>
 cudaError_t argmin_launch(const ArgminArgs &a, const ArgminITaps &it, dim3 grd, dim3 blk, size_t bytes,
                           cudaStream_t s) {
@@ -401,6 +664,14 @@ cudaError_t argmin_launch(const ArgminArgs &a, const ArgminITaps &it, dim3 grd, 
 }
 
 cudaError_t launch_argmin(const ArgminArgs &a, const ArgminITaps &it, cudaStream_t s) {
+  if (a.screen && a.tab.tmax == 12 && it.n > 0) {
+    // two nodes per thread on 32 x 16 tiles (k_argmin2)
+    dim3 blk(kTX, kTY), grd((a.tab.m + kTX - 1) / kTX, (a.tab.m + kTY2 - 1) / kTY2);
+    const size_t bytes = argmin_tile_bytes(a.SW, kTY2 + 2 * a.halo, true) + 2 * size_t(a.tab.K) * sizeof(float4);
+    note_launch();
+    k_argmin2<12><<<grd, blk, bytes, s>>>(a, it);
+    return cudaGetLastError();
+  }
   dim3 blk(kTX, kTY), grd((a.tab.m + kTX - 1) / kTX, (a.tab.m + kTY - 1) / kTY);
   const size_t bytes = argmin_tile_bytes(a.SW, a.SH, a.screen) + (a.screen ? 2 * size_t(a.tab.K) * sizeof(float4) : 0);
   if (!a.screen) return argmin_launch<0, 0>(a, it, grd, blk, bytes, s);
@@ -1048,7 +1319,8 @@ cudaError_t prepare_fine_kernels() {
                       reinterpret_cast<const void *>(k_argmin<1, 12>),
                       reinterpret_cast<const void *>(k_argmin<1, 16>),
                       reinterpret_cast<const void *>(k_argmin<1, 20>),
-                      reinterpret_cast<const void *>(k_argmin<1, 0>)};
+                      reinterpret_cast<const void *>(k_argmin<1, 0>),
+                      reinterpret_cast<const void *>(k_argmin2<12>)};
   for (const void *f : fs) {
     cudaError_t e = allow_dynamic_smem(f);
     if (e != cudaSuccess) return e;
