@@ -581,6 +581,15 @@ void smooth(sl_hjb *h, int l, double dt, const T *b, T *&cur, T *&other, int swe
   }
 }
 
+// Number of times smooth() exchanges its two buffers over one V-cycle level: every sweep (or
+// half-sweep) that reads one buffer and writes the other.  A cycle that starts its
+// pre-smoothing in the work buffer when this is odd ends its post-smoothing in x, with no copy.
+inline int smooth_swaps(const sl_hjb *h) {
+  const int per = (h->o.smoother == 1 && !h->transposed) ? 2 : 1;
+  const int pre = h->o.nu1 > 0 ? per * h->o.nu1 - 1 : 0;
+  return pre + per * h->o.nu2;
+}
+
 template <typename T>
 void vbufs(VBuf &v, T **x, T **t, T **r, T **b);
 template <>
@@ -621,8 +630,11 @@ sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) 
   }
   T *bx, *bt, *br, *bb;
   vbufs<T>(h->vb[l], &bx, &bt, &br, &bb);
+  // the buffer the pre-smoothing starts in is chosen so that the last sweep writes x; bt's
+  // boundary entries are zero (no operator writes a boundary entry), as x's must be
   T *cur = x, *other = bt;
-  if (h->o.nu1 == 0) launch_fill<T>(x, N, T(0), s);
+  if (smooth_swaps(h) & 1) std::swap(cur, other);
+  if (h->o.nu1 == 0) launch_fill<T>(cur, N, T(0), s);
   else smooth<T>(h, l, dt, b, cur, other, h->o.nu1, true, s);
   level_op<T>(h, l, OP_RESID, dt, cur, b, br, s);
   T *cx, *ct, *cr, *cb;
@@ -1500,7 +1512,8 @@ sl_status vcycle_into(sl_hjb *h, int l, double dt, const T *b, T *x, T *const *t
     return SL_OK;
   }
   T *cur = x, *other = t[l];
-  if (h->o.nu1 == 0) launch_fill<T>(x, N, T(0), s);
+  if (smooth_swaps(h) & 1) std::swap(cur, other);
+  if (h->o.nu1 == 0) launch_fill<T>(cur, N, T(0), s);
   else smooth<T>(h, l, dt, b, cur, other, h->o.nu1, true, s);
   level_op<T>(h, l, OP_RESID, dt, cur, b, r[l], s);
   launch_restrict<T>(r[l], h->cl[l].n, cb[l + 1], h->cl[l + 1].n, s);
