@@ -185,6 +185,17 @@ typedef struct {
                            next tile's copies in flight while it computes the current one (two
                            buffers); 0: the threads stage every tile.  All three compute each row
                            the same way and give the same result bit for bit. */
+  int coarse_fusion;    /* f >= 1: the V-cycle's levels l >= f (coarse levels only: f = 1 is the
+                           first coarse level) above the single-block tail, with the Jacobi
+                           smoother and nu1, nu2 >= 1, take two launches per level and cycle: the
+                           last pre-smoothing sweep (or the first, from zero), the residual and
+                           the full-weighting restriction in one kernel; the prolongation with
+                           the first post-smoothing sweep in another; each tile of rows stages its
+                           values once in shared memory.  0: one launch per operation on every
+                           level.  All settings give the same result bit for bit.  Default 3: on
+                           the first two coarse levels (the widest, where a tile's explicit rows
+                           and its halo cost more than the launches saved) the one-pass kernels
+                           are faster. */
 } sl_opts;
 
 typedef struct {
@@ -204,7 +215,7 @@ typedef struct {
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
  * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
- * extrapolate 1, precond 0, amg_k_levels 2, smoother 0, fine_tma 1. */
+ * extrapolate 1, precond 0, amg_k_levels 2, smoother 0, fine_tma 1, coarse_fusion 3. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every
@@ -445,9 +456,30 @@ sl_status sl_hjb_linear_solve(sl_hjb *h, const double *u_prev_dev, double *x_ext
                               double dt, sl_stats *stats, void *stream);
 
 /* Sizes of level `level` of the current hierarchy: nodes per dimension, stored explicit
- * rows, and the number of non-zeros (class rows counted with their table's non-zeros). */
+ * rows, and the number of non-zeros (class rows counted with their table's non-zeros,
+ * explicit rows with the non-zero entries of their windows; -1 on the matrix-free level 0).
+ * Reads the tables back from the device: synchronises with the device (diagnostic use). */
 sl_status sl_hjb_level_info(const sl_hjb *h, int level, int *n, long long *explicit_rows,
                             long long *nnz);
+
+/* Storage statistics of one level of the Galerkin hierarchy (Section 3.3's R A P operators),
+ * for diagnostics: the fine level is matrix-free; a coarse row is either a class row (stencil
+ * from a per-control table) or an explicit row (a dense (2 reach + 1)^2 window). */
+typedef struct {
+  int n;                       /* nodes per dimension */
+  int reach;                   /* stencil reach in nodes (level 0: the fine operator's halo) */
+  long long explicit_rows;     /* rows stored as dense windows (0 on level 0) */
+  long long class_nnz;         /* non-zeros of the class rows (-1 on level 0) */
+  long long explicit_nnz;      /* non-zero entries of the explicit windows
+                                  (both count coefficients of interior columns only: rows next
+                                  to the boundary also hold weights of boundary nodes, which
+                                  multiply the Dirichlet zero of the correction) */
+  long long explicit_entries;  /* stored window entries: explicit_rows * (2 reach + 1)^2 */
+} sl_level_stats;
+
+/* Fills *out for level `level`.  SL_EINVAL for a null handle or output or a level outside
+ * [0, sl_hjb_num_levels).  Synchronises with the device (the tables are read back). */
+sl_status sl_hjb_level_stats(const sl_hjb *h, int level, sl_level_stats *out);
 
 /* Number of levels in use. */
 int sl_hjb_num_levels(const sl_hjb *h);

@@ -30,7 +30,8 @@ EXPORTED = ["sl_opts_default", "sl_hjb_create", "sl_hjb_step", "sl_hjb_solve",
             "sl_batch_create", "sl_batch_run", "sl_batch_worker_of", "sl_batch_plan",
             "sl_batch_last_error", "sl_batch_destroy", "sl_amg_create", "sl_amg_num_levels",
             "sl_amg_level", "sl_amg_apply", "sl_amg_last_error", "sl_amg_destroy",
-            "sl_hjb_recorded_policy", "sl_hjb_set_launch", "sl_batch_autotune"]
+            "sl_hjb_recorded_policy", "sl_hjb_set_launch", "sl_batch_autotune",
+            "sl_hjb_level_stats"]
 
 
 class SlGrid(ctypes.Structure):
@@ -64,7 +65,8 @@ class SlOpts(ctypes.Structure):
                 ("argmin_screen", ctypes.c_int), ("rebuild_frac", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("coarse_tail_rows", ctypes.c_int),
                 ("extrapolate", ctypes.c_int), ("precond", ctypes.c_int), ("amg_k_levels", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("fine_tma", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("fine_tma", ctypes.c_int),
+                ("coarse_fusion", ctypes.c_int)]
 
 
 class SlInstance(ctypes.Structure):
@@ -76,6 +78,12 @@ class SlInstance(ctypes.Structure):
 class SlTuneChoice(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("instances", ctypes.c_int), ("coarse_tail_rows", ctypes.c_int),
                 ("probe_seconds", ctypes.c_double)]
+
+
+class SlLevelStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("reach", ctypes.c_int), ("explicit_rows", ctypes.c_longlong),
+                ("class_nnz", ctypes.c_longlong), ("explicit_nnz", ctypes.c_longlong),
+                ("explicit_entries", ctypes.c_longlong)]
 
 
 class SlStats(ctypes.Structure):
@@ -120,6 +128,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "sl_hjb_linear_solve": (i, [vp, vp, vp, d, d, ctypes.POINTER(SlStats), vp]),
         "sl_hjb_level_info": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ll), ctypes.POINTER(ll)]),
         "sl_hjb_num_levels": (i, [vp]),
+        "sl_hjb_level_stats": (i, [vp, i, ctypes.POINTER(SlLevelStats)]),
         "sl_launch_count": (ll, []),
         "sl_hjb_vcycle_noalloc": (i, [vp, i, vp, vp, vp]),
         "sl_hjb_solve_record": (i, [vp, vp, d, d, i, i, ctypes.POINTER(SlStats), vp]),
@@ -423,7 +432,13 @@ class Solver:
         nnz = ctypes.c_longlong(0)
         self._check(self._lib.sl_hjb_level_info(self.h, level, ctypes.byref(n), ctypes.byref(ex),
                                                 ctypes.byref(nnz)))
-        return n.value, ex.value
+        return n.value, ex.value, nnz.value
+
+    def level_stats(self, level: int) -> dict:
+        """sl_hjb_level_stats: reach, class and explicit non-zeros of one hierarchy level."""
+        st = SlLevelStats()
+        self._check(self._lib.sl_hjb_level_stats(self.h, level, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
 
 
 def _problem_args(prob, dev):

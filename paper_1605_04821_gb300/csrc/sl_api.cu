@@ -31,8 +31,8 @@ struct CoarseBuf {
   float *ewin32 = nullptr, *cw32 = nullptr, *cdiag32 = nullptr;
   double *cdense64 = nullptr, *WT64 = nullptr;  // class windows [k*win + e]; rows of A_l^T
   float *cdense32 = nullptr, *WT32 = nullptr;
-  long long class_nnz_sum = 0;  // sum over class rows of their table's non-zeros
-  std::vector<int> cnt_host;
+  std::vector<int> cnt_host;       // taps per class
+  std::vector<int32_t> coff_host;  // class taps' packed offsets (dy << 16) | (dx & 0xffff)
 };
 
 template <typename T> T *pick(double *a, float *b);
@@ -406,7 +406,7 @@ sl_status build_class_tables(sl_hjb *h, double dt) {
       AL(c.cpk64, size_t(h->K) * ctmax);
     }
     {
-      const int SWl = 32 + 2 * c.R;
+      const int SWl = coarse_pitch(c.R);
       std::vector<int2> p32(size_t(h->K) * ctmax, make_int2(0, 0));
       std::vector<longlong2> p64(size_t(h->K) * ctmax);
       for (size_t i = 0; i < p64.size(); ++i) { p64[i].x = 0; p64[i].y = 0; }
@@ -453,6 +453,7 @@ sl_status build_class_tables(sl_hjb *h, double dt) {
     CK(cudaMemcpy(c.cdiag64, diag.data(), diag.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c.cdiag32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice));
     c.cnt_host = cnt;
+    c.coff_host = off;
     prev.swap(cur);
     Rprev = c.R;
   }
@@ -634,15 +635,36 @@ sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) 
   // boundary entries are zero (no operator writes a boundary entry), as x's must be
   T *cur = x, *other = bt;
   if (smooth_swaps(h) & 1) std::swap(cur, other);
+  T *cx, *ct, *cr, *cb;
+  vbufs<T>(h->vb[l + 1], &cx, &ct, &cr, &cb);
+  const int nc = h->cl[l + 1].n;
+  // coarse levels with the Jacobi smoother: two fused passes (sl_opts.coarse_fusion)
+  const bool fused = l > 0 && h->o.coarse_fusion > 0 && l >= h->o.coarse_fusion && h->o.smoother == 0 &&
+                     !h->transposed && h->o.nu1 >= 1 && h->o.nu2 >= 1;
+  if (fused) {
+    const CoarseLev<T> L = lev_view<T>(h, l);
+    if (h->o.nu1 == 1) {
+      launch_coarse_down<T>(L, T(h->o.omega), b, nullptr, cur, cb, nc, s);
+    } else {
+      smooth<T>(h, l, dt, b, cur, other, h->o.nu1, true, s);
+      launch_coarse_down<T>(L, T(h->o.omega), b, cur, nullptr, cb, nc, s);
+    }
+    sl_status st = vcycle<T>(h, l + 1, dt, cb, cx, s);
+    if (st != SL_OK) return st;
+    launch_coarse_up<T>(L, T(h->o.omega), b, cur, cx, nc, other, s);
+    std::swap(cur, other);
+    smooth<T>(h, l, dt, b, cur, other, h->o.nu2 - 1, false, s);
+    if (cur != x) CK(cudaMemcpyAsync(x, cur, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+    return SL_OK;
+  }
   if (h->o.nu1 == 0) launch_fill<T>(cur, N, T(0), s);
   else smooth<T>(h, l, dt, b, cur, other, h->o.nu1, true, s);
   level_op<T>(h, l, OP_RESID, dt, cur, b, br, s);
-  T *cx, *ct, *cr, *cb;
-  vbufs<T>(h->vb[l + 1], &cx, &ct, &cr, &cb);
-  launch_restrict<T>(br, h->cl[l].n, cb, h->cl[l + 1].n, s);
+  launch_restrict<T>(br, h->cl[l].n, cb, nc, s);
   sl_status st = vcycle<T>(h, l + 1, dt, cb, cx, s);
   if (st != SL_OK) return st;
-  launch_prolong_add<T>(cx, h->cl[l + 1].n, cur, h->cl[l].n, s);
+  launch_prolong_add<T>(cx, nc, cur, h->cl[l].n, s);
   smooth<T>(h, l, dt, b, cur, other, h->o.nu2, false, s);
   if (cur != x) CK(cudaMemcpyAsync(x, cur, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CK(cudaGetLastError());
@@ -1595,6 +1617,7 @@ void sl_opts_default(sl_opts *o) {
   o->amg_k_levels = 2;
   o->fine_tma = 1;
   o->smoother = 0;
+  o->coarse_fusion = 3;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -1643,6 +1666,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
     return fail(h, SL_EINVAL, "bad iteration options");
   if (h->o.precond != 0 && h->o.precond != 1) return fail(h, SL_EINVAL, "precond must be 0 or 1");
   if (h->o.smoother != 0 && h->o.smoother != 1) return fail(h, SL_EINVAL, "smoother must be 0 or 1");
+  if (h->o.coarse_fusion < 0) return fail(h, SL_EINVAL, "coarse_fusion must be >= 0");
   if (h->o.precond == 1 && (h->o.nu1 < 1 || h->o.amg_k_levels < 0))
     return fail(h, SL_EINVAL, "the aggregation K-cycle needs nu1 >= 1 and amg_k_levels >= 0");
   h->amg.nu1 = h->o.nu1;
@@ -2194,12 +2218,75 @@ sl_status sl_hjb_recorded_policy(sl_hjb *h, int step, uint8_t *policy_dev, void 
   return SL_OK;
 }
 
-sl_status sl_hjb_level_info(const sl_hjb *h, int level, int *n, long long *explicit_rows, long long *nnz) {
-  if (!h || level < 0 || level >= h->L) return SL_EINVAL;
+sl_status sl_hjb_level_stats(const sl_hjb *h, int level, sl_level_stats *out) {
+  if (!h || !out || level < 0 || level >= h->L) return SL_EINVAL;
   const CoarseBuf &c = h->cl[level];
-  if (n) *n = c.n;
-  if (explicit_rows) *explicit_rows = level == 0 ? 0 : c.nexpl;
-  if (nnz) *nnz = -1;
+  *out = sl_level_stats{};
+  out->n = c.n;
+  if (level == 0) {
+    out->reach = h->halo;
+    out->class_nnz = -1;
+    return SL_OK;
+  }
+  out->reach = c.R;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SL_ECUDA;
+  int nexpl = 0;
+  if (cudaMemcpy(&nexpl, c.d_nexpl, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SL_ECUDA;
+  std::vector<int32_t> cls(size_t(c.m) * c.m);
+  if (cudaMemcpy(cls.data(), c.cls, cls.size() * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SL_ECUDA;
+  // only coefficients of interior columns count: a row next to the boundary may also carry
+  // weights of boundary nodes, which multiply the Dirichlet zero of the correction
+  auto interior = [&](int i1, int i2) { return i1 >= 1 && i1 <= c.m && i2 >= 1 && i2 <= c.m; };
+  for (size_t I = 0; I < cls.size(); ++I) {
+    const int k = cls[I];
+    if (k < 0 || size_t(k) >= c.cnt_host.size()) continue;
+    const int I1 = 1 + int(I % c.m), I2 = 1 + int(I / c.m);
+    for (int t = 0; t < c.cnt_host[k]; ++t) {
+      const int o = c.coff_host[size_t(k) * c.ctmax + t];
+      const int dx = int(int16_t(o & 0xffff)), dy = o >> 16;
+      out->class_nnz += interior(I1 + dx, I2 + dy);
+    }
+  }
+  out->explicit_rows = nexpl;
+  out->explicit_entries = (long long)nexpl * c.win;
+  if (nexpl > 0) {
+    const bool fp64 = h->o.precision == 0;
+    std::vector<int32_t> erow(nexpl);
+    if (cudaMemcpy(erow.data(), c.erow, nexpl * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return SL_ECUDA;
+    std::vector<double> w64;
+    std::vector<float> w32;
+    const int Wd = 2 * c.R + 1;
+    for (int e = 0; e < c.win; ++e) {  // one window entry of every explicit row at a time
+      const int dy = e / Wd - c.R, dx = e % Wd - c.R;
+      cudaError_t err;
+      if (fp64) {
+        w64.resize(nexpl);
+        err = cudaMemcpy(w64.data(), c.ewin64 + size_t(e) * c.cap, nexpl * sizeof(double),
+                         cudaMemcpyDeviceToHost);
+      } else {
+        w32.resize(nexpl);
+        err = cudaMemcpy(w32.data(), c.ewin32 + size_t(e) * c.cap, nexpl * sizeof(float),
+                         cudaMemcpyDeviceToHost);
+      }
+      if (err != cudaSuccess) return SL_ECUDA;
+      for (int q = 0; q < nexpl; ++q) {
+        const bool nz = fp64 ? w64[q] != 0.0 : w32[q] != 0.0f;
+        out->explicit_nnz += nz && interior(erow[q] % c.n + dx, erow[q] / c.n + dy);
+      }
+    }
+  }
+  return SL_OK;
+}
+
+sl_status sl_hjb_level_info(const sl_hjb *h, int level, int *n, long long *explicit_rows, long long *nnz) {
+  sl_level_stats st;
+  const sl_status r = sl_hjb_level_stats(h, level, &st);
+  if (r != SL_OK) return r;
+  if (n) *n = st.n;
+  if (explicit_rows) *explicit_rows = st.explicit_rows;
+  if (nnz) *nnz = level == 0 ? -1 : st.class_nnz + st.explicit_nnz;
   return SL_OK;
 }
 

@@ -360,7 +360,7 @@ constexpr int kClassTabSmemTiles = 256;          // only levels with at most thi
 
 template <typename T>
 __host__ __device__ inline size_t coarse_tile_bytes(int R) {
-  return (size_t(32 + 2 * R) * (kCRowsY + 2 * R) * sizeof(T) + 15) / 16 * 16;
+  return (size_t(coarse_pitch(R)) * (kCRowsY + 2 * R) * sizeof(T) + 15) / 16 * 16;
 }
 
 // Capped at six blocks of 256 threads per SM (40 registers): the explicit rows' unrolled
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(256, 6) k_coarse_op(CoarseLev<T> L, const int 
     using PK = typename ClassTap<T>::Packed;
     T *xs = reinterpret_cast<T *>(smem_raw);
     PK *ts = reinterpret_cast<PK *>(smem_raw + coarse_tile_bytes<T>(L.R));
-    const int R = L.R, SW = 32 + 2 * R, SH = kCRowsY + 2 * R;
+    const int R = L.R, SW = coarse_pitch(R), SH = kCRowsY + 2 * R;
     const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     if (STAB && OP != OP_JACOBI0) {
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(256, 6) k_coarse_op(CoarseLev<T> L, const int 
       stage_window<4, T>(xs, SW, SH, tx, ty, [&](int r, int c) {
         const int g2 = o2 + r, g1 = o1 + c;
         return (g2 >= 0 && g2 < L.n && g1 >= 0 && g1 < L.n) ? x[size_t(g2) * L.n + g1] : T(0);
-      });
+      }, 32 + 2 * R);
       __syncthreads();
     }
     const int I1 = 1 + bx * 32 + tx;
@@ -504,6 +504,332 @@ template void launch_coarse_op<double>(int, const CoarseLev<double> &, const int
                                        const double *, const double *, double *, cudaStream_t, int);
 template void launch_coarse_op<float>(int, const CoarseLev<float> &, const int *, float, const float *,
                                       const float *, float *, cudaStream_t, int);
+
+// ----------------------------------------------------------------------------- fused level passes
+// The V-cycle's passes over one coarse level l >= 1 with the Jacobi smoother, two launches per
+// level instead of five:
+//   k_coarse_down: x = omega D^-1 b (the first pre-smoothing sweep from zero) or x as given,
+//                  r = b - A_l x, and b_{l+1} = R r (full weighting);
+//   k_coarse_up:   v = x + P x_{l+1} (the coarse-grid correction), then one Jacobi sweep
+//                  y = v + omega D^-1 (b - A_l v).
+// A block owns a tile of 32 x TH rows and stages its values plus a halo of R in shared memory,
+// computing the staged values (omega b / d, or x + P x_c) for the halo itself, so no pass
+// needs another block's output.  Class rows sum their taps from the tile; the tile's explicit
+// rows go to a shared list that the whole block then works through in the order of
+// k_coarse_op's explicit blocks (four threads per row, each summing the window
+// rows dy = ylo + p mod 4, then two shuffles), so each value equals that of the one-pass
+// kernels bit for bit.  The restriction needs the residuals of one row and one column past the tile
+// (its last coarse node's full-weighting stencil), which the down pass computes as well.
+
+// Diagonal of interior row (g1, g2): the class table's centre, or the explicit window's.
+template <typename T>
+__device__ __forceinline__ T coarse_diag(const CoarseLev<T> &L, int g1, int g2) {
+  const int k = L.cls[(g2 - 1) * L.m + (g1 - 1)];
+  if (k >= 0) return L.cdiag[k];
+  return L.ewin[size_t(L.R * (2 * L.R + 1) + L.R) * L.cap + (-k - 1)];
+}
+
+template <typename T, int STAB>
+__device__ __forceinline__ T class_sum_staged(const CoarseLev<T> &L, const typename ClassTap<T>::Packed *ts,
+                                              int k, const T *xs, int sidx) {
+  T acc = T(0);
+  const int nt = L.cnt[k];
+  if (STAB) {
+    const typename ClassTap<T>::Packed *tk = ts + k * L.ctmax;
+#pragma unroll 4
+    for (int t = 0; t < nt; ++t) {
+      int off;
+      T w;
+      ClassTap<T>::unpack(tk[t], off, w);
+      acc = fma(w, xs[sidx + off], acc);
+    }
+  } else {
+#pragma unroll 4
+    for (int t = 0; t < nt; ++t) {
+      int off;
+      T w;
+      ClassTap<T>::get(L, k * L.ctmax + t, off, w);
+      acc = fma(w, xs[sidx + off], acc);
+    }
+  }
+  return acc;
+}
+
+// Partial window sum of explicit row `slot`, centre (I1, I2) staged at xs[sidx] (pitch P): the
+// window rows dy = ylo + part, ylo + part + 4, ..., each in ascending dx, as one of the four
+// threads of k_coarse_op's explicit blocks computes it; four threads per row then add their
+// parts with the same two shuffles, so the row's value is that of the one-pass kernel.
+template <typename T, int RR>
+__device__ __forceinline__ T expl_part_staged(const CoarseLev<T> &L, int slot, int I1, int I2, const T *xs,
+                                              int sidx, int P, int part) {
+  const int R = RR > 0 ? RR : L.R, Wd = 2 * R + 1;
+  const int ylo = max(-R, -I2), yhi = min(R, L.n - 1 - I2);
+  const int xlo = max(-R, -I1), xhi = min(R, L.n - 1 - I1);
+  T acc = T(0);
+  for (int dy = ylo + part; dy <= yhi; dy += 4) {
+    const T *wrow = L.ewin + size_t((dy + R) * Wd + R) * L.cap + slot;
+    const T *xrow = xs + sidx + dy * P;
+    if (RR > 0) {
+#pragma unroll
+      for (int dx = -RR; dx <= RR; ++dx)
+        if (dx >= xlo && dx <= xhi) acc = fma(__ldg(wrow + ptrdiff_t(dx) * L.cap), xrow[dx], acc);
+    } else {
+      for (int dx = xlo; dx <= xhi; ++dx) acc = fma(__ldg(wrow + ptrdiff_t(dx) * L.cap), xrow[dx], acc);
+    }
+  }
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T expl_part_staged_any(const CoarseLev<T> &L, int slot, int I1, int I2, const T *xs,
+                                                  int sidx, int P, int part) {
+  switch (L.R) {
+    case 1: return expl_part_staged<T, 1>(L, slot, I1, I2, xs, sidx, P, part);
+    case 2: return expl_part_staged<T, 2>(L, slot, I1, I2, xs, sidx, P, part);
+    case 3: return expl_part_staged<T, 3>(L, slot, I1, I2, xs, sidx, P, part);
+    case 4: return expl_part_staged<T, 4>(L, slot, I1, I2, xs, sidx, P, part);
+    case 5: return expl_part_staged<T, 5>(L, slot, I1, I2, xs, sidx, P, part);
+    case 6: return expl_part_staged<T, 6>(L, slot, I1, I2, xs, sidx, P, part);
+    default: return expl_part_staged<T, 0>(L, slot, I1, I2, xs, sidx, P, part);
+  }
+}
+
+// Shared-memory layout of the fused passes: [class table (STAB)] [tile] [residuals (down)]
+// [explicit list: local row index, slot].
+template <typename T>
+struct FusedSmem {
+  size_t tab, tile, res, list;
+  __host__ __device__ FusedSmem(int R, int TH, int nk, int ctmax, bool stab, bool down) {
+    tab = stab ? (size_t(nk) * ctmax * sizeof(typename ClassTap<T>::Packed) + 15) / 16 * 16 : 0;
+    const int rows = down ? TH + 1 : TH, cols = down ? 33 : 32;
+    tile = (size_t(coarse_pitch(R)) * (rows + 2 * R) * sizeof(T) + 15) / 16 * 16;
+    res = down ? (size_t(rows) * cols * sizeof(T) + 15) / 16 * 16 : 0;
+    list = size_t(rows) * cols * 2 * sizeof(int);
+  }
+  __host__ __device__ size_t total() const { return tab + tile + res + list; }
+};
+
+template <typename T, int STAB>
+__device__ __forceinline__ void stage_class_table(const CoarseLev<T> &L, typename ClassTap<T>::Packed *ts) {
+  if (!STAB) return;
+  using PK = typename ClassTap<T>::Packed;
+  const PK *src = ClassTap<T>::table(L);
+  const int nt_all = L.nk * L.ctmax;
+  for (int i0 = threadIdx.x; i0 < nt_all; i0 += 4 * blockDim.x) {  // four loads, then four stores
+    PK v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + q * blockDim.x;
+      if (i < nt_all) v[q] = src[i];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + q * blockDim.x;
+      if (i < nt_all) ts[i] = v[q];
+    }
+  }
+}
+
+template <typename T, int TH, int STAB, int FROM_ZERO>
+__global__ void __launch_bounds__(256) k_coarse_down(CoarseLev<T> L, int tiles_x, T omega,
+                                                     const T *__restrict__ b, const T *__restrict__ xin,
+                                                     T *__restrict__ xout, T *__restrict__ bc, int nc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int ecount;
+  using PK = typename ClassTap<T>::Packed;
+  constexpr int RW = 33, NQ = (TH + 1) * RW;  // residual rows: the tile plus its ring
+  const int R = L.R, P = coarse_pitch(R);
+  const FusedSmem<T> lay(R, TH, L.nk, L.ctmax, STAB != 0, true);
+  PK *ts = reinterpret_cast<PK *>(smem_raw);
+  T *xs = reinterpret_cast<T *>(smem_raw + lay.tab);
+  T *rs = reinterpret_cast<T *>(smem_raw + lay.tab + lay.tile);
+  int *eq = reinterpret_cast<int *>(smem_raw + lay.tab + lay.tile + lay.res);
+  int *eslot = eq + NQ;
+  const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (threadIdx.x == 0) ecount = 0;
+  stage_class_table<T, STAB>(L, ts);
+  const int o1 = 1 + bx * 32, o2 = 1 + by * TH;
+  // staged node (r, c) is grid node (o1 - R + c, o2 - R + r); boundary and outside nodes are 0
+  stage_window<(TH >= 16 ? 4 : 2), T>(xs, P, TH + 1 + 2 * R, tx, ty, [&](int r, int c) {
+    const int g2 = o2 - R + r, g1 = o1 - R + c;
+    if (g2 < 1 || g2 > L.m || g1 < 1 || g1 > L.m) return T(0);
+    if (FROM_ZERO) return omega * b[size_t(g2) * L.n + g1] / coarse_diag<T>(L, g1, g2);
+    return xin[size_t(g2) * L.n + g1];
+  });
+  __syncthreads();
+  for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+    const int r = q / RW, c = q - r * RW;
+    const int g1 = o1 + c, g2 = o2 + r;
+    T res = T(0);
+    if (g1 <= L.m && g2 <= L.m) {
+      const int sidx = (r + R) * P + c + R;
+      const size_t j = size_t(g2) * L.n + g1;
+      if (FROM_ZERO && r < TH && c < 32) xout[j] = xs[sidx];
+      const int k = L.cls[(g2 - 1) * L.m + (g1 - 1)];
+      if (k < 0) {
+        const int e = atomicAdd(&ecount, 1);
+        eq[e] = q;
+        eslot[e] = -k - 1;
+        continue;
+      }
+      res = b[j] - class_sum_staged<T, STAB>(L, ts, k, xs, sidx);
+    }
+    rs[q] = res;
+  }
+  __syncthreads();
+  // explicit rows: four threads per row (window rows dy = ylo + part mod 4), then two shuffles
+  const int ne4 = 4 * ecount;
+  for (int base = 0; base < ne4; base += blockDim.x) {
+    const int idx = base + threadIdx.x, part = idx & 3;
+    T acc = T(0);
+    int q = 0, g1 = 0, g2 = 0;
+    if (idx < ne4) {
+      q = eq[idx >> 2];
+      const int r = q / RW, c = q - r * RW;
+      g1 = o1 + c;
+      g2 = o2 + r;
+      acc = expl_part_staged_any<T>(L, eslot[idx >> 2], g1, g2, xs, (r + R) * P + c + R, P, part);
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (idx < ne4 && part == 0) rs[q] = b[size_t(g2) * L.n + g1] - acc;
+  }
+  __syncthreads();
+  // full weighting: this tile's coarse nodes I1 = 16 bx + 1 + c1, I2 = (TH / 2) by + 1 + c2 sit at
+  // residual rows 1 + 2 c2, columns 1 + 2 c1
+  constexpr int CH = TH / 2;
+  const int c1 = threadIdx.x & 15, c2 = threadIdx.x >> 4;
+  if (c2 < CH) {
+    const int I1 = 16 * bx + 1 + c1, I2 = CH * by + 1 + c2;
+    if (I1 <= nc - 2 && I2 <= nc - 2) bc[size_t(I2) * nc + I1] = restrict_point<T>(rs + RW + 1, RW, c1, c2);
+  }
+}
+
+template <typename T, int TH, int STAB>
+__global__ void __launch_bounds__(256) k_coarse_up(CoarseLev<T> L, int tiles_x, T omega, const T *__restrict__ b,
+                                                   const T *__restrict__ cur, const T *__restrict__ xc, int nc,
+                                                   T *__restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int ecount;
+  using PK = typename ClassTap<T>::Packed;
+  constexpr int NQ = TH * 32;
+  const int R = L.R, P = coarse_pitch(R), Wd = 2 * R + 1;
+  const FusedSmem<T> lay(R, TH, L.nk, L.ctmax, STAB != 0, false);
+  PK *ts = reinterpret_cast<PK *>(smem_raw);
+  T *xs = reinterpret_cast<T *>(smem_raw + lay.tab);
+  int *eq = reinterpret_cast<int *>(smem_raw + lay.tab + lay.tile);
+  int *eslot = eq + NQ;
+  const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (threadIdx.x == 0) ecount = 0;
+  stage_class_table<T, STAB>(L, ts);
+  const int o1 = 1 + bx * 32, o2 = 1 + by * TH;
+  stage_window<(TH >= 16 ? 4 : 2), T>(xs, P, TH + 2 * R, tx, ty, [&](int r, int c) {
+    const int g2 = o2 - R + r, g1 = o1 - R + c;
+    if (g2 < 1 || g2 > L.m || g1 < 1 || g1 > L.m) return T(0);
+    return cur[size_t(g2) * L.n + g1] + prolong_point<T>(xc, nc, g1, g2);
+  }, 32 + 2 * R);
+  __syncthreads();
+  for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+    const int r = q >> 5, c = q & 31;
+    const int g1 = o1 + c, g2 = o2 + r;
+    if (g1 > L.m || g2 > L.m) continue;
+    const int k = L.cls[(g2 - 1) * L.m + (g1 - 1)];
+    if (k < 0) {
+      const int e = atomicAdd(&ecount, 1);
+      eq[e] = q;
+      eslot[e] = -k - 1;
+      continue;
+    }
+    const int sidx = (r + R) * P + c + R;
+    const size_t j = size_t(g2) * L.n + g1;
+    const T acc = class_sum_staged<T, STAB>(L, ts, k, xs, sidx);
+    y[j] = xs[sidx] + omega * (b[j] - acc) / L.cdiag[k];
+  }
+  __syncthreads();
+  const int ne4 = 4 * ecount;
+  for (int base = 0; base < ne4; base += blockDim.x) {
+    const int idx = base + threadIdx.x, part = idx & 3;
+    T acc = T(0);
+    int slot = 0, sidx = 0;
+    size_t j = 0;
+    if (idx < ne4) {
+      const int q = eq[idx >> 2];
+      slot = eslot[idx >> 2];
+      const int r = q >> 5, c = q & 31;
+      const int g1 = o1 + c, g2 = o2 + r;
+      sidx = (r + R) * P + c + R;
+      j = size_t(g2) * L.n + g1;
+      acc = expl_part_staged_any<T>(L, slot, g1, g2, xs, sidx, P, part);
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (idx < ne4 && part == 0) {
+      const T d = L.ewin[size_t(R * Wd + R) * L.cap + slot];
+      y[j] = xs[sidx] + omega * (b[j] - acc) / d;
+    }
+  }
+}
+
+// Tile height of the fused passes: the tallest of 32, 16, 8 rows that still gives at least
+// 512 tiles (about three per SM); small levels take 8.
+static int fused_tile_rows(int m) {
+  const int tx = (m + 31) / 32;
+  for (int th : {32, 16})
+    if (tx * ((m + th - 1) / th) >= 512) return th;
+  return 8;
+}
+
+template <typename T>
+static bool fused_stab(const CoarseLev<T> &L, int blocks) {
+  const size_t tab_bytes = size_t(L.nk) * L.ctmax * sizeof(typename ClassTap<T>::Packed);
+  return L.nk > 0 && tab_bytes <= kClassTabSmemMax && blocks <= kClassTabSmemTiles;
+}
+
+template <typename T>
+void launch_coarse_down(const CoarseLev<T> &L, T omega, const T *b, const T *xin, T *xout, T *bc, int nc,
+                        cudaStream_t s) {
+  const int th = fused_tile_rows(L.m);
+  const int tx = (L.m + 31) / 32, blocks = tx * ((L.m + th - 1) / th);
+  const bool stab = fused_stab(L, blocks);
+  const size_t bytes = FusedSmem<T>(L.R, th, L.nk, L.ctmax, stab, true).total();
+  const bool z = xin == nullptr;
+  note_launch();
+#define SL_DOWN(TH, ST, Z) \
+  k_coarse_down<T, TH, ST, Z><<<blocks, 256, bytes, s>>>(L, tx, omega, b, xin, xout, bc, nc)
+#define SL_DOWN_TH(TH) \
+  if (stab) { if (z) SL_DOWN(TH, 1, 1); else SL_DOWN(TH, 1, 0); } \
+  else { if (z) SL_DOWN(TH, 0, 1); else SL_DOWN(TH, 0, 0); }
+  if (th == 32) { SL_DOWN_TH(32) }
+  else if (th == 16) { SL_DOWN_TH(16) }
+  else { SL_DOWN_TH(8) }
+#undef SL_DOWN_TH
+#undef SL_DOWN
+}
+
+template <typename T>
+void launch_coarse_up(const CoarseLev<T> &L, T omega, const T *b, const T *cur, const T *xc, int nc, T *y,
+                      cudaStream_t s) {
+  const int th = fused_tile_rows(L.m);
+  const int tx = (L.m + 31) / 32, blocks = tx * ((L.m + th - 1) / th);
+  const bool stab = fused_stab(L, blocks);
+  const size_t bytes = FusedSmem<T>(L.R, th, L.nk, L.ctmax, stab, false).total();
+  note_launch();
+#define SL_UP(TH, ST) k_coarse_up<T, TH, ST><<<blocks, 256, bytes, s>>>(L, tx, omega, b, cur, xc, nc, y)
+  if (th == 32) { if (stab) SL_UP(32, 1); else SL_UP(32, 0); }
+  else if (th == 16) { if (stab) SL_UP(16, 1); else SL_UP(16, 0); }
+  else { if (stab) SL_UP(8, 1); else SL_UP(8, 0); }
+#undef SL_UP
+}
+template void launch_coarse_down<double>(const CoarseLev<double> &, double, const double *, const double *,
+                                         double *, double *, int, cudaStream_t);
+template void launch_coarse_down<float>(const CoarseLev<float> &, float, const float *, const float *, float *,
+                                        float *, int, cudaStream_t);
+template void launch_coarse_up<double>(const CoarseLev<double> &, double, const double *, const double *,
+                                       const double *, int, double *, cudaStream_t);
+template void launch_coarse_up<float>(const CoarseLev<float> &, float, const float *, const float *,
+                                      const float *, int, float *, cudaStream_t);
 
 // ----------------------------------------------------------------------------- V-cycle tail
 // The coarse end of the V-cycle (every level from l0 down, each with at most a few thousand
@@ -754,7 +1080,15 @@ static cudaError_t prepare_coarse_T() {
                       reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI0, 0>),
                       reinterpret_cast<const void *>(k_coarse_op<T, OP_APPLY, 1>),
                       reinterpret_cast<const void *>(k_coarse_op<T, OP_RESID, 1>),
-                      reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI, 1>)};
+                      reinterpret_cast<const void *>(k_coarse_op<T, OP_JACOBI, 1>),
+#define SL_FUSED(TH) \
+  reinterpret_cast<const void *>(k_coarse_down<T, TH, 0, 0>), \
+  reinterpret_cast<const void *>(k_coarse_down<T, TH, 0, 1>), \
+  reinterpret_cast<const void *>(k_coarse_down<T, TH, 1, 0>), \
+  reinterpret_cast<const void *>(k_coarse_down<T, TH, 1, 1>), \
+  reinterpret_cast<const void *>(k_coarse_up<T, TH, 0>), reinterpret_cast<const void *>(k_coarse_up<T, TH, 1>)
+                      SL_FUSED(8), SL_FUSED(16), SL_FUSED(32)};
+#undef SL_FUSED
   for (const void *f : fs) {
     cudaError_t e = allow_dynamic_smem(f);
     if (e != cudaSuccess) return e;

@@ -236,6 +236,11 @@ SL_HD void rap_scatter(T *win, int R, int I1, int I2, int j1, int j2, T rv) {
   }
 }
 
+// Row pitch of a staged coarse-level tile, and the pitch the packed class-table offsets assume:
+// 32 columns plus a halo of R on each side, plus the one column of the residual ring that the
+// fused residual-and-restriction kernel computes beyond its tile.
+SL_HD int coarse_pitch(int R) { return 33 + 2 * R; }
+
 // Full weighting at coarse interior node (I1, I2):
 // b_c(I) = sum_{a in {-1,0,1}^2} w_a1 w_a2 r_f(2I + a), w = (1/4, 1/2, 1/4).
 template <typename T>

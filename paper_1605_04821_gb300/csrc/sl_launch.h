@@ -102,6 +102,17 @@ cudaError_t launch_rap_explicit(int level, const FineTab &tab, const int32_t *fi
 template <typename T>
 void launch_coarse_op(int op, const CoarseLev<T> &L, const int *nexpl_dev, T omega, const T *x,
                       const T *b, T *y, cudaStream_t s, int color = -1);
+
+// Fused coarse-level passes of the Jacobi V-cycle (levels >= 1): down = (x = omega D^-1 b when
+// xin is null, else x = xin) + residual + full-weighting restriction into bc; up = y = one
+// Jacobi sweep from cur + P xc.
+template <typename T>
+void launch_coarse_down(const CoarseLev<T> &L, T omega, const T *b, const T *xin, T *xout, T *bc, int nc,
+                        cudaStream_t s);
+template <typename T>
+void launch_coarse_up(const CoarseLev<T> &L, T omega, const T *b, const T *cur, const T *xc, int nc, T *y,
+                      cudaStream_t s);
+
 // Levels l0 .. L-1 of one V-cycle in a single thread block (x[l0] = M_l0^{-1} b[l0]).
 template <typename T>
 struct TailArgs {

@@ -110,6 +110,41 @@ def test_operators_on_every_level(name, precision):
         assert rel_maxnorm(got, ref) <= tol, f"level {level}"
 
 
+@pytest.mark.parametrize("name", ["s65", "s129"])
+def test_level_stats_describe_the_galerkin_operators(name):
+    """sl_hjb_level_stats against the oracle's R A P matrices: every non-zero lies within the
+    reported reach of its row, and the class and explicit non-zeros cover the oracle's
+    significant entries.  The counts are not compared exactly: an entry that cancels to zero
+    in exact arithmetic is a rounding residue of either sign or an exact zero depending on the
+    order of the Galerkin sums, which differs between the two sides (about 4 % of the entries
+    on the first coarse level of the 65^2 case)."""
+    prob = CASES[name]()
+    s = _solver(prob, precision=0)
+    n = prob.n - 2
+    pol = (np.arange(n)[None, :] // 16 + np.arange(n)[:, None] // 24).ravel() % prob.K
+    s.set_policy(to_dev(pol, torch.uint8))
+    s.build_hierarchy(prob.dt)
+    A, _ = lisl.assemble(prob, pol, prob.g, 0.0, prob.dt)
+    H = mg.galerkin_hierarchy(A, prob.n, s.num_levels())
+    st0 = s.level_stats(0)
+    assert st0["n"] == prob.n and st0["class_nnz"] == -1 and st0["explicit_rows"] == 0
+    for level in range(1, s.num_levels()):
+        st = s.level_stats(level)
+        m = H.n[level] - 2
+        assert st["n"] == H.n[level]
+        assert st["explicit_entries"] == st["explicit_rows"] * (2 * st["reach"] + 1) ** 2
+        assert 0 <= st["explicit_nnz"] <= st["explicit_entries"]
+        Al = H.A[level].tocoo()
+        nz = np.abs(Al.data) > 0
+        r, c = Al.row[nz], Al.col[nz]
+        assert np.all(np.abs(r % m - c % m) <= st["reach"]), level
+        assert np.all(np.abs(r // m - c // m) <= st["reach"]), level
+        got = st["class_nnz"] + st["explicit_nnz"]
+        big = int((np.abs(Al.data) > 1e-12 * np.abs(Al.data).max()).sum())
+        assert big <= got <= 1.1 * nz.sum(), (level, st, big, int(nz.sum()))
+        assert s.level_info(level) == (st["n"], st["explicit_rows"], got)
+
+
 @pytest.mark.parametrize("name", ["c33", "heavy33", "s65", "s129", "cb33"])
 def test_vcycle_matches_oracle(name):
     prob = CASES[name]()
