@@ -398,6 +398,13 @@ def run_ours(args):
         amg = amg_record(slp, prob, dev, stream, args, extra, g)
         torch.cuda.nvtx.range_pop()
 
+    # ---- the plain FP64 configuration (513^2, 33 controls, 64 steps)
+    fp64_513 = None
+    if not args.no_fp64:
+        torch.cuda.nvtx.range_push("fp64_513")
+        fp64_513 = fp64_513_record(slp, W, dev, stream)
+        torch.cuda.nvtx.range_pop()
+
     # ---- two-colour Gauss-Seidel against damped Jacobi on the same steps
     smoother = None
     if not args.no_smoother:
@@ -443,6 +450,7 @@ def run_ours(args):
             "batched": batched,
             "amg": amg,
             "smoother": smoother,
+            "fp64_513": fp64_513,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -539,6 +547,37 @@ def amg_record(slp, prob, dev, stream, args, extra, g):
         torch.cuda.empty_cache()
     out["value"] = out["aggregation_kcycle"]["value"]
     return out
+
+
+def fp64_513_record(slp, W, dev, stream):
+    """The plain FP64 workload: 513 x 513 grid, 33 controls, 64 implicit steps to T = 1, V(2,2)
+    damped Jacobi (omega 0.8), BiCGSTAB to the default tolerance, every step FP64.  The whole
+    march is timed with CUDA events, its first step included (it is part of the workload); the
+    GPU tests compare the same march with the oracle's stored one."""
+    import torch
+    p = W.plain_fp64()
+    s = slp.solver_from_problem(p, device=dev, precision=0, nu1=2, nu2=2, omega=0.8)
+    dt = p.T / p.n_steps
+    u = torch.as_tensor(p.g, dtype=torch.float64, device=dev)
+    s.step(u.clone(), dt, dt)  # builds the graphs of this step size once (not timed)
+    s.reset()                  # the timed march starts like a new handle's
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = {"pi_iters": 0, "krylov_iters": 0}
+    e0.record(stream)
+    for i in range(1, p.n_steps + 1):
+        r = s.step(u, i * dt, dt)
+        for kk in st:
+            st[kk] += r[kk]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    del s
+    torch.cuda.empty_cache()
+    return {"workload": f"{p.n}x{p.n} grid, {p.K} controls, {p.n_steps} steps to T = {p.T}, FP64, "
+                        "V(2,2) damped Jacobi omega 0.8, 8 levels",
+            "value": p.n * p.n * p.n_steps / (ms / 1e3), "unit": UNIT, "ms_total": ms,
+            "ms_per_step": ms / p.n_steps, **st}
 
 
 def smoother_record(slp, prob, dev, stream, args, extra, g):

@@ -59,7 +59,8 @@ typedef enum {
 
 /* Grid of Eq. 1.1 (Section 2.4: "N_x x N_x equispaced nodes"). */
 typedef struct {
-  int nx, ny;                     /* nodes per dimension, boundary included; nx == ny >= 5 */
+  int nx, ny;                     /* nodes per dimension, boundary included; nx == ny, 5 <= nx <= 46340
+                                     (nx^2 < 2^31: grid indices are 32-bit) */
   double x_lo, x_hi, y_lo, y_hi;  /* square cells: x_hi - x_lo == y_hi - y_lo */
 } sl_grid;
 

@@ -1649,6 +1649,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
                              const sl_opts *opts) {
   if (!g || !c || !src) return fail(h, SL_EINVAL, "null argument");
   if (g->nx != g->ny || g->nx < 5) return fail(h, SL_EINVAL, "grid must be square with nx >= 5");
+  if (g->nx > 46340) return fail(h, SL_EINVAL, "nx must be at most 46340 (grid indices are 32-bit)");
   const double hx = (g->x_hi - g->x_lo) / (g->nx - 1), hy = (g->y_hi - g->y_lo) / (g->ny - 1);
   if (!(hx > 0) || std::fabs(hx - hy) > 1e-12 * hx) return fail(h, SL_EINVAL, "cells must be square");
   if (c->K < 1 || c->K > 255) return fail(h, SL_EINVAL, "K must be in 1..255");

@@ -937,9 +937,247 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a) {
   }
 }
 
+// The same tail with every level's vectors and stencils in shared memory.  The block loads the
+// stencils of the tail's levels once per cycle (a few hundred KB from L2), every row as a dense
+// (2R+1)^2 window (a class row's taps scattered into its window, zeros elsewhere); after that
+// every phase reads shared memory only, with the window loops unrolled on the reach, so a
+// phase costs a few hundred cycles instead of the chain of L2 round trips (row class, then taps
+// and values) of the global form.  Each row sums its window in the order of the explicit rows
+// of tail_op (dy, then dx ascending); a class row's added zeros leave its sum unchanged.
+// Launched when the levels fit (launch_vcycle_tail).
+struct TailSmem {
+  int vec[kMaxLevels];  // byte offsets: x, t, r, b (n^2 values each) of level l
+  int win[kMaxLevels];  // windows [e][I] (win * m^2 values)
+  int cls[kMaxLevels];  // row classes (m^2 ints)
+  int bytes;
+};
+
+template <typename T>
+static bool tail_smem_layout(const TailArgs<T> &a, TailSmem &lay, int limit) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 15) / 16 * 16;
+    return o;
+  };
+  for (int l = a.l0; l < a.L; ++l) {
+    const CoarseLev<T> &L = a.lev[l];
+    const size_t N = size_t(L.n) * L.n, m2 = size_t(L.m) * L.m;
+    lay.vec[l] = int(take(4 * N * sizeof(T)));
+    if (l < a.L - 1) {
+      lay.win[l] = int(take(size_t(L.win) * m2 * sizeof(T)));
+      lay.cls[l] = int(take(m2 * sizeof(int)));
+    } else {
+      lay.win[l] = lay.cls[l] = 0;
+    }
+    if (off > size_t(limit)) return false;
+  }
+  lay.bytes = int(off);
+  return true;
+}
+
+template <typename T, int RR>
+__device__ __forceinline__ T stail_window(const T *W, int m2, int I, int Rl, const T *x, int j, int n, int I1,
+                                          int I2) {
+  const int R = RR > 0 ? RR : Rl, Wd = 2 * R + 1;
+  const int ylo = max(-R, -I2), yhi = min(R, n - 1 - I2);
+  const int xlo = max(-R, -I1), xhi = min(R, n - 1 - I1);
+  T acc = T(0);
+  if (RR > 0) {
+#pragma unroll
+    for (int dy = -RR; dy <= RR; ++dy) {
+      if (dy < ylo || dy > yhi) continue;
+      const T *wrow = W + size_t((dy + RR) * Wd + RR) * m2 + I;
+      const T *xrow = x + j + dy * n;
+#pragma unroll
+      for (int dx = -RR; dx <= RR; ++dx)
+        if (dx >= xlo && dx <= xhi) acc = fma(wrow[dx * m2], xrow[dx], acc);
+    }
+  } else {
+    for (int dy = ylo; dy <= yhi; ++dy) {
+      const T *wrow = W + size_t((dy + R) * Wd + R) * m2 + I;
+      const T *xrow = x + j + dy * n;
+      for (int dx = xlo; dx <= xhi; ++dx) acc = fma(wrow[dx * m2], xrow[dx], acc);
+    }
+  }
+  return acc;
+}
+
+template <typename T>
+__device__ void stail_op(const CoarseLev<T> &L, const T *W, int op, T omega, const T *x, const T *b, T *y,
+                         int color) {
+  const int m2 = L.m * L.m, R = L.R, Wd = 2 * R + 1;
+  for (int I = threadIdx.x; I < m2; I += blockDim.x) {
+    const int I1 = 1 + I % L.m, I2 = 1 + I / L.m;
+    const int j = I2 * L.n + I1;
+    if (op != OP_RESID && color >= 0 && ((I1 + I2) & 1) != color) {
+      y[j] = op == OP_JACOBI ? x[j] : T(0);
+      continue;
+    }
+    const T d = W[size_t(R * Wd + R) * m2 + I];
+    if (op == OP_JACOBI0) {
+      y[j] = omega * b[j] / d;
+      continue;
+    }
+    T acc;
+    switch (R) {
+      case 1: acc = stail_window<T, 1>(W, m2, I, R, x, j, L.n, I1, I2); break;
+      case 2: acc = stail_window<T, 2>(W, m2, I, R, x, j, L.n, I1, I2); break;
+      case 3: acc = stail_window<T, 3>(W, m2, I, R, x, j, L.n, I1, I2); break;
+      default: acc = stail_window<T, 0>(W, m2, I, R, x, j, L.n, I1, I2); break;
+    }
+    if (op == OP_RESID) y[j] = b[j] - acc;
+    else y[j] = x[j] + omega * (b[j] - acc) / d;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void stail_smooth(const CoarseLev<T> &L, const T *W, const TailArgs<T> &a, const T *b, T *&c,
+                             T *&o, int sweeps, bool from_zero) {
+  for (int it = 0; it < sweeps; ++it) {
+    if (a.rbgs) {
+      for (int col = 0; col < 2; ++col) {
+        if (from_zero && it == 0 && col == 0) {
+          stail_op<T>(L, W, OP_JACOBI0, a.omega, nullptr, b, c, 0);
+        } else {
+          stail_op<T>(L, W, OP_JACOBI, a.omega, c, b, o, col);
+          T *sw = c; c = o; o = sw;
+        }
+      }
+    } else if (from_zero && it == 0) {
+      stail_op<T>(L, W, OP_JACOBI0, a.omega, nullptr, b, c, -1);
+    } else {
+      stail_op<T>(L, W, OP_JACOBI, a.omega, c, b, o, -1);
+      T *sw = c; c = o; o = sw;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_vcycle_tail_smem(TailArgs<T> a, TailSmem lay) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto vec = [&](int l, int q) {
+    return reinterpret_cast<T *>(smem_raw + lay.vec[l]) + size_t(q) * a.lev[l].n * a.lev[l].n;
+  };
+  auto wins = [&](int l) { return reinterpret_cast<T *>(smem_raw + lay.win[l]); };
+  auto clss = [&](int l) { return reinterpret_cast<int *>(smem_raw + lay.cls[l]); };
+  // 1. zero the vectors (boundary entries stay zero) and the windows; load the row classes
+  for (int l = a.l0; l < a.L; ++l) {
+    const CoarseLev<T> &L = a.lev[l];
+    T *v = vec(l, 0);
+    const int N4 = 4 * L.n * L.n;
+    for (int i = threadIdx.x; i < N4; i += blockDim.x) v[i] = T(0);
+    if (l < a.L - 1) {
+      T *W = wins(l);
+      const int tot = L.win * L.m * L.m;
+      for (int i = threadIdx.x; i < tot; i += blockDim.x) W[i] = T(0);
+      int *C = clss(l);
+      for (int I = threadIdx.x; I < L.m * L.m; I += blockDim.x) C[I] = L.cls[I];
+    }
+  }
+  {
+    const CoarseLev<T> &L = a.lev[a.l0];
+    T *b0 = vec(a.l0, 3);
+    for (int i = threadIdx.x; i < L.n * L.n; i += blockDim.x) b0[i] = a.b[a.l0][i];
+  }
+  __syncthreads();
+  // 2. the stencils: explicit windows copied, class taps scattered; four loads in flight per
+  // thread before their stores
+  for (int l = a.l0; l < a.L - 1; ++l) {
+    const CoarseLev<T> &L = a.lev[l];
+    const int m2 = L.m * L.m, tot = L.win * m2, Wd = 2 * L.R + 1;
+    const int *C = clss(l);
+    T *W = wins(l);
+    for (int i0 = threadIdx.x; i0 < tot; i0 += 4 * blockDim.x) {
+      T v[4];
+      int dst[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int idx = i0 + q * blockDim.x;
+        dst[q] = -1;
+        v[q] = T(0);
+        if (idx < tot) {
+          const int e = idx / m2, I = idx - e * m2;
+          const int c = C[I];
+          if (c < 0) {
+            v[q] = L.ewin[size_t(e) * L.cap + (-c - 1)];
+            dst[q] = idx;
+          } else if (e < L.cnt[c]) {  // tap e of the class table
+            const int o = L.coff[c * L.ctmax + e];
+            const int dx = int(int16_t(o & 0xffff)), dy = o >> 16;
+            v[q] = L.cw[c * L.ctmax + e];
+            dst[q] = ((dy + L.R) * Wd + dx + L.R) * m2 + I;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (dst[q] >= 0) W[dst[q]] = v[q];
+    }
+  }
+  __syncthreads();
+  // 3. the cycle
+  T *cur[kMaxLevels];
+  for (int l = a.l0; l < a.L - 1; ++l) {
+    const CoarseLev<T> &L = a.lev[l];
+    const T *W = wins(l);
+    T *c = vec(l, 0), *o = vec(l, 1), *r = vec(l, 2), *b = vec(l, 3);
+    if (a.nu1 > 0) stail_smooth<T>(L, W, a, b, c, o, a.nu1, true);  // nu1 = 0: x = 0, the zeroed vector
+    stail_op<T>(L, W, OP_RESID, a.omega, c, b, r, -1);
+    const CoarseLev<T> &Cl = a.lev[l + 1];
+    T *bn = vec(l + 1, 3);
+    for (int I = threadIdx.x; I < Cl.m * Cl.m; I += blockDim.x) {
+      const int I1 = 1 + I % Cl.m, I2 = 1 + I / Cl.m;
+      bn[I2 * Cl.n + I1] = restrict_point<T>(r, L.n, I1, I2);
+    }
+    __syncthreads();
+    cur[l] = c;
+  }
+  {  // coarsest: x = A^{-1} b
+    const CoarseLev<T> &Cl = a.lev[a.L - 1];
+    const int N = Cl.m * Cl.m;
+    const T *bc = vec(a.L - 1, 3);
+    T *xc = vec(a.L - 1, 0);
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      T acc = T(0);
+      for (int c = 0; c < N; ++c) acc = fma(__ldg(a.Ainv + size_t(r) * N + c), bc[(1 + c / Cl.m) * Cl.n + 1 + c % Cl.m], acc);
+      xc[(1 + r / Cl.m) * Cl.n + 1 + r % Cl.m] = acc;
+    }
+    __syncthreads();
+    cur[a.L - 1] = xc;
+  }
+  for (int l = a.L - 2; l >= a.l0; --l) {
+    const CoarseLev<T> &L = a.lev[l];
+    const CoarseLev<T> &Cl = a.lev[l + 1];
+    const T *W = wins(l);
+    T *c = cur[l], *o = (c == vec(l, 0)) ? vec(l, 1) : vec(l, 0);
+    for (int I = threadIdx.x; I < L.m * L.m; I += blockDim.x) {
+      const int i1 = 1 + I % L.m, i2 = 1 + I / L.m;
+      c[i2 * L.n + i1] += prolong_point<T>(cur[l + 1], Cl.n, i1, i2);
+    }
+    __syncthreads();
+    stail_smooth<T>(L, W, a, vec(l, 3), c, o, a.nu2, false);
+    cur[l] = c;
+  }
+  const CoarseLev<T> &L = a.lev[a.l0];
+  for (int I = threadIdx.x; I < L.m * L.m; I += blockDim.x) {
+    const int j = (1 + I / L.m) * L.n + 1 + I % L.m;
+    a.x[a.l0][j] = cur[a.l0][j];
+  }
+}
+
 template <typename T>
 void launch_vcycle_tail(const TailArgs<T> &a, cudaStream_t s) {
   note_launch();
+  int dev = 0, optin = 0;
+  TailSmem lay{};
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+      tail_smem_layout<T>(a, lay, optin - 1024)) {
+    k_vcycle_tail_smem<T><<<1, 1024, lay.bytes, s>>>(a, lay);
+    return;
+  }
   k_vcycle_tail<T><<<1, 1024, 0, s>>>(a);
 }
 template void launch_vcycle_tail<double>(const TailArgs<double> &, cudaStream_t);
@@ -1087,7 +1325,8 @@ static cudaError_t prepare_coarse_T() {
   reinterpret_cast<const void *>(k_coarse_down<T, TH, 1, 0>), \
   reinterpret_cast<const void *>(k_coarse_down<T, TH, 1, 1>), \
   reinterpret_cast<const void *>(k_coarse_up<T, TH, 0>), reinterpret_cast<const void *>(k_coarse_up<T, TH, 1>)
-                      SL_FUSED(8), SL_FUSED(16), SL_FUSED(32)};
+                      SL_FUSED(8), SL_FUSED(16), SL_FUSED(32),
+                      reinterpret_cast<const void *>(k_vcycle_tail_smem<T>)};
 #undef SL_FUSED
   for (const void *f : fs) {
     cudaError_t e = allow_dynamic_smem(f);

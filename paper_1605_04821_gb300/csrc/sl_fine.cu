@@ -1268,12 +1268,26 @@ __global__ void k_restrict(const T *__restrict__ rf, int nf, T *__restrict__ bc,
   bc[size_t(I2) * nc + I1] = restrict_point<T>(rf, nf, I1, I2);
 }
 
+// One thread per coarse cell [J1, J1 + 1] x [J2, J2 + 1]: it reads the cell's four coarse
+// values once and updates the fine nodes (2 J1 + a1, 2 J2 + a2), a in {0, 1}, with the
+// weights and the order of additions of prolong_point (the same values bit for bit), instead
+// of each fine node gathering its own one to four coarse values with parity branches.
 template <typename T>
 __global__ void k_prolong_add(const T *__restrict__ xc, int nc, T *__restrict__ xf, int nf) {
-  const int i1 = 1 + blockIdx.x * 32 + threadIdx.x;
-  const int i2 = 1 + blockIdx.y * 8 + threadIdx.y;
-  if (i1 > nf - 2 || i2 > nf - 2) return;
-  xf[size_t(i2) * nf + i1] += prolong_point<T>(xc, nc, i1, i2);
+  const int J1 = blockIdx.x * 32 + threadIdx.x;
+  const int J2 = blockIdx.y * 8 + threadIdx.y;
+  if (J1 > nc - 2 || J2 > nc - 2) return;
+  const T *c0 = xc + size_t(J2) * nc + J1;
+  const T c00 = c0[0], c10 = c0[1], c01 = c0[nc], c11 = c0[nc + 1];
+  const int i1 = 2 * J1, i2 = 2 * J2;
+  T *f0 = xf + size_t(i2) * nf + i1;
+  if (J2 > 0) {  // fine row 2 J2 (row 0 is the boundary)
+    if (J1 > 0) f0[0] += c00;
+    f0[1] += T(0.5) * (c00 + c10);
+  }
+  T *f1 = f0 + nf;  // fine row 2 J2 + 1 <= nf - 2
+  if (J1 > 0) f1[0] += T(0.5) * (c00 + c01);
+  f1[1] += T(0.25) * ((c00 + c10) + (c01 + c11));
 }
 
 template <typename T>
@@ -1284,7 +1298,7 @@ void launch_restrict(const T *rf, int nf, T *bc, int nc, cudaStream_t s) {
 }
 template <typename T>
 void launch_prolong_add(const T *xc, int nc, T *xf, int nf, cudaStream_t s) {
-  dim3 blk(32, 8), grd((nf - 2 + 31) / 32, (nf - 2 + 7) / 8);
+  dim3 blk(32, 8), grd((nc - 1 + 31) / 32, (nc - 1 + 7) / 8);
   note_launch();
   k_prolong_add<T><<<grd, blk, 0, s>>>(xc, nc, xf, nf);
 }

@@ -406,10 +406,20 @@ void launch_add_f32_to_f64(double *x, const float *e, size_t N, cudaStream_t s) 
 
 // Sum of squares and max-abs of one vector: which = 0 stores (||b||^2, ||b||_inf) and the
 // stop threshold; which = 1 stores (||r||^2, ||r||_inf).
+// |a| as an ordered integer: the bit pattern with the sign cleared.  For non-NaN doubles the
+// order of these integers is the order of the magnitudes, so their maximum is the bit pattern of
+// max |a|; every NaN pattern lies above that of infinity.  The maxima below run on the integer
+// pipe: fabs and fmax on doubles would take the narrow FP64 pipe beside the one FMA per value.
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+__device__ __forceinline__ unsigned long long abs_bits(double a) {
+  return static_cast<unsigned long long>(__double_as_longlong(a)) & 0x7fffffffffffffffull;
+}
+
 __global__ void __launch_bounds__(kVecThreads) k_norms(const double *__restrict__ a, size_t N, int which,
                                                        BicgScalars *S, double *partials,
                                                        unsigned *counter) {
-  double s2 = 0.0, mx = 0.0;
+  double s2 = 0.0;
+  unsigned long long mb = 0;
   const size_t st = size_t(gridDim.x) * blockDim.x;
   for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
     double av[kU];
@@ -419,11 +429,12 @@ __global__ void __launch_bounds__(kVecThreads) k_norms(const double *__restrict_
     for (int u = 0; u < kU; ++u) {
       if (i0 + u * st < N) {
         s2 = fma(av[u], av[u], s2);
-        mx = fmax(mx, fabs(av[u]));
-        if (!(av[u] == av[u])) mx = INFINITY;
+        mb = max(mb, abs_bits(av[u]));
       }
     }
   }
+  // max |a|, or infinity when a NaN was seen
+  double mx = mb > kInfBits ? INFINITY : __longlong_as_double(static_cast<long long>(mb));
   s2 = warp_sum(s2);
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __shared__ double ss[kVecThreads / 32], sm[kVecThreads / 32];
@@ -478,8 +489,11 @@ __global__ void __launch_bounds__(kVecThreads) k_maxabs_diff(const double *__res
                                                              const double *__restrict__ b, int n,
                                                              double *out, unsigned *counter,
                                                              double *partials) {
-  double d = 0.0, x = 0.0;
-  const size_t N = size_t(n) * n;
+  // maxima as ordered bit patterns (abs_bits): a NaN difference or value is skipped, as fmax
+  // skips it, and a NaN in a sets d to infinity
+  unsigned long long db = 0, xb = 0;
+  bool a_nan = false;
+  const size_t N = size_t(n) * n;  // < 2^31 (sl_hjb_create limits n)
   const size_t st = size_t(gridDim.x) * blockDim.x;
   for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
     double av[kU], bv[kU];
@@ -493,13 +507,16 @@ __global__ void __launch_bounds__(kVecThreads) k_maxabs_diff(const double *__res
     for (int u = 0; u < kU; ++u) {
       const size_t i = i0 + u * st;
       if (i >= N) continue;
-      const int i1 = int(i % n), i2 = int(i / n);
-      if (i1 == 0 || i2 == 0 || i1 == n - 1 || i2 == n - 1) continue;
-      d = fmax(d, fabs(av[u] - bv[u]));
-      x = fmax(x, fabs(av[u]));
-      if (!(av[u] == av[u])) d = INFINITY;
+      const unsigned i2 = unsigned(i) / unsigned(n), i1 = unsigned(i) - i2 * unsigned(n);
+      if (i1 == 0 || i2 == 0 || i1 == unsigned(n) - 1 || i2 == unsigned(n) - 1) continue;
+      const unsigned long long dd = abs_bits(av[u] - bv[u]), aa = abs_bits(av[u]);
+      if (dd <= kInfBits) db = max(db, dd);
+      if (aa <= kInfBits) xb = max(xb, aa);
+      else a_nan = true;
     }
   }
+  double d = a_nan ? INFINITY : __longlong_as_double(static_cast<long long>(db));
+  double x = __longlong_as_double(static_cast<long long>(xb));
   for (int o = 16; o > 0; o >>= 1) {
     d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
     x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));

@@ -93,3 +93,31 @@ def test_march_fused_equals_unfused(precision):
         outs.append((u, st))
     assert torch.equal(outs[0][0], outs[1][0])
     assert outs[0][1]["krylov_iters"] == outs[1][1]["krylov_iters"]
+
+
+@pytest.mark.parametrize("n", [129, 513])
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_vcycle_tail_matches_level_by_level_cycle(n, smoother):
+    """The single-block tail (levels of at most 1024 rows; in shared memory when they fit, as
+    here) against the same levels run one launch per operation: equal to FP32 rounding (the
+    explicit rows sum their windows in another order)."""
+    S = _lib()
+    prob = W.scaled(n, 17, 4, seed=n + 1)
+    pol = to_dev(_policy(n - 2, prob.K, n), torch.uint8)
+    rng = np.random.default_rng(n)
+    b = np.zeros((n, n))
+    b[1:-1, 1:-1] = rng.standard_normal((n - 2, n - 2))
+    out = []
+    for tail in (1024, 0):
+        kw = dict(omega=1.0) if smoother == 1 else {}
+        s = S.solver_from_problem(prob, precision=1, smoother=smoother, coarse_tail_rows=tail, **kw)
+        s.set_policy(pol)
+        s.build_hierarchy(prob.dt)
+        x = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+        s.vcycle(to_dev(b, torch.float32), x)
+        torch.cuda.synchronize()
+        out.append(x.double())
+        s.close()
+    a, c = out
+    assert torch.isfinite(a).all()
+    assert float((a - c).abs().max() / c.abs().max()) <= 1e-5
