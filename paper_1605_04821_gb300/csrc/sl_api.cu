@@ -57,7 +57,7 @@ struct IterGraph {  // one captured BiCGSTAB iteration
 struct DevStepGraph {
   cudaGraphExec_t exec = nullptr;
   double dt = -1.0;
-  long long k_step = 0, k_imp0 = 0, k_pi = 0, k_rebuild = 0, k_ir = 0, k_enter = 0, k_kry = 0,
+  long long k_step = 0, k_imp0 = 0, k_pre = 0, k_pi = 0, k_rebuild = 0, k_ir = 0, k_enter = 0, k_kry = 0,
             k_ok = 0;
 };
 
@@ -887,7 +887,8 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
   CK(cudaMemcpyAsync(h->X, u, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   sl_status r = coef(h, t, h->X, s);
   if (r != SL_OK) return r;
-  if (!h->have_policy) {
+  const bool first_improve = !h->have_policy;
+  if (first_improve) {
     long long ch = 0;
     r = improve(h, h->X, &ch, s);
     if (r != SL_OK) return r;
@@ -899,6 +900,14 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
     // first linear solve starts from 2 U^{n-1} - U^{n-2} (interior; psi(t_n) stays on the boundary)
     launch_extrapolate(h->X, h->Uprev, h->Uprev2, h->n, s);
     CK(cudaGetLastError());
+  }
+  if (!first_improve && h->o.howard_init == 1) {
+    // the previous step's policy, improved at this step's first iterate
+    long long ch = 0;
+    r = improve(h, h->X, &ch, s);
+    if (r != SL_OK) return r;
+    h->changes_since_build += ch;
+    if (st) st->policy_changes += ch;
   }
   h->have_prev2 = h->o.extrapolate != 0;
   h->prev_t = t;
@@ -1204,10 +1213,12 @@ sl_status cap_pi_body(sl_hjb *h, double dt, cudaStream_t s, int depth, long long
 sl_status cap_step_body(sl_hjb *h, double dt, cudaStream_t s, int depth, long long *nested,
                         DevStepGraph &G, const double *tau_table) {
   const size_t N = NN(h, 0);
-  cudaGraphConditionalHandle him, hpi;
+  cudaGraphConditionalHandle him, hpre, hpi;
   CK(new_cond_handle(s, &him));
+  CK(new_cond_handle(s, &hpre));
   CK(new_cond_handle(s, &hpi));
-  launch_ctl_step_begin(h->ctl, tau_table, h->nq + h->npsi, h->d_tau, h->o.extrapolate, him, hpi, s);
+  launch_ctl_step_begin(h->ctl, tau_table, h->nq + h->npsi, h->d_tau, h->o.extrapolate, h->o.howard_init, him,
+                        hpre, hpi, s);
   CK(cudaMemcpyAsync(h->X, h->Uprev, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   launch_coef(h->G, h->nf, h->nq, h->d_tau, h->Psi, h->npsi, h->d_tau + h->nq, h->n, h->F, h->F32,
               h->X, h->Xb, s);
@@ -1223,6 +1234,15 @@ sl_status cap_step_body(sl_hjb *h, double dt, cudaStream_t s, int depth, long lo
   if (st != SL_OK) return st;
   CK(cudaMemcpyAsync(h->Xpi, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   launch_extrapolate_ctl(h->X, h->Uprev, h->Uprev2, h->n, h->ctl, s);
+  st = add_cond(h, s, depth, hpre, cudaGraphCondTypeIf, &G.k_pre, &t,
+                [&](cudaStream_t sb, int, long long *) -> sl_status {
+                  const sl_status r = cap_improve(h, sb);
+                  if (r != SL_OK) return r;
+                  launch_ctl_preimproved(h->ctl, h->d_changes, h->d_flags, hpi, sb);
+                  return SL_OK;
+                });
+  *nested += t;
+  if (st != SL_OK) return st;
   st = add_cond(h, s, depth, hpi, cudaGraphCondTypeWhile, &G.k_pi, &t,
                 [&](cudaStream_t sb, int d, long long *nest) -> sl_status {
                   return cap_pi_body(h, dt, sb, d, nest, G, hpi);
@@ -1241,7 +1261,8 @@ bool dev_step_ok(const sl_hjb *h) {
 
 // Kernels one step graph launch ran, from the device's loop counts.
 long long dev_kernels(const DevStepGraph &G, const DevCtl &c) {
-  return G.k_step * c.c_steps + G.k_imp0 * c.c_improve0 + G.k_pi * c.c_pibody + G.k_rebuild * c.c_rebuild +
+  return G.k_step * c.c_steps + G.k_imp0 * c.c_improve0 + G.k_pre * c.c_pre + G.k_pi * c.c_pibody +
+         G.k_rebuild * c.c_rebuild +
          G.k_ir * c.c_ir + G.k_enter * c.c_enter + G.k_kry * c.c_kry + G.k_ok * c.c_ok;
 }
 
@@ -1618,6 +1639,7 @@ void sl_opts_default(sl_opts *o) {
   o->fine_tma = 1;
   o->smoother = 0;
   o->coarse_fusion = 3;
+  o->howard_init = 1;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -1668,6 +1690,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   if (h->o.precond != 0 && h->o.precond != 1) return fail(h, SL_EINVAL, "precond must be 0 or 1");
   if (h->o.smoother != 0 && h->o.smoother != 1) return fail(h, SL_EINVAL, "smoother must be 0 or 1");
   if (h->o.coarse_fusion < 0) return fail(h, SL_EINVAL, "coarse_fusion must be >= 0");
+  if (h->o.howard_init != 0 && h->o.howard_init != 1) return fail(h, SL_EINVAL, "howard_init must be 0 or 1");
   if (h->o.precond == 1 && (h->o.nu1 < 1 || h->o.amg_k_levels < 0))
     return fail(h, SL_EINVAL, "the aggregation K-cycle needs nu1 >= 1 and amg_k_levels >= 0");
   h->amg.nu1 = h->o.nu1;

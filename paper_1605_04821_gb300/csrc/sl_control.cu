@@ -49,8 +49,8 @@ void launch_ctl_march_begin(DevCtl *c, int nsteps, int extrap_first, int need_im
 // table the host filled for every step, and only the march's first step may start without a
 // policy or without extrapolation.
 __global__ void k_ctl_step_begin(DevCtl *c, const double *tau_table, int ntau, double *d_tau,
-                                 int extrap_opt, cudaGraphConditionalHandle improve0,
-                                 cudaGraphConditionalHandle pi) {
+                                 int extrap_opt, int howard_init, cudaGraphConditionalHandle improve0,
+                                 cudaGraphConditionalHandle pre, cudaGraphConditionalHandle pi) {
   if (tau_table) {
     const int st = c->step;
     for (int q = 0; q < ntau; ++q) d_tau[q] = tau_table[size_t(st - 1) * ntau + q];
@@ -60,13 +60,35 @@ __global__ void k_ctl_step_begin(DevCtl *c, const double *tau_table, int ntau, d
   c->pi_it = 0;
   c->c_steps += 1;
   cudaGraphSetConditional(improve0, c->need_improve ? 1u : 0u);
+  // a step that keeps the previous policy improves it at its first iterate (howard_init 1)
+  cudaGraphSetConditional(pre, (howard_init && !c->need_improve && c->status == SL_OK) ? 1u : 0u);
   cudaGraphSetConditional(pi, c->status == SL_OK ? 1u : 0u);
 }
 void launch_ctl_step_begin(DevCtl *c, const double *tau_table, int ntau, double *d_tau, int extrap_opt,
-                           cudaGraphConditionalHandle improve0, cudaGraphConditionalHandle pi,
-                           cudaStream_t s) {
+                           int howard_init, cudaGraphConditionalHandle improve0,
+                           cudaGraphConditionalHandle pre, cudaGraphConditionalHandle pi, cudaStream_t s) {
   note_launch();
-  k_ctl_step_begin<<<1, 1, 0, s>>>(c, tau_table, ntau, d_tau, extrap_opt, improve0, pi);
+  k_ctl_step_begin<<<1, 1, 0, s>>>(c, tau_table, ntau, d_tau, extrap_opt, howard_init, improve0, pre, pi);
+}
+
+// After the improvement at a step's first iterate: its changes count toward the rebuild test;
+// a NaN stops the step before its Howard loop.
+__global__ void k_ctl_preimproved(DevCtl *c, const unsigned long long *changes, const int *flags,
+                                  cudaGraphConditionalHandle pi) {
+  c->c_pre += 1;
+  if (*flags & 1) {
+    c->status = SL_ENAN;
+    cudaGraphSetConditional(pi, 0u);
+    return;
+  }
+  const long long ch = (long long)*changes;
+  c->changes_since_build += ch;
+  c->c_changes += ch;
+}
+void launch_ctl_preimproved(DevCtl *c, const unsigned long long *changes, const int *flags,
+                            cudaGraphConditionalHandle pi, cudaStream_t s) {
+  note_launch();
+  k_ctl_preimproved<<<1, 1, 0, s>>>(c, changes, flags, pi);
 }
 
 // After the first improvement of a march (the policy has changed wholesale).

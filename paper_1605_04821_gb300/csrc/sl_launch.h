@@ -262,6 +262,7 @@ struct DevCtl {
   long long c_steps, c_improve0, c_pibody, c_pi, c_rebuild, c_ir, c_enter, c_kry, c_ok, c_changes;
   int nexpl[16];         // explicit rows of each level after the last rebuild in the graph
   int tma_err;           // a bounded wait of the TMA fine operator gave up (FineTab::tma_err)
+  long long c_pre;       // improvements at a step's first iterate (sl_opts.howard_init 1)
 };
 
 // Explicit-row counts of the coarse levels, gathered into DevCtl::nexpl (levels 1 .. L-1).
@@ -284,8 +285,10 @@ void launch_ctl_step_prep(DevCtl *c, const StepPrep &p, double *d_tau, cudaStrea
 void launch_ctl_march_begin(DevCtl *c, int nsteps, int extrap_first, int need_improve_first,
                             cudaGraphConditionalHandle march, cudaStream_t s);
 void launch_ctl_step_begin(DevCtl *c, const double *tau_table, int ntau, double *d_tau, int extrap_opt,
-                           cudaGraphConditionalHandle improve0, cudaGraphConditionalHandle pi,
-                           cudaStream_t s);
+                           int howard_init, cudaGraphConditionalHandle improve0,
+                           cudaGraphConditionalHandle pre, cudaGraphConditionalHandle pi, cudaStream_t s);
+void launch_ctl_preimproved(DevCtl *c, const unsigned long long *changes, const int *flags,
+                            cudaGraphConditionalHandle pi, cudaStream_t s);
 void launch_ctl_improved0(DevCtl *c, cudaStream_t s);
 void launch_extrapolate_ctl(double *X, const double *U, const double *V, int n, const DevCtl *c,
                             cudaStream_t s);

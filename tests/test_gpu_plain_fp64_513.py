@@ -7,8 +7,11 @@ here) is stored in tests/golden/plain_fp64_513.npz by tests/golden/make_plain_fp
 which calls only the oracle.  Checks, element by element: U after step 1 and at t = T to 1e-10
 relative max-norm; the policies after step 1 and at T equal up to near-ties within 1e-12
 (judged with the oracle's control values at the nodes where they differ); the Howard
-iteration count of every step.  At 513^2 the stencil offsets reach 3.4-3.8 cells, so the
-truncation band of Section 2.1 is exercised along the whole boundary.
+iteration count of every step (with sl_opts.howard_init = 0, the oracle's initial policy).
+At 513^2 the stencil offsets reach 3.4-3.8 cells, so the truncation band of Section 2.1 is
+exercised along the whole boundary.  A second march with the default howard_init = 1 (each
+step's policy first improved at its extrapolated first iterate) must reach the same U(T) and
+policy, in no more Howard iterations in total.
 """
 import os
 
@@ -49,7 +52,9 @@ def test_plain_fp64_513_matches_the_oracle_march():
     S.load()
     gold = np.load(GOLD)
     p = W.plain_fp64()
-    sol = S.solver_from_problem(p, precision=0, nu1=2, nu2=2, omega=0.8)
+    # howard_init 0: each step starts from the previous step's policy, as the oracle's march
+    # does, so that the Howard counts can be compared step by step
+    sol = S.solver_from_problem(p, precision=0, nu1=2, nu2=2, omega=0.8, howard_init=0)
     assert sol.num_levels() == 8
     u = to_dev(p.g)
     m = p.n - 2
@@ -73,3 +78,23 @@ def test_plain_fp64_513_matches_the_oracle_march():
                                 gold["policy_T"].astype(np.int64))
     assert ok, f"t = T: {nd} policy entries differ beyond the tie window"
     assert pis == [int(x) for x in gold["pi_iters"]]
+
+
+def test_plain_fp64_513_predictor_start_reaches_the_same_march():
+    if not os.path.exists(GOLD):
+        pytest.skip("tests/golden/plain_fp64_513.npz not generated")
+    import paper_1605_04821_gb300 as S
+    S.load()
+    gold = np.load(GOLD)
+    p = W.plain_fp64()
+    sol = S.solver_from_problem(p, precision=0, nu1=2, nu2=2, omega=0.8, howard_init=1)
+    u = to_dev(p.g)
+    m = p.n - 2
+    pol = torch.empty(m * m, dtype=torch.uint8, device="cuda")
+    st = sol.solve(u, 0.0, p.T, p.n_steps, policy_out=pol)
+    sol.close()
+    assert rel_maxnorm(u.cpu().numpy(), gold["U_T"]) <= TOL_FP64
+    ok, nd = _policies_agree_at(p, gold["U_T"], p.T, pol.cpu().numpy().astype(np.int64),
+                                gold["policy_T"].astype(np.int64))
+    assert ok, f"t = T: {nd} policy entries differ beyond the tie window"
+    assert st["pi_iters"] <= int(gold["pi_iters"].sum())
