@@ -198,14 +198,19 @@ typedef struct {
                            and its halo cost more than the launches saved) the one-pass kernels
                            are faster. */
   int howard_init;      /* initial policy of each implicit step's Howard iteration after the first
-                           step (the first step improves on U^0): 1 (default): the previous step's
-                           final policy improved at the step's first iterate (2 U^{n-1} - U^{n-2}
-                           when extrapolating, else U^{n-1}), which already follows most of the
-                           switching fronts that move during the step; 0: the previous step's
-                           final policy as it is.  Howard's iteration converges to the same
-                           discrete solution from either (the stop rule is unchanged); 1 usually
-                           takes one linear solve fewer per step at the cost of one policy
-                           improvement. */
+                           step (the first step improves on U^0): 0 (default): the previous step's
+                           final policy; 1: that policy improved at the step's first iterate
+                           (2 U^{n-1} - U^{n-2} when extrapolating, else U^{n-1}).  Howard's
+                           iteration converges to the same discrete solution from either (the
+                           stop rule is unchanged); 1 saves a linear solve in the steps whose
+                           switching fronts the extrapolation predicts, at the cost of one policy
+                           improvement in every step. */
+  double howard_loose_tol; /* > 0: the first linear solve of each step's Howard iteration stops at
+                           this relative residual instead of krylov_tol (it only has to place the
+                           switching fronts for the next improvement); an iterate solved this
+                           loosely never ends the iteration, so the step's last solve is always at
+                           krylov_tol and its policy is the improvement of its result.  Default
+                           1e-7; 0: every solve at krylov_tol.  At least krylov_tol. */
 } sl_opts;
 
 typedef struct {
@@ -225,7 +230,8 @@ typedef struct {
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
  * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
- * extrapolate 1, precond 0, amg_k_levels 2, smoother 0, fine_tma 1, coarse_fusion 3, howard_init 1. */
+ * extrapolate 1, precond 0, amg_k_levels 2, smoother 0, fine_tma 1, coarse_fusion 3, howard_init 0,
+ * howard_loose_tol 1e-7. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every

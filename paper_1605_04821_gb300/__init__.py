@@ -66,7 +66,8 @@ class SlOpts(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("coarse_tail_rows", ctypes.c_int),
                 ("extrapolate", ctypes.c_int), ("precond", ctypes.c_int), ("amg_k_levels", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("fine_tma", ctypes.c_int),
-                ("coarse_fusion", ctypes.c_int), ("howard_init", ctypes.c_int)]
+                ("coarse_fusion", ctypes.c_int), ("howard_init", ctypes.c_int),
+                ("howard_loose_tol", ctypes.c_double)]
 
 
 class SlInstance(ctypes.Structure):

@@ -137,6 +137,10 @@ struct sl_hjb {
   bool transposed = false;      // level operators act as A_l^T (backward solves)
   int *chunk_scratch = nullptr; // classification counts / offsets
   int tail_l0 = 0;              // first level run by the single-block V-cycle tail (0: none)
+  unsigned char *tail_img = nullptr;  // the tail levels' stencils packed for the shared-memory tail
+  size_t tail_img_bytes = 0;          // its size (0: the tail runs from global memory)
+  size_t tail_img_cap = 0;            // bytes allocated
+  double ls_tol = 0.0;                // > 0: the tolerance of the next linear_solve (else krylov_tol)
   cudaStream_t cap_stream = nullptr;
   // adjoint: fine A^T (CSR), gradient tables and the recorded forward march
   int32_t *t_rowptr = nullptr, *t_col = nullptr;
@@ -462,6 +466,8 @@ sl_status build_class_tables(sl_hjb *h, double dt) {
   return SL_OK;
 }
 
+void tail_pack(sl_hjb *h, cudaStream_t s);
+
 template <typename T>
 sl_status build_hierarchy_T(sl_hjb *h, double dt, cudaStream_t s) {
   for (int l = 1; l < h->L; ++l) {
@@ -480,6 +486,7 @@ sl_status build_hierarchy_T(sl_hjb *h, double dt, cudaStream_t s) {
   CoarseLev<T> cv = lev_view<T>(h, lc);
   launch_coarsest_setup<T>(lc, h->tab, h->policy, T(dt), cv, lc == 0 ? h->d_off : h->cl[lc].coff,
                            h->cwork, pick<T>(h->Ainv64, h->Ainv32), s);
+  tail_pack(h, s);
   CK(cudaGetLastError());
   return SL_OK;
 }
@@ -602,24 +609,58 @@ void vbufs<float>(VBuf &v, float **x, float **t, float **r, float **b) {
   *x = v.x32; *t = v.t32; *r = v.r32; *b = v.b32;
 }
 
+// The arguments of the single-block V-cycle tail from level l0 = h->tail_l0 down.
+template <typename T>
+TailArgs<T> tail_args(sl_hjb *h) {
+  TailArgs<T> a{};
+  const int l = h->tail_l0;
+  a.l0 = l;
+  a.L = h->L;
+  a.nu1 = h->o.nu1;
+  a.nu2 = h->o.nu2;
+  a.rbgs = h->o.smoother == 1 ? 1 : 0;
+  a.omega = T(h->o.omega);
+  for (int q = l; q < h->L; ++q) {
+    a.lev[q] = lev_view<T>(h, q);
+    vbufs<T>(h->vb[q], &a.x[q], &a.t[q], &a.r[q], &a.b[q]);
+  }
+  a.Ainv = pick<T>(h->Ainv64, h->Ainv32);
+  a.img = h->tail_img_bytes ? reinterpret_cast<const T *>(h->tail_img) : nullptr;
+  return a;
+}
+
+// Packs the tail levels' stencils of the current hierarchy for the shared-memory tail; every
+// path that builds the hierarchy calls this at its end.
+void tail_pack(sl_hjb *h, cudaStream_t s) {
+  // before the first hierarchy the class tables do not exist yet: nothing to pack
+  if (h->tail_l0 <= 0 || h->tail_img_bytes == 0 || !h->class_valid) return;
+  if (h->o.precision == 0) launch_tail_pack<double>(tail_args<double>(h), reinterpret_cast<double *>(h->tail_img), s);
+  else launch_tail_pack<float>(tail_args<float>(h), reinterpret_cast<float *>(h->tail_img), s);
+}
+
+// Room for the packed tail stencils (sizes only grow); none when the tail's levels do not fit in
+// one block's shared memory.
+sl_status alloc_tail_image(sl_hjb *h) {
+  h->tail_img_bytes = 0;
+  if (h->tail_l0 <= 0) return SL_OK;
+  const size_t need = h->o.precision == 0 ? tail_image_bytes<double>(tail_args<double>(h))
+                                          : tail_image_bytes<float>(tail_args<float>(h));
+  if (need == 0) return SL_OK;
+  if (need > h->tail_img_cap) {
+    AL(h->tail_img, need);
+    h->tail_img_cap = need;
+  }
+  h->tail_img_bytes = need;
+  return SL_OK;
+}
+
 // x = M_l^{-1} b: V(nu1, nu2) from a zero initial guess, exact solve on the coarsest level.
 template <typename T>
 sl_status vcycle(sl_hjb *h, int l, double dt, const T *b, T *x, cudaStream_t s) {
   const size_t N = NN(h, l);
   if (l > 0 && l == h->tail_l0 && l < h->L - 1 && !h->transposed) {
     // coarse end of the cycle in one thread block; b and x are this level's own buffers
-    TailArgs<T> a{};
-    a.l0 = l;
-    a.L = h->L;
-    a.nu1 = h->o.nu1;
-    a.nu2 = h->o.nu2;
-    a.rbgs = h->o.smoother == 1 ? 1 : 0;
-    a.omega = T(h->o.omega);
-    for (int q = l; q < h->L; ++q) {
-      a.lev[q] = lev_view<T>(h, q);
-      vbufs<T>(h->vb[q], &a.x[q], &a.t[q], &a.r[q], &a.b[q]);
-    }
-    a.Ainv = pick<T>(h->Ainv64, h->Ainv32);
+    const TailArgs<T> a = tail_args<T>(h);
     if (b != a.b[l] || x != a.x[l]) return fail(h, SL_EINVAL, "V-cycle tail called on foreign buffers");
     launch_vcycle_tail<T>(a, s);
     CK(cudaGetLastError());
@@ -824,7 +865,7 @@ sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
   CK(cudaGetLastError());
   double *X = h->transposed ? h->mu : h->X;
   KBuf &k = h->kb;
-  const double tol = h->o.krylov_tol;
+  const double tol = h->ls_tol > 0.0 ? h->ls_tol : h->o.krylov_tol;
   double tolk = tol;   // threshold handed to BiCGSTAB's recurrence
   int total = 0;
   const bool fp64 = h->o.precision == 0;
@@ -930,7 +971,11 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
       }
     }
     double ts = now_ms();
+    // the first solve of the iteration at howard_loose_tol when that is set
+    const bool loose = h->o.howard_loose_tol > 0.0 && it == 1;
+    h->ls_tol = loose ? h->o.howard_loose_tol : 0.0;
     r = linear_solve(h, dt, st, s);
+    h->ls_tol = 0.0;
     if (st) st->t_solve_ms += now_ms() - ts;
     if (r != SL_OK) return r;
     if (h->rec_slot)  // the policy that defines A_n for the adjoint
@@ -950,7 +995,7 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
     }
     if (!std::isfinite(h->h_maxd[0])) return fail(h, SL_ENAN, "non-finite iterate");
     const bool small = h->h_maxd[0] <= h->o.pi_tol * std::max(1.0, h->h_maxd[1]);
-    if (ch == 0 || small) {
+    if ((ch == 0 || small) && !loose) {  // a loosely solved iterate is solved again, tightly
       CK(cudaMemcpyAsync(u, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       if (pol_out)
         CK(cudaMemcpyAsync(pol_out, h->policy, size_t(h->m) * h->m, cudaMemcpyDeviceToDevice, s));
@@ -1069,6 +1114,7 @@ sl_status cap_hierarchy_T(sl_hjb *h, double dt, cudaStream_t s) {
   CoarseLev<T> cv = lev_view<T>(h, lc);
   launch_coarsest_setup<T>(lc, h->tab, h->policy, T(dt), cv, lc == 0 ? h->d_off : h->cl[lc].coff,
                            h->cwork, pick<T>(h->Ainv64, h->Ainv32), s);
+  tail_pack(h, s);
   CK(cudaGetLastError());
   return SL_OK;
 }
@@ -1110,7 +1156,7 @@ sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long
                    h->SW, s, std::max(1, h->cl[0].R));
   cudaGraphConditionalHandle hir;
   CK(new_cond_handle(s, &hir));
-  launch_ctl_ls_begin(h->ctl, h->o.krylov_tol, hir, s);
+  launch_ctl_ls_begin(h->ctl, h->o.krylov_tol, h->o.howard_loose_tol, hir, s);
   const int rounds = fp64 ? 12 : h->o.ir_max + 1;
   long long tot = 0;
   const sl_status st = add_cond(
@@ -1639,7 +1685,8 @@ void sl_opts_default(sl_opts *o) {
   o->fine_tma = 1;
   o->smoother = 0;
   o->coarse_fusion = 3;
-  o->howard_init = 1;
+  o->howard_init = 0;
+  o->howard_loose_tol = 1e-7;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -1691,6 +1738,8 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   if (h->o.smoother != 0 && h->o.smoother != 1) return fail(h, SL_EINVAL, "smoother must be 0 or 1");
   if (h->o.coarse_fusion < 0) return fail(h, SL_EINVAL, "coarse_fusion must be >= 0");
   if (h->o.howard_init != 0 && h->o.howard_init != 1) return fail(h, SL_EINVAL, "howard_init must be 0 or 1");
+  if (!(h->o.howard_loose_tol >= 0.0) || (h->o.howard_loose_tol > 0.0 && h->o.howard_loose_tol < h->o.krylov_tol))
+    return fail(h, SL_EINVAL, "howard_loose_tol must be 0 or at least krylov_tol");
   if (h->o.precond == 1 && (h->o.nu1 < 1 || h->o.amg_k_levels < 0))
     return fail(h, SL_EINVAL, "the aggregation K-cycle needs nu1 >= 1 and amg_k_levels >= 0");
   h->amg.nu1 = h->o.nu1;
@@ -1955,6 +2004,10 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
     AL(h->chunk_scratch, 2 * ((m1 * m1 + 255) / 256) + 2);
   }
   set_tail(h);
+  {
+    const sl_status ts = alloc_tail_image(h);
+    if (ts != SL_OK) return ts;
+  }
   const int mc = h->cl[h->L - 1].m;
   AL(h->cwork, size_t(2) * mc * mc * mc * mc);
   if (p64) AL(h->Ainv64, size_t(mc) * mc * mc * mc);
@@ -2228,6 +2281,10 @@ sl_status sl_hjb_set_launch(sl_hjb *h, int use_graphs, int coarse_tail_rows) {
   h->o.use_graphs = use_graphs;
   h->o.coarse_tail_rows = coarse_tail_rows;
   set_tail(h);
+  sl_status st = alloc_tail_image(h);
+  if (st != SL_OK) return st;
+  tail_pack(h, nullptr);  // the current hierarchy's stencils for the new tail levels
+  CK(cudaDeviceSynchronize());
   drop_graphs(h);
   return SL_OK;
 }

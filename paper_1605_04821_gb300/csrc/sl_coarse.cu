@@ -937,19 +937,19 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T> a) {
   }
 }
 
-// The same tail with every level's vectors and stencils in shared memory.  The block loads the
-// stencils of the tail's levels once per cycle (a few hundred KB from L2), every row as a dense
-// (2R+1)^2 window (a class row's taps scattered into its window, zeros elsewhere); after that
-// every phase reads shared memory only, with the window loops unrolled on the reach, so a
-// phase costs a few hundred cycles instead of the chain of L2 round trips (row class, then taps
-// and values) of the global form.  Each row sums its window in the order of the explicit rows
-// of tail_op (dy, then dx ascending); a class row's added zeros leave its sum unchanged.
-// Launched when the levels fit (launch_vcycle_tail).
+// The same tail with every level's vectors and stencils in shared memory.  Each row's stencil
+// is a dense (2R+1)^2 window ([e][I]: window entry e of row I; a class row's taps scattered
+// into its window, zeros elsewhere), packed once per hierarchy into a device image
+// (k_tail_pack) in exactly the shared-memory layout, so the block copies it with 16-byte loads
+// (a few hundred KB from L2); after that every phase reads shared memory only, with the window
+// loops unrolled on the reach, so a phase costs a few hundred cycles instead of the chain of
+// L2 round trips (row class, then taps and values) of the global form.  Each row sums its
+// window in the order of the explicit rows of tail_op (dy, then dx ascending); a class row's
+// added zeros leave its sum unchanged.  Launched when the levels fit (launch_vcycle_tail).
 struct TailSmem {
-  int vec[kMaxLevels];  // byte offsets: x, t, r, b (n^2 values each) of level l
-  int win[kMaxLevels];  // windows [e][I] (win * m^2 values)
-  int cls[kMaxLevels];  // row classes (m^2 ints)
-  int bytes;
+  int win[kMaxLevels];  // byte offsets of the windows of level l (first, contiguous: the image)
+  int vec[kMaxLevels];  // x, t, r, b (n^2 values each) of level l
+  int wbytes, bytes;    // windows only (the image), and everything
 };
 
 template <typename T>
@@ -962,19 +962,72 @@ static bool tail_smem_layout(const TailArgs<T> &a, TailSmem &lay, int limit) {
   };
   for (int l = a.l0; l < a.L; ++l) {
     const CoarseLev<T> &L = a.lev[l];
-    const size_t N = size_t(L.n) * L.n, m2 = size_t(L.m) * L.m;
-    lay.vec[l] = int(take(4 * N * sizeof(T)));
-    if (l < a.L - 1) {
-      lay.win[l] = int(take(size_t(L.win) * m2 * sizeof(T)));
-      lay.cls[l] = int(take(m2 * sizeof(int)));
-    } else {
-      lay.win[l] = lay.cls[l] = 0;
-    }
-    if (off > size_t(limit)) return false;
+    lay.win[l] = l < a.L - 1 ? int(take(size_t(L.win) * L.m * L.m * sizeof(T))) : 0;
   }
+  lay.wbytes = int(off);
+  for (int l = a.l0; l < a.L; ++l) lay.vec[l] = int(take(4 * size_t(a.lev[l].n) * a.lev[l].n * sizeof(T)));
   lay.bytes = int(off);
-  return true;
+  return off <= size_t(limit);
 }
+
+static int tail_smem_limit() {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return optin - 1024;
+}
+
+template <typename T>
+size_t tail_image_bytes(const TailArgs<T> &a) {
+  TailSmem lay{};
+  return tail_smem_layout<T>(a, lay, tail_smem_limit()) ? size_t(lay.wbytes) : 0;
+}
+template size_t tail_image_bytes<double>(const TailArgs<double> &);
+template size_t tail_image_bytes<float>(const TailArgs<float> &);
+
+// Window entry e of row I of level L: the explicit row's own window, or the class row's tap at
+// that offset (0 where it has none).  Indices are checked, so a hierarchy that was never built
+// packs garbage values but reads nothing out of bounds.
+template <typename T>
+__device__ T tail_window_entry(const CoarseLev<T> &L, int e, int I) {
+  const int c = L.cls[I];
+  if (c < 0) {
+    const int slot = -c - 1;
+    return slot < L.cap ? L.ewin[size_t(e) * L.cap + slot] : T(0);
+  }
+  if (c >= L.nk || !L.cnt || !L.coff || !L.cw) return T(0);
+  const int Wd = 2 * L.R + 1, dy = e / Wd - L.R, dx = e % Wd - L.R;
+  const int nt = min(L.cnt[c], L.ctmax);
+  for (int t = 0; t < nt; ++t) {
+    const int o = L.coff[c * L.ctmax + t];
+    if (int(int16_t(o & 0xffff)) == dx && (o >> 16) == dy) return L.cw[c * L.ctmax + t];
+  }
+  return T(0);
+}
+
+template <typename T>
+__global__ void k_tail_pack(TailArgs<T> a, TailSmem lay, T *__restrict__ img) {
+  for (int l = a.l0; l < a.L - 1; ++l) {
+    const CoarseLev<T> &L = a.lev[l];
+    const int m2 = L.m * L.m, tot = L.win * m2;
+    T *W = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(img) + lay.win[l]);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += gridDim.x * blockDim.x) {
+      const int e = idx / m2, I = idx - e * m2;
+      W[idx] = tail_window_entry<T>(L, e, I);
+    }
+  }
+}
+
+template <typename T>
+void launch_tail_pack(const TailArgs<T> &a, T *img, cudaStream_t s) {
+  TailSmem lay{};
+  if (!img || !tail_smem_layout<T>(a, lay, tail_smem_limit())) return;
+  note_launch();
+  k_tail_pack<T><<<2 * 152, 256, 0, s>>>(a, lay, img);
+}
+template void launch_tail_pack<double>(const TailArgs<double> &, double *, cudaStream_t);
+template void launch_tail_pack<float>(const TailArgs<float> &, float *, cudaStream_t);
 
 template <typename T, int RR>
 __device__ __forceinline__ T stail_window(const T *W, int m2, int I, int Rl, const T *x, int j, int n, int I1,
@@ -1060,64 +1113,35 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail_smem(TailArgs<T> a, TailSm
   auto vec = [&](int l, int q) {
     return reinterpret_cast<T *>(smem_raw + lay.vec[l]) + size_t(q) * a.lev[l].n * a.lev[l].n;
   };
-  auto wins = [&](int l) { return reinterpret_cast<T *>(smem_raw + lay.win[l]); };
-  auto clss = [&](int l) { return reinterpret_cast<int *>(smem_raw + lay.cls[l]); };
-  // 1. zero the vectors (boundary entries stay zero) and the windows; load the row classes
-  for (int l = a.l0; l < a.L; ++l) {
-    const CoarseLev<T> &L = a.lev[l];
-    T *v = vec(l, 0);
-    const int N4 = 4 * L.n * L.n;
-    for (int i = threadIdx.x; i < N4; i += blockDim.x) v[i] = T(0);
-    if (l < a.L - 1) {
-      T *W = wins(l);
-      const int tot = L.win * L.m * L.m;
-      for (int i = threadIdx.x; i < tot; i += blockDim.x) W[i] = T(0);
-      int *C = clss(l);
-      for (int I = threadIdx.x; I < L.m * L.m; I += blockDim.x) C[I] = L.cls[I];
+  auto wins = [&](int l) { return reinterpret_cast<const T *>(smem_raw + lay.win[l]); };
+  // the packed stencils (16-byte pieces, eight loads in flight per thread before their stores)
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(a.img);
+    float4 *dst = reinterpret_cast<float4 *>(smem_raw);
+    const int n16 = lay.wbytes / 16;
+    for (int i0 = threadIdx.x; i0 < n16; i0 += 8 * blockDim.x) {
+      float4 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q * int(blockDim.x) < n16) v[q] = __ldg(src + i0 + q * blockDim.x);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q * int(blockDim.x) < n16) dst[i0 + q * blockDim.x] = v[q];
     }
   }
+  // the vectors: zero (boundary entries stay zero), then b of the first level
+  {
+    T *v0 = reinterpret_cast<T *>(smem_raw + lay.wbytes);
+    const int nv = (lay.bytes - lay.wbytes) / int(sizeof(T));
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) v0[i] = T(0);
+  }
+  __syncthreads();
   {
     const CoarseLev<T> &L = a.lev[a.l0];
     T *b0 = vec(a.l0, 3);
     for (int i = threadIdx.x; i < L.n * L.n; i += blockDim.x) b0[i] = a.b[a.l0][i];
   }
   __syncthreads();
-  // 2. the stencils: explicit windows copied, class taps scattered; four loads in flight per
-  // thread before their stores
-  for (int l = a.l0; l < a.L - 1; ++l) {
-    const CoarseLev<T> &L = a.lev[l];
-    const int m2 = L.m * L.m, tot = L.win * m2, Wd = 2 * L.R + 1;
-    const int *C = clss(l);
-    T *W = wins(l);
-    for (int i0 = threadIdx.x; i0 < tot; i0 += 4 * blockDim.x) {
-      T v[4];
-      int dst[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int idx = i0 + q * blockDim.x;
-        dst[q] = -1;
-        v[q] = T(0);
-        if (idx < tot) {
-          const int e = idx / m2, I = idx - e * m2;
-          const int c = C[I];
-          if (c < 0) {
-            v[q] = L.ewin[size_t(e) * L.cap + (-c - 1)];
-            dst[q] = idx;
-          } else if (e < L.cnt[c]) {  // tap e of the class table
-            const int o = L.coff[c * L.ctmax + e];
-            const int dx = int(int16_t(o & 0xffff)), dy = o >> 16;
-            v[q] = L.cw[c * L.ctmax + e];
-            dst[q] = ((dy + L.R) * Wd + dx + L.R) * m2 + I;
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (dst[q] >= 0) W[dst[q]] = v[q];
-    }
-  }
-  __syncthreads();
-  // 3. the cycle
   T *cur[kMaxLevels];
   for (int l = a.l0; l < a.L - 1; ++l) {
     const CoarseLev<T> &L = a.lev[l];
@@ -1170,11 +1194,8 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail_smem(TailArgs<T> a, TailSm
 template <typename T>
 void launch_vcycle_tail(const TailArgs<T> &a, cudaStream_t s) {
   note_launch();
-  int dev = 0, optin = 0;
   TailSmem lay{};
-  if (cudaGetDevice(&dev) == cudaSuccess &&
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
-      tail_smem_layout<T>(a, lay, optin - 1024)) {
+  if (a.img && tail_smem_layout<T>(a, lay, tail_smem_limit())) {
     k_vcycle_tail_smem<T><<<1, 1024, lay.bytes, s>>>(a, lay);
     return;
   }

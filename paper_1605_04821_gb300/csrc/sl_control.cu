@@ -142,16 +142,20 @@ void launch_ctl_built(DevCtl *c, const NexplPtrs &np, cudaStream_t s) {
 }
 
 // Start of a linear solve.
-__global__ void k_ctl_ls_begin(DevCtl *c, double tol, cudaGraphConditionalHandle ir) {
+// Start of a linear solve: the first solve of a step's Howard iteration stops at loose_tol when
+// that is set (sl_opts.howard_loose_tol), every other at tol.
+__global__ void k_ctl_ls_begin(DevCtl *c, double tol, double loose_tol, cudaGraphConditionalHandle ir) {
   c->round = 0;
   c->total = 0;
-  c->tolk = tol;
+  c->ls_loose = (loose_tol > 0.0 && c->pi_it == 0) ? 1 : 0;
+  c->ls_tol = c->ls_loose ? loose_tol : tol;
+  c->tolk = c->ls_tol;
   c->ls_done = 0;
   cudaGraphSetConditional(ir, 1u);
 }
-void launch_ctl_ls_begin(DevCtl *c, double tol, cudaGraphConditionalHandle ir, cudaStream_t s) {
+void launch_ctl_ls_begin(DevCtl *c, double tol, double loose_tol, cudaGraphConditionalHandle ir, cudaStream_t s) {
   note_launch();
-  k_ctl_ls_begin<<<1, 1, 0, s>>>(c, tol, ir);
+  k_ctl_ls_begin<<<1, 1, 0, s>>>(c, tol, loose_tol, ir);
 }
 
 // k_init_scalars with the threshold (tolk)^2 from the loop state.
@@ -175,6 +179,7 @@ void launch_init_scalars_ctl(BicgScalars *S, const DevCtl *c, cudaStream_t s) {
 __global__ void k_ctl_ir_decide(DevCtl *c, const BicgScalars *S, double tol, int fp64, int kry_max,
                                 cudaGraphConditionalHandle enter) {
   c->c_ir += 1;
+  tol = c->ls_tol;  // this solve's tolerance (k_ctl_ls_begin)
   const double bn2 = S->bnorm2, bmax = S->bmax, rr = S->rr, rmax = S->rmax;
   unsigned go = 0;
   if (S->nonfinite || !isfinite(rr)) {
@@ -289,7 +294,8 @@ __global__ void k_ctl_pi_post(DevCtl *c, const unsigned long long *changes, cons
       c->status = SL_ENAN;
     } else {
       const bool small = maxd[0] <= pi_tol * fmax(1.0, maxd[1]);
-      if (!(ch == 0 || small)) {
+      // a loosely solved iterate never ends the iteration: the next solve is tight
+      if (!(ch == 0 || small) || c->ls_loose) {
         if (c->pi_it >= pi_max) c->status = SL_ENOCONV_PI;
         else more = 1;
       }

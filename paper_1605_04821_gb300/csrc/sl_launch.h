@@ -122,9 +122,17 @@ struct TailArgs {
   CoarseLev<T> lev[kMaxLevels];
   T *x[kMaxLevels], *t[kMaxLevels], *r[kMaxLevels], *b[kMaxLevels];
   const T *Ainv;
+  const T *img;  // the levels' stencils packed in the shared-memory layout (launch_tail_pack), or null
 };
 template <typename T>
 void launch_vcycle_tail(const TailArgs<T> &a, cudaStream_t s);
+// Bytes of the packed tail stencils of a (0: they do not fit in one block's shared memory).
+template <typename T>
+size_t tail_image_bytes(const TailArgs<T> &a);
+// Packs the tail levels' stencils into img (tail_image_bytes(a) bytes), in the layout the
+// shared-memory tail copies; after every change of the hierarchy or of the tail's levels.
+template <typename T>
+void launch_tail_pack(const TailArgs<T> &a, T *img, cudaStream_t s);
 
 template <typename T>
 void launch_coarsest_setup(int level, const FineTab &tab, const uint8_t *policy, T dt,
@@ -263,6 +271,8 @@ struct DevCtl {
   int nexpl[16];         // explicit rows of each level after the last rebuild in the graph
   int tma_err;           // a bounded wait of the TMA fine operator gave up (FineTab::tma_err)
   long long c_pre;       // improvements at a step's first iterate (sl_opts.howard_init 1)
+  double ls_tol;         // stop tolerance of the current linear solve
+  int ls_loose;          // the current solve is a step's first, at howard_loose_tol
 };
 
 // Explicit-row counts of the coarse levels, gathered into DevCtl::nexpl (levels 1 .. L-1).
@@ -294,7 +304,7 @@ void launch_extrapolate_ctl(double *X, const double *U, const double *V, int n, 
                             cudaStream_t s);
 void launch_ctl_pi_pre(DevCtl *c, long long thresh, cudaGraphConditionalHandle rebuild, cudaStream_t s);
 void launch_ctl_built(DevCtl *c, const NexplPtrs &np, cudaStream_t s);
-void launch_ctl_ls_begin(DevCtl *c, double tol, cudaGraphConditionalHandle ir, cudaStream_t s);
+void launch_ctl_ls_begin(DevCtl *c, double tol, double loose_tol, cudaGraphConditionalHandle ir, cudaStream_t s);
 void launch_init_scalars_ctl(BicgScalars *S, const DevCtl *c, cudaStream_t s);
 void launch_ctl_ir_decide(DevCtl *c, const BicgScalars *S, double tol, int fp64, int kry_max,
                           cudaGraphConditionalHandle enter, cudaStream_t s);

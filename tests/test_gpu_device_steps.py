@@ -37,10 +37,10 @@ def _case(name):
     return p
 
 
-def _march(p, mode, precision):
+def _march(p, mode, precision, **kw):
     import paper_1605_04821_gb300 as S
     S.load()
-    sol = S.solver_from_problem(p, precision=precision, argmin_screen=precision, use_graphs=mode)
+    sol = S.solver_from_problem(p, precision=precision, argmin_screen=precision, use_graphs=mode, **kw)
     u = to_dev(p.g)
     m = p.n - 2
     pol = torch.empty(m * m, dtype=torch.uint8, device="cuda")
@@ -68,6 +68,28 @@ def test_graph_steps_equal_host_steps(name, precision):
         assert a["graph_steps"] == 0 and b["graph_steps"] == 1
     ref = lisl.solve(p)
     assert rel_maxnorm(u2[-1].cpu().numpy(), ref.U) <= (TOL_FP64 if precision == 0 else TOL_MIXED)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("opts", [dict(howard_init=1), dict(howard_loose_tol=1e-6),
+                                  dict(howard_init=1, howard_loose_tol=1e-6)])
+def test_howard_variants_graph_equal_host_and_match_the_oracle(opts, precision):
+    """The Howard start (sl_opts.howard_init) and the loose first solve (howard_loose_tol) run
+    the same way in both modes and reach the oracle's solution: the last solve of every step
+    stays at krylov_tol and its policy is the improvement of its result."""
+    p = _case("s129")
+    u1, pol1, st1 = _march(p, 1, precision, **opts)
+    u2, pol2, st2 = _march(p, 2, precision, **opts)
+    for i, (a, b) in enumerate(zip(u1, u2)):
+        assert torch.equal(a, b), f"step {i + 1} differs"
+    assert torch.equal(pol1, pol2)
+    for a, b in zip(st1, st2):
+        for key in ("pi_iters", "krylov_iters", "ir_iters", "rebuilds", "policy_changes"):
+            assert a[key] == b[key], (key, a[key], b[key])
+    ref = lisl.solve(p)
+    assert rel_maxnorm(u2[-1].cpu().numpy(), ref.U) <= (TOL_FP64 if precision == 0 else TOL_MIXED)
+    if "howard_loose_tol" in opts:  # every step solved at least twice (loose, then tight)
+        assert all(st["pi_iters"] >= 2 for st in st2)
 
 
 def test_graph_solve_counts_every_step():
