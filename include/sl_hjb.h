@@ -211,6 +211,15 @@ typedef struct {
                            loosely never ends the iteration, so the step's last solve is always at
                            krylov_tol and its policy is the improvement of its result.  Default
                            1e-7; 0: every solve at krylov_tol.  At least krylov_tol. */
+  int argmin_skip;      /* with the FP32 screen (argmin_screen 1): 1 (default): a policy
+                           improvement after the first one of a step re-decides only the nodes
+                           whose last decision could change.  Each decision's margin (how far,
+                           in a rigorous bound, every other control lies above the chosen one) is
+                           kept; a control value moves by at most (2 sum |w| + |c|) max|dX| when
+                           X moves, so a node whose margin exceeds twice that bound for the X
+                           change since the last improvement keeps its control, and a tile
+                           whose nodes all keep theirs is not evaluated.  The policies are the
+                           same as with 0 (every node re-decided). */
 } sl_opts;
 
 typedef struct {
@@ -231,7 +240,7 @@ typedef struct {
  * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
  * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
  * extrapolate 1, precond 0, amg_k_levels 2, smoother 0, fine_tma 1, coarse_fusion 3, howard_init 0,
- * howard_loose_tol 1e-7. */
+ * howard_loose_tol 1e-7, argmin_skip 1. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every

@@ -169,6 +169,8 @@ struct sl_hjb {
   bool dev_off = false;                        // a capture failed: host-driven steps from then on
   AmgEngine amg;                               // precond 1
   ArgminITaps *itaps = nullptr;                // interior-class taps for the argmin's parameter
+  float *d_gap = nullptr;                      // per interior node: margin of its last decision
+  double Wabs = 0.0;                           // max over table entries of sum |w|
   long long amg_gen = 0;                       // bumped by every AMG setup (its sizes change)
   std::vector<void *> allocs;
   std::string err;
@@ -278,7 +280,7 @@ sl_status coef(sl_hjb *h, double t, double *Xext, cudaStream_t s) {
 
 // ---------------------------------------------------------------------- argmin
 // Arguments of the policy improvement on Xext (psi on the boundary) for the handle's tables.
-ArgminArgs argmin_args(sl_hjb *h, const double *Xext) {
+ArgminArgs argmin_args(sl_hjb *h, const double *Xext, bool skip = false) {
   ArgminArgs a{};
   a.tab = h->tab;
   a.slin = h->d_slin;
@@ -304,10 +306,17 @@ ArgminArgs argmin_args(sl_hjb *h, const double *Xext) {
   a.SW = h->SW;
   a.SH = h->SH;
   a.screen = h->o.argmin_screen;
+  // decisions that cannot change are skipped inside a step (the paired screen only: it is the
+  // kernel that records the margins)
+  const bool paired = a.screen && h->tab.tmax == 12 && h->itaps && h->itaps->n > 0;
+  a.gap = paired ? h->d_gap : nullptr;
+  a.skip_flag = (paired && skip && h->o.argmin_skip == 1) ? &h->ctl->skip_ok : nullptr;
+  a.Xprev = h->Xpi;
+  a.Wabs = h->Wabs;
   return a;
 }
 
-sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_t s) {
+sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_t s, bool skip = false) {
   if (h->general) {
     CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
@@ -322,7 +331,7 @@ sl_status improve(sl_hjb *h, const double *Xext, long long *changes, cudaStream_
     h->have_policy = true;
     return SL_OK;
   }
-  const ArgminArgs a = argmin_args(h, Xext);
+  const ArgminArgs a = argmin_args(h, Xext, skip);
   CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
   CK(launch_argmin(a, *h->itaps, s));
@@ -928,6 +937,7 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
   CK(cudaMemcpyAsync(h->X, u, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   sl_status r = coef(h, t, h->X, s);
   if (r != SL_OK) return r;
+  CK(cudaMemsetAsync(&h->ctl->skip_ok, 0, sizeof(int), s));  // no improvement in this step yet
   const bool first_improve = !h->have_policy;
   if (first_improve) {
     long long ch = 0;
@@ -982,10 +992,12 @@ sl_status step_impl(sl_hjb *h, double *u, double t, double dt, uint8_t *pol_out,
       CK(cudaMemcpyAsync(h->rec_slot, h->policy, size_t(h->m) * h->m, cudaMemcpyDeviceToDevice, s));
     double ta = now_ms();
     long long ch = 0;
-    r = improve(h, h->X, &ch, s);
-    if (r != SL_OK) return r;
-    h->changes_since_build += ch;
+    // the stop test's max |X - X^{m-1}| first: the argmin's skip test reads it
     launch_maxabs_diff(h->X, h->Xpi, h->n, h->d_maxd, h->counter, h->partials, s);
+    r = improve(h, h->X, &ch, s, true);
+    if (r != SL_OK) return r;
+    CK(cudaMemsetAsync(&h->ctl->skip_ok, 1, sizeof(int), s));  // this improvement was at X = X^m
+    h->changes_since_build += ch;
     CK(cudaMemcpyAsync(h->h_maxd, h->d_maxd, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (st) {
@@ -1204,10 +1216,10 @@ sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long
 }
 
 // The argmin with its change counter and flags cleared first (improve() without the host read).
-sl_status cap_improve(sl_hjb *h, cudaStream_t s) {
+sl_status cap_improve(sl_hjb *h, cudaStream_t s, bool skip = false) {
   CK(cudaMemsetAsync(h->d_changes, 0, sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
-  CK(launch_argmin(argmin_args(h, h->X), *h->itaps, s));
+  CK(launch_argmin(argmin_args(h, h->X, skip), *h->itaps, s));
   return SL_OK;
 }
 
@@ -1240,9 +1252,10 @@ sl_status cap_pi_body(sl_hjb *h, double dt, cudaStream_t s, int depth, long long
   launch_ctl_after_ls(h->ctl, hok, hpi, s);
   st = add_cond(h, s, depth, hok, cudaGraphCondTypeIf, &G.k_ok, &t,
                 [&](cudaStream_t sb, int, long long *) -> sl_status {
-                  const sl_status r = cap_improve(h, sb);
-                  if (r != SL_OK) return r;
+                  // the stop test's max |X - X^{m-1}| first: the argmin's skip test reads it
                   launch_maxabs_diff(h->X, h->Xpi, h->n, h->d_maxd, h->counter, h->partials, sb);
+                  const sl_status r = cap_improve(h, sb, true);
+                  if (r != SL_OK) return r;
                   launch_ctl_pi_post(h->ctl, h->d_changes, h->d_flags, h->d_maxd, h->o.pi_tol,
                                      h->o.pi_max, hpi, sb);
                   CK(cudaMemcpyAsync(h->Xpi, h->X, N * sizeof(double), cudaMemcpyDeviceToDevice, sb));
@@ -1687,6 +1700,7 @@ void sl_opts_default(sl_opts *o) {
   o->coarse_fusion = 3;
   o->howard_init = 0;
   o->howard_loose_tol = 1e-7;
+  o->argmin_skip = 1;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -1738,6 +1752,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   if (h->o.smoother != 0 && h->o.smoother != 1) return fail(h, SL_EINVAL, "smoother must be 0 or 1");
   if (h->o.coarse_fusion < 0) return fail(h, SL_EINVAL, "coarse_fusion must be >= 0");
   if (h->o.howard_init != 0 && h->o.howard_init != 1) return fail(h, SL_EINVAL, "howard_init must be 0 or 1");
+  if (h->o.argmin_skip != 0 && h->o.argmin_skip != 1) return fail(h, SL_EINVAL, "argmin_skip must be 0 or 1");
   if (!(h->o.howard_loose_tol >= 0.0) || (h->o.howard_loose_tol > 0.0 && h->o.howard_loose_tol < h->o.krylov_tol))
     return fail(h, SL_EINVAL, "howard_loose_tol must be 0 or at least krylov_tol");
   if (h->o.precond == 1 && (h->o.nu1 < 1 || h->o.amg_k_levels < 0))
@@ -1862,6 +1877,16 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
     }
     h->itaps->n = h->K * ft.tmax;
   }
+  // the argmin's skip test: a control value moves by at most sum_t |w_t| |dX_t - dX_j|
+  // + |c_k| |dX_j| when X moves by dX
+  h->Wabs = 0.0;
+  for (int e = 0; e < int(ft.nt.size()); ++e) {
+    double sw = 0.0;
+    for (int t = 0; t < ft.nt[e]; ++t) sw += std::fabs(ft.w[size_t(e) * ft.tmax + t]);
+    h->Wabs = std::max(h->Wabs, sw);
+  }
+  h->Wabs *= 1.0 + 1e-12;
+  if (h->o.argmin_screen && !h->general) AL(h->d_gap, size_t(h->m) * h->m);
   UP(h->d_lin, lin);
   UP(h->d_slin, slin);
   UP(h->d_off, off);

@@ -59,6 +59,7 @@ __global__ void k_ctl_step_begin(DevCtl *c, const double *tau_table, int ntau, d
   }
   c->pi_it = 0;
   c->c_steps += 1;
+  c->skip_ok = 0;  // no improvement in this step yet
   cudaGraphSetConditional(improve0, c->need_improve ? 1u : 0u);
   // a step that keeps the previous policy improves it at its first iterate (howard_init 1)
   cudaGraphSetConditional(pre, (howard_init && !c->need_improve && c->status == SL_OK) ? 1u : 0u);
@@ -286,6 +287,7 @@ __global__ void k_ctl_pi_post(DevCtl *c, const unsigned long long *changes, cons
     c->status = SL_ENAN;
   } else {
     const long long ch = (long long)*changes;
+    c->skip_ok = 1;  // this improvement was at the iterate the next stop test measures from
     c->changes_since_build += ch;
     c->c_pi += 1;
     c->c_changes += ch;

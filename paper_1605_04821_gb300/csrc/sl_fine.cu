@@ -2,6 +2,7 @@
 // FP64 HJB residual and grid transfers.
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <type_traits>
@@ -412,7 +413,20 @@ struct NodeScreen {
   unsigned long long cand;
   int ncand;
   bool overflow;
+  float l1, l2, umin;  // smallest and second smallest lower bound, smallest upper bound
+  int i1;              // the control of l1
 };
+
+// The two smallest lower bounds of a node's screen and the control of the smallest.
+__device__ __forceinline__ void track_lb(NodeScreen &ns, float lb, int k) {
+  if (lb < ns.l1) {
+    ns.l2 = ns.l1;
+    ns.l1 = lb;
+    ns.i1 = k;
+  } else {
+    ns.l2 = fminf(ns.l2, lb);
+  }
+}
 
 // k_argmin's screen of one node over every control (any table entry).
 template <int TMAX>
@@ -442,6 +456,7 @@ __device__ __forceinline__ void screen_one(const ArgminArgs &a, const ArgminITap
     const float lb = v - E, ub = v + E;
     const float tw = a.tie2_32 * fmaxf(1.0f, fabsf(v)) + 4.0f * u * fabsf(v);
     Umin = fminf(Umin, ub);
+    track_lb(ns, lb, k);
     if (ub + tw < Lmin) {
       ns.cand = (unsigned long long)k;
       ns.ncand = 1;
@@ -452,6 +467,7 @@ __device__ __forceinline__ void screen_one(const ArgminArgs &a, const ArgminITap
       Lmin = fminf(Lmin, lb);
     }
   }
+  ns.umin = Umin;
 }
 
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
@@ -503,6 +519,7 @@ __device__ __forceinline__ void screen_pair(const ArgminArgs &a, const ArgminITa
       if (!(vq == vq)) continue;
       const float lbq = q ? lb.y : lb.x, ubq = q ? ub.y : ub.x, twq = q ? tw.y : tw.x;
       Umin[q] = fminf(Umin[q], ubq);
+      track_lb(*ns[q], lbq, k);
       if (ubq + twq < Lmin[q]) {
         ns[q]->cand = (unsigned long long)k;
         ns[q]->ncand = 1;
@@ -514,11 +531,14 @@ __device__ __forceinline__ void screen_pair(const ArgminArgs &a, const ArgminITa
       }
     }
   }
+  n0.umin = Umin[0];
+  n1.umin = Umin[1];
 }
 
 // The exact FP64 decision among a node's screened candidates (all controls on overflow), as in
 // k_argmin's pass 2: the lowest index within the tie window of the FP64 minimum; -1 if none.
-__device__ __forceinline__ int decide_fp64(const ArgminArgs &a, const NodeScreen &ns) {
+__device__ __forceinline__ int decide_fp64(const ArgminArgs &a, const NodeScreen &ns, double &vbest) {
+  vbest = __longlong_as_double(0x7ff8000000000000ll);  // NaN: not evaluated in FP64
   if (ns.ncand == 1 && !ns.overflow) return int(ns.cand & 0xffull);
   if (ns.ncand == 0 && !ns.overflow) return -1;
   const FineTab &tab = a.tab;
@@ -549,13 +569,42 @@ __device__ __forceinline__ int decide_fp64(const ArgminArgs &a, const NodeScreen
   for (int c = 0; c < cnt; ++c) {
     const int k = ns.overflow ? c : int((ns.cand >> (8 * c)) & 0xffull);
     const double v = c < kMaxCand ? vals[c] : value(k);
-    if (v <= thr) return k;
+    if (v <= thr) {
+      vbest = v;
+      return k;
+    }
   }
   return -1;
 }
 
+// The margin of a node's decision for ArgminArgs::gap: every other control's value exceeds the
+// chosen one's by at least this much more than four tie windows, in exact arithmetic, at the X
+// of this improvement (the other controls' screen lower bounds against the chosen value: its
+// FP64 value rounded up, or its screen upper bound when it was the only candidate).  -inf when
+// no margin is known.
+__device__ __forceinline__ float decision_gap(const ArgminArgs &a, const NodeScreen &ns, int best, double vbest) {
+  if (best < 0 || ns.overflow) return -INFINITY;
+  if (a.tab.K == 1) return INFINITY;
+  const float others = best == ns.i1 ? ns.l2 : ns.l1;
+  float vup;
+  if (vbest == vbest) {
+    const float vf = float(vbest);
+    vup = vf + fabsf(vf) * 1.2e-7f + 1e-30f;
+  } else {
+    vup = ns.umin;
+  }
+  if (!(others == others) || !(vup == vup) || others == INFINITY) return -INFINITY;
+  const float u = 5.9604645e-8f;
+  const float g = others - vup;
+  return g - fabsf(g) * 1e-6f - 8.0f * u * fmaxf(fabsf(others), fabsf(vup)) -
+         2.0f * a.tie2_32 * fmaxf(1.0f, fabsf(vup));
+}
+
+// Capped at four blocks of 256 threads per SM (64 registers): the skip test's extra live values
+// would otherwise take the kernel to 80 registers and three blocks per SM (10.12 against 9.95 ms
+// per step at 2049^2, K = 65).
 template <int TMAX>
-__global__ void __launch_bounds__(kTX *kTY) k_argmin2(const __grid_constant__ ArgminArgs a,
+__global__ void __launch_bounds__(kTX *kTY, 4) k_argmin2(const __grid_constant__ ArgminArgs a,
                                                       const __grid_constant__ ArgminITaps it) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned red_cnt[kTX * kTY / 32];
@@ -567,6 +616,88 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin2(const __grid_constant__ Ar
   const FineTab &tab = a.tab;
   const int n = tab.n, m = tab.m;
   const int tid = threadIdx.y * kTX + threadIdx.x;
+  const int i1 = 1 + blockIdx.x * kTX + threadIdx.x;
+  // Nodes whose last decision cannot change.  Since the last improvement (this step, same
+  // coefficients) X has moved by dX = X - Xprev; over this tile and its halo a control value
+  // has moved by at most Wabs osc(dX) + cmax max|dX| (osc: max dX - min dX), so a node whose
+  // margin exceeds twice that keeps its control and its margin shrinks by the same amount.  A
+  // block whose nodes all keep theirs stages nothing.  dX is formed in FP64 and its extremes
+  // are taken on ordered integer images of the values (the integer pipe, not the narrow FP64
+  // one); a NaN anywhere in the window disables the test.
+  bool warp_keeps = false;  // every node of this warp keeps its control (skip its screen)
+  float kept_gap[2] = {0.f, 0.f};
+  if (a.gap && a.skip_flag && *a.skip_flag) {
+    __shared__ long long sk_max[kTX * kTY / 32], sk_min[kTX * kTY / 32];
+    __shared__ int sk_nan[kTX * kTY / 32];
+    __shared__ float sk_shrink;
+    const int WW = kTX + 2 * a.halo, HH = kTY2 + 2 * a.halo;
+    const int b1 = 1 + blockIdx.x * kTX - a.halo, b2 = 1 + blockIdx.y * kTY2 - a.halo;
+    long long omax = LLONG_MIN, omin = LLONG_MAX;
+    int nan = 0;
+    for (int idx = tid; idx < WW * HH; idx += kTX * kTY) {
+      const int r = idx / WW, cc = idx - r * WW;
+      const int g1 = b1 + cc, g2 = b2 + r;
+      if (g1 < 0 || g1 >= n || g2 < 0 || g2 >= n) continue;
+      const size_t gj = size_t(g2) * n + g1;
+      const long long bits = __double_as_longlong(a.X[gj] - a.Xprev[gj]);
+      nan |= (bits & 0x7fffffffffffffffll) > 0x7ff0000000000000ll;
+      const long long ord = bits >= 0 ? bits : (bits ^ 0x7fffffffffffffffll);
+      omax = max(omax, ord);
+      omin = min(omin, ord);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+      omin = min(omin, __shfl_xor_sync(0xffffffffu, omin, o));
+      nan |= __shfl_xor_sync(0xffffffffu, nan, o);
+    }
+    if ((tid & 31) == 0) {
+      sk_max[tid >> 5] = omax;
+      sk_min[tid >> 5] = omin;
+      sk_nan[tid >> 5] = nan;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < kTX * kTY / 32; ++w) {
+        omax = max(omax, sk_max[w]);
+        omin = min(omin, sk_min[w]);
+        nan |= sk_nan[w];
+      }
+      const long long bmax = omax >= 0 ? omax : (omax ^ 0x7fffffffffffffffll);
+      const long long bmin = omin >= 0 ? omin : (omin ^ 0x7fffffffffffffffll);
+      const double dmax = __longlong_as_double(bmax), dmin = __longlong_as_double(bmin);
+      // each dX is X - Xprev rounded (relative error <= 2^-53): widen by that much of max|dX|
+      const double amax = fmax(fabs(dmax), fabs(dmin));
+      const double osc = (dmax - dmin) * (1.0 + 1e-15) + 4.5e-16 * amax;
+      const double sh = 2.0 * (a.Wabs * osc + a.cmax * amax) * (1.0 + 1e-12);
+      sk_shrink = (nan || !(sh < 1e30)) ? INFINITY : float(sh) * 1.000001f + 1e-30f;
+    }
+    __syncthreads();
+    const float shrink = sk_shrink;
+    bool keep = shrink < INFINITY;
+    float g[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i2 = 1 + blockIdx.y * kTY2 + threadIdx.y + 8 * q;
+      g[q] = INFINITY;
+      if (i1 <= m && i2 <= m) {
+        g[q] = a.gap[(i2 - 1) * m + (i1 - 1)];
+        keep = keep && g[q] > shrink;
+      }
+    }
+    if (__syncthreads_and(keep)) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int i2 = 1 + blockIdx.y * kTY2 + threadIdx.y + 8 * q;
+        if (i1 <= m && i2 <= m) a.gap[(i2 - 1) * m + (i1 - 1)] = g[q] - shrink;
+      }
+      return;
+    }
+    // the block stages its tile for the warps that must decide; a warp whose nodes all keep
+    // their controls only shrinks their margins
+    warp_keeps = __all_sync(0xffffffffu, keep);
+    kept_gap[0] = g[0] - shrink;
+    kept_gap[1] = g[1] - shrink;
+  }
   const int o1 = 1 + blockIdx.x * kTX - a.halo, o2 = 1 + blockIdx.y * kTY2 - a.halo;
   const int c1 = min(1 + blockIdx.x * kTX + kTX / 2, n - 2), c2 = min(1 + blockIdx.y * kTY2 + kTY2 / 2, n - 2);
   const double xc = a.X[size_t(c2) * n + c1];
@@ -596,7 +727,6 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin2(const __grid_constant__ Ar
   for (int w = 0; w < kTX * kTY / 32; ++w) Dmax = fmaxf(Dmax, red_max[w]);
   const float eta = 2.0f * u * Dmax * 1.001f + 1e-30f;
 
-  const int i1 = 1 + blockIdx.x * kTX + threadIdx.x;
   NodeScreen ns[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
@@ -607,6 +737,8 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin2(const __grid_constant__ Ar
     s.ncand = 0;
     s.overflow = false;
     s.itap = false;
+    s.l1 = s.l2 = s.umin = INFINITY;
+    s.i1 = -1;
     if (!s.valid) continue;
     s.j = i2 * n + i1;
     s.q1 = class_q(i1, n, tab.B);
@@ -624,7 +756,15 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin2(const __grid_constant__ Ar
     s.x0 = xs32[s.sidx];
     s.itap = TMAX > 0 && it.n > 0 && s.q1 == tab.B && s.q2 == tab.B;
   }
-  if (ns[0].valid && ns[1].valid && ns[0].itap && ns[1].itap) {
+  if (warp_keeps) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (!ns[q].valid) continue;
+      const int i2 = 1 + blockIdx.y * kTY2 + threadIdx.y + 8 * q;
+      a.gap[(i2 - 1) * m + (i1 - 1)] = kept_gap[q];
+      ns[q].valid = false;
+    }
+  } else if (ns[0].valid && ns[1].valid && ns[0].itap && ns[1].itap) {
     screen_pair<TMAX>(a, it, xs32, ctl_phi, ctl_cw, eta, ns[0], ns[1]);
   } else {
 #pragma unroll
@@ -635,9 +775,11 @@ __global__ void __launch_bounds__(kTX *kTY) k_argmin2(const __grid_constant__ Ar
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     if (!ns[q].valid) continue;
-    const int best = decide_fp64(a, ns[q]);
+    double vbest;
+    const int best = decide_fp64(a, ns[q], vbest);
     const int i2 = 1 + blockIdx.y * kTY2 + threadIdx.y + 8 * q;
     const int pidx = (i2 - 1) * m + (i1 - 1);
+    if (a.gap) a.gap[pidx] = decision_gap(a, ns[q], best, vbest);
     if (best < 0) {
       atomicOr(a.flags, 1);
     } else if (a.policy[pidx] != uint8_t(best)) {

@@ -47,6 +47,17 @@ struct ArgminArgs {
   int *flags;              // bit 0: non-finite control value
   int halo, SW, SH;        // staged tile: (32 + 2 halo) x (8 + 2 halo)
   int screen;
+  // Skipping decisions that cannot change (k_argmin2).  gap[I]: a lower bound, in the units of
+  // the control values, on how far every other control lies above the chosen one at the X of
+  // the last improvement (Xprev), less the tie window; null: no skipping.  With dX = X - Xprev,
+  // a control value moves by at most sum_t |w_t| |dX_t - dX_j| + |c_k| |dX_j|
+  // <= Wabs osc(dX) + cmax max|dX| over a block's tile and halo, so a node whose gap exceeds
+  // twice that keeps its control.  skip_flag != 0 only within a step after an improvement at
+  // Xprev.
+  float *gap;
+  const double *Xprev;
+  const int *skip_flag;
+  double Wabs;             // max over table entries of sum_t |w_t|
 };
 
 // The packed taps {byte offset in the FP32 staged tile, fp32 weight bits} of the interior
@@ -273,6 +284,7 @@ struct DevCtl {
   long long c_pre;       // improvements at a step's first iterate (sl_opts.howard_init 1)
   double ls_tol;         // stop tolerance of the current linear solve
   int ls_loose;          // the current solve is a step's first, at howard_loose_tol
+  int skip_ok;           // the argmin may skip settled nodes (ArgminArgs::skip_flag)
 };
 
 // Explicit-row counts of the coarse levels, gathered into DevCtl::nexpl (levels 1 .. L-1).

@@ -121,3 +121,42 @@ def test_step_size_change_recaptures():
         outs.append(u)
         sol.close()
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("name", ["heavy33", "s129"])
+def test_argmin_skip_keeps_every_decision(name, mode):
+    """sl_opts.argmin_skip: re-deciding only the nodes whose margin does not cover the move of X
+    since the step's last improvement gives the policies, states and counts of re-deciding every
+    node, bit for bit."""
+    p = _case(name)
+    u0, pol0, st0 = _march(p, mode, 1, argmin_skip=0)
+    u1, pol1, st1 = _march(p, mode, 1, argmin_skip=1)
+    for i, (a, b) in enumerate(zip(u0, u1)):
+        assert torch.equal(a, b), f"step {i + 1} differs"
+    assert torch.equal(pol0, pol1)
+    for a, b in zip(st0, st1):
+        for key in ("pi_iters", "krylov_iters", "ir_iters", "rebuilds", "policy_changes"):
+            assert a[key] == b[key], (key, a[key], b[key])
+
+
+def test_argmin_skip_on_the_2049_workload():
+    """The same on three steps of the 2049^2, 65-control workload, where most nodes keep their
+    control in the improvement that follows each step's tight solve."""
+    import paper_1605_04821_gb300 as S
+    S.load()
+    p = W.mixed_2049(seed=0)
+    dt = 1.0 / 128
+    outs = []
+    for skip in (0, 1):
+        sol = S.solver_from_problem(p, precision=1, argmin_screen=1, argmin_skip=skip)
+        u = to_dev(p.g)
+        m = p.n - 2
+        pol = torch.empty(m * m, dtype=torch.uint8, device="cuda")
+        sts = [sol.step(u, i * dt, dt, policy_out=pol) for i in range(1, 4)]
+        sol.close()
+        outs.append((u, pol, sts))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1])
+    for a, b in zip(outs[0][2], outs[1][2]):
+        assert a["pi_iters"] == b["pi_iters"] and a["policy_changes"] == b["policy_changes"]
