@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--amg-steps", type=int, default=8)
     p.add_argument("--batched-instances", type=int, default=256)
     p.add_argument("--batched-workers", type=int, default=16)
+    p.add_argument("--batched-graphs", type=int, default=1, choices=[1, 2],
+                   help="graph mode of the batch's handles (sl_opts.use_graphs)")
     p.add_argument("--batched-one-worker", action="store_true",
                    help="also time the batch with a single worker thread (about 25 s)")
     p.add_argument("--adjoint-steps", type=int, default=64,
@@ -629,7 +631,7 @@ def batched_record(slp, W, dev, args, extra, rank, world, barrier, dist):
     us = [torch.as_tensor(p.g, dtype=torch.float64, device=dev) for p in sub]
     kw = dict(precision=1, argmin_screen=1)
     kw.update(extra)
-    kw["use_graphs"] = 1
+    kw["use_graphs"] = args.batched_graphs
     out = {"workload": f"{len(probs)} instances of the uncertain-correlation family: n uniform in "
                        "{65,129,257,513}, (s1,s2) ~ U[0.15,0.4]^2, K ~ U{17..65}, rho in "
                        "[-0.9,0.9], 32 steps of 1/32 (seed 0); mixed precision",
