@@ -841,8 +841,8 @@ sl_status true_residual(sl_hjb *h, double dt, double tolk, double *r, ResNorms *
     launch_fineT_op<double>(OP_RESID, csrT_view<double>(h), h->o.omega, h->mu, h->lam, r, s);
   else
     launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r, h->halo, h->SW, s);
-  launch_init_scalars(h->S, tolk * tolk, s);
-  launch_norms(h->transposed ? h->lam : h->Fvec, N, 0, h->S, h->partials, h->counter, s);
+  // ||F|| (or ||lambda||) was taken once by linear_solve before its first round
+  launch_init_scalars_keep_b(h->S, tolk * tolk, s);
   launch_norms(r, N, 1, h->S, h->partials, h->counter, s);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(h->hS, h->S, sizeof(BicgScalars), cudaMemcpyDeviceToHost, s));
@@ -872,6 +872,9 @@ sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
     launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, h->halo,
                      h->SW, s, std::max(1, h->cl[0].R));
   CK(cudaGetLastError());
+  // the right-hand side's norms, once per solve (every round keeps them in S)
+  launch_init_scalars(h->S, 0.0, s);
+  launch_norms(h->transposed ? h->lam : h->Fvec, N, 0, h->S, h->partials, h->counter, s);
   double *X = h->transposed ? h->mu : h->X;
   KBuf &k = h->kb;
   const double tol = h->ls_tol > 0.0 ? h->ls_tol : h->o.krylov_tol;
@@ -1166,6 +1169,9 @@ sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long
   KBuf &k = h->kb;
   launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, h->halo,
                    h->SW, s, std::max(1, h->cl[0].R));
+  // the right-hand side's norms, once per solve (every round keeps them in S)
+  launch_init_scalars(h->S, 0.0, s);
+  launch_norms(h->Fvec, N, 0, h->S, h->partials, h->counter, s);
   cudaGraphConditionalHandle hir;
   CK(new_cond_handle(s, &hir));
   launch_ctl_ls_begin(h->ctl, h->o.krylov_tol, h->o.howard_loose_tol, hir, s);
@@ -1177,7 +1183,6 @@ sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long
         double *r64 = fp64 ? k.r64 : h->R;
         launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r64, h->halo, h->SW, sb);
         launch_init_scalars_ctl(h->S, h->ctl, sb);
-        launch_norms(h->Fvec, N, 0, h->S, h->partials, h->counter, sb);
         launch_norms(r64, N, 1, h->S, h->partials, h->counter, sb);
         cudaGraphConditionalHandle hen;
         CK(new_cond_handle(sb, &hen));

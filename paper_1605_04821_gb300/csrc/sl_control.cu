@@ -159,7 +159,8 @@ void launch_ctl_ls_begin(DevCtl *c, double tol, double loose_tol, cudaGraphCondi
   k_ctl_ls_begin<<<1, 1, 0, s>>>(c, tol, loose_tol, ir);
 }
 
-// k_init_scalars with the threshold (tolk)^2 from the loop state.
+// k_init_scalars with the threshold (tolk)^2 from the loop state, keeping the norms of the
+// solve's right-hand side (computed once before its first round).
 __global__ void k_init_scalars_ctl(BicgScalars *S, const DevCtl *c) {
   BicgScalars z = {};
   z.rho_old = 1.0;
@@ -167,6 +168,9 @@ __global__ void k_init_scalars_ctl(BicgScalars *S, const DevCtl *c) {
   z.omega = 1.0;
   const double tk = c->tolk;
   z.tolrel2 = tk * tk;
+  z.bnorm2 = S->bnorm2;
+  z.bmax = S->bmax;
+  z.tol2 = z.tolrel2 * z.bnorm2;
   *S = z;
 }
 void launch_init_scalars_ctl(BicgScalars *S, const DevCtl *c, cudaStream_t s) {

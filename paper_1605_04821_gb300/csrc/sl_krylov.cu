@@ -340,6 +340,24 @@ void launch_init_scalars(BicgScalars *S, double tolrel2, cudaStream_t s) {
   k_init_scalars<<<1, 1, 0, s>>>(S, tolrel2);
 }
 
+// k_init_scalars keeping the right-hand side's norms (||b||^2, ||b||_inf) of the solve: a
+// refinement round's right-hand side is the same as the previous round's.
+__global__ void k_init_scalars_keep_b(BicgScalars *S, double tolrel2) {
+  BicgScalars z = {};
+  z.rho_old = 1.0;
+  z.alpha = 1.0;
+  z.omega = 1.0;
+  z.tolrel2 = tolrel2;
+  z.bnorm2 = S->bnorm2;
+  z.bmax = S->bmax;
+  z.tol2 = tolrel2 * z.bnorm2;
+  *S = z;
+}
+void launch_init_scalars_keep_b(BicgScalars *S, double tolrel2, cudaStream_t s) {
+  note_launch();
+  k_init_scalars_keep_b<<<1, 1, 0, s>>>(S, tolrel2);
+}
+
 template <typename T>
 __global__ void k_fill(T *x, size_t N, T v) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x)

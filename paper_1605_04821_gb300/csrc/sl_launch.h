@@ -255,6 +255,7 @@ void launch_bicg_xr(TX *x, const T *phat, const T *shat, const T *sv, const T *t
 void launch_norms(const double *a, size_t N, int which, BicgScalars *S, double *partials,
                   unsigned *counter, cudaStream_t s);
 void launch_init_scalars(BicgScalars *S, double tolrel2, cudaStream_t s);
+void launch_init_scalars_keep_b(BicgScalars *S, double tolrel2, cudaStream_t s);
 void launch_maxabs_diff(const double *a, const double *b, int n, double *out2,
                         unsigned *counter, double *partials, cudaStream_t s);
 
