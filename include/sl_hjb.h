@@ -237,7 +237,7 @@ typedef struct {
 } sl_stats;
 
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
- * krylov_tol 1e-12, kry_max 200, inner_tol 3e-3, ir_max 30, pi_tol 1e-10, pi_max 100,
+ * krylov_tol 1e-12, kry_max 200, inner_tol 1e-2, ir_max 30, pi_tol 1e-10, pi_max 100,
  * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
  * extrapolate 1, precond 0, amg_k_levels 2, smoother 0, fine_tma 1, coarse_fusion 3, howard_init 0,
  * howard_loose_tol 1e-7, argmin_skip 1. */

@@ -1688,7 +1688,7 @@ void sl_opts_default(sl_opts *o) {
   o->omega = 0.8;
   o->krylov_tol = 1e-12;
   o->kry_max = 200;
-  o->inner_tol = 3e-3;
+  o->inner_tol = 1e-2;
   o->ir_max = 30;
   o->pi_tol = 1e-10;
   o->pi_max = 100;
