@@ -138,8 +138,9 @@ typedef struct {
   double pi_tol;        /* Howard stop: ||X^m - X^{m-1}||_inf <= pi_tol max(1, ||X^m||_inf) */
   int pi_max;           /* Howard iterations per step */
   double tie_rel;       /* argmin picks the lowest k with v_k <= v_min + tie_rel max(1, |v_min|) */
-  int argmin_screen;    /* 1: screen controls in FP32 with a rigorous rounding bound, then
-                           decide in FP64 among the survivors (identical result); 0: all FP64 */
+  int argmin_screen;    /* 1 (default): screen controls in FP32 with a rigorous rounding bound,
+                           then decide in FP64 among the survivors (identical result, in either
+                           precision); 0: all FP64 */
   double rebuild_frac;  /* rebuild the Galerkin hierarchy when more than rebuild_frac * N
                            rows changed control since the last build (0: on any change).
                            The fine level always applies the current policy; a coarse
@@ -238,7 +239,7 @@ typedef struct {
 
 /* Fills o with the defaults: FP64, as many levels as possible, V(2,2), omega 0.8,
  * krylov_tol 1e-12, kry_max 200, inner_tol 1e-2, ir_max 30, pi_tol 1e-10, pi_max 100,
- * tie_rel 1e-12, argmin_screen 0, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
+ * tie_rel 1e-12, argmin_screen 1, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
  * extrapolate 1, precond 0, amg_k_levels 2, smoother 0, fine_tma 1, coarse_fusion 3, howard_init 0,
  * howard_loose_tol 1e-7, argmin_skip 1. */
 void sl_opts_default(sl_opts *o);

@@ -1693,7 +1693,7 @@ void sl_opts_default(sl_opts *o) {
   o->pi_tol = 1e-10;
   o->pi_max = 100;
   o->tie_rel = 1e-12;
-  o->argmin_screen = 0;
+  o->argmin_screen = 1;
   o->rebuild_frac = 0.01;
   o->use_graphs = 2;
   o->coarse_tail_rows = -1;
