@@ -772,13 +772,14 @@ __global__ void __launch_bounds__(256) k_coarse_up(CoarseLev<T> L, int tiles_x, 
   }
 }
 
-// Tile height of the fused passes: the tallest of 32, 16, 8 rows that still gives at least
-// 512 tiles (about three per SM); small levels take 8.
+// Tile height of the fused passes: the tallest of 32, 16 rows that still gives at least 512
+// tiles (about three per SM); smaller levels take 8, and 4 when 8 would give fewer than 128
+// tiles (their passes are latency-bound: more, smaller blocks run their phases in parallel).
 static int fused_tile_rows(int m) {
   const int tx = (m + 31) / 32;
   for (int th : {32, 16})
     if (tx * ((m + th - 1) / th) >= 512) return th;
-  return 8;
+  return tx * ((m + 7) / 8) >= 128 ? 8 : 4;
 }
 
 template <typename T>
@@ -803,7 +804,8 @@ void launch_coarse_down(const CoarseLev<T> &L, T omega, const T *b, const T *xin
   else { if (z) SL_DOWN(TH, 0, 1); else SL_DOWN(TH, 0, 0); }
   if (th == 32) { SL_DOWN_TH(32) }
   else if (th == 16) { SL_DOWN_TH(16) }
-  else { SL_DOWN_TH(8) }
+  else if (th == 8) { SL_DOWN_TH(8) }
+  else { SL_DOWN_TH(4) }
 #undef SL_DOWN_TH
 #undef SL_DOWN
 }
@@ -819,7 +821,8 @@ void launch_coarse_up(const CoarseLev<T> &L, T omega, const T *b, const T *cur, 
 #define SL_UP(TH, ST) k_coarse_up<T, TH, ST><<<blocks, 256, bytes, s>>>(L, tx, omega, b, cur, xc, nc, y)
   if (th == 32) { if (stab) SL_UP(32, 1); else SL_UP(32, 0); }
   else if (th == 16) { if (stab) SL_UP(16, 1); else SL_UP(16, 0); }
-  else { if (stab) SL_UP(8, 1); else SL_UP(8, 0); }
+  else if (th == 8) { if (stab) SL_UP(8, 1); else SL_UP(8, 0); }
+  else { if (stab) SL_UP(4, 1); else SL_UP(4, 0); }
 #undef SL_UP
 }
 template void launch_coarse_down<double>(const CoarseLev<double> &, double, const double *, const double *,
@@ -1346,7 +1349,7 @@ static cudaError_t prepare_coarse_T() {
   reinterpret_cast<const void *>(k_coarse_down<T, TH, 1, 0>), \
   reinterpret_cast<const void *>(k_coarse_down<T, TH, 1, 1>), \
   reinterpret_cast<const void *>(k_coarse_up<T, TH, 0>), reinterpret_cast<const void *>(k_coarse_up<T, TH, 1>)
-                      SL_FUSED(8), SL_FUSED(16), SL_FUSED(32),
+                      SL_FUSED(4), SL_FUSED(8), SL_FUSED(16), SL_FUSED(32),
                       reinterpret_cast<const void *>(k_vcycle_tail_smem<T>)};
 #undef SL_FUSED
   for (const void *f : fs) {
