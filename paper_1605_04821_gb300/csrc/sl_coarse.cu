@@ -773,13 +773,13 @@ __global__ void __launch_bounds__(256) k_coarse_up(CoarseLev<T> L, int tiles_x, 
 }
 
 // Tile height of the fused passes: the tallest of 32, 16 rows that still gives at least 512
-// tiles (about three per SM); smaller levels take 8, and 4 when 8 would give fewer than 128
+// tiles (about three per SM); smaller levels take 8, and 4 when 8 would give fewer than 512
 // tiles (their passes are latency-bound: more, smaller blocks run their phases in parallel).
 static int fused_tile_rows(int m) {
   const int tx = (m + 31) / 32;
   for (int th : {32, 16})
     if (tx * ((m + th - 1) / th) >= 512) return th;
-  return tx * ((m + 7) / 8) >= 128 ? 8 : 4;
+  return tx * ((m + 7) / 8) >= 512 ? 8 : 4;
 }
 
 template <typename T>
