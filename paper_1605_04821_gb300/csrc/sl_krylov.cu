@@ -439,15 +439,45 @@ __global__ void __launch_bounds__(kVecThreads) k_norms(const double *__restrict_
   double s2 = 0.0;
   unsigned long long mb = 0;
   const size_t st = size_t(gridDim.x) * blockDim.x;
-  for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
-    double av[kU];
+  if (which == 1) {
+    // The residual: its squares in FP32, each value turned into FP32 by integer operations
+    // (its exponent moved by -e_b, e_b the exponent of ||b||_inf from the solve's first call,
+    // the mantissa truncated to 24 bits) so that nothing of this loop runs on the narrow FP64
+    // pipe; relative to ||b|| the scaled values neither overflow nor underflow FP32 in any
+    // residual that the stop test can accept, and the 2^-23 truncation is far inside the test's
+    // needs.  The sum is scaled back in FP64 per thread.
+    const int eb = int((__double_as_longlong(S->bmax) >> 52) & 0x7ff);
+    const int shift = eb > 0 ? 1023 - eb : 0;  // exponent offset that brings ||b||_inf to about 1
+    float s2f = 0.f;
+    for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+      double av[kU];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) av[u] = i0 + u * st < N ? a[i0 + u * st] : 0.0;
+      for (int u = 0; u < kU; ++u) av[u] = i0 + u * st < N ? a[i0 + u * st] : 0.0;
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      if (i0 + u * st < N) {
-        s2 = fma(av[u], av[u], s2);
-        mb = max(mb, abs_bits(av[u]));
+      for (int u = 0; u < kU; ++u) {
+        if (i0 + u * st < N) {
+          const unsigned long long b = abs_bits(av[u]);
+          mb = max(mb, b);
+          const int e = int(b >> 52) + shift - 1023 + 127;  // FP32 biased exponent of the scaled value
+          const unsigned fb = e <= 0 ? 0u : (e >= 255 ? 0x7f7fffffu
+                                                       : (unsigned(e) << 23) | unsigned((b >> 29) & 0x7fffffull));
+          const float f = __uint_as_float(fb);
+          s2f = fmaf(f, f, s2f);
+        }
+      }
+    }
+    s2 = double(s2f) * exp2(-2.0 * shift);
+  } else {
+    for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
+      double av[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) av[u] = i0 + u * st < N ? a[i0 + u * st] : 0.0;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if (i0 + u * st < N) {
+          s2 = fma(av[u], av[u], s2);
+          mb = max(mb, abs_bits(av[u]));
+        }
       }
     }
   }
