@@ -510,6 +510,15 @@ sl_status sl_hjb_level_stats(const sl_hjb *h, int level, sl_level_stats *out);
 /* Number of levels in use. */
 int sl_hjb_num_levels(const sl_hjb *h);
 
+/* Test hook for the breakdown path of BiCGSTAB.  Marks the `iterations`-th BiCGSTAB iteration
+ * from now (counted over every later solve of the handle, separately for the FP64 iteration
+ * and the FP32 inner iteration of mixed precision) as a breakdown, as if rho had vanished; the
+ * solve then restarts from the true residual as after a real breakdown.  iterations == 0
+ * cancels a pending mark.  If the marked iteration meets the stop test, the solve ends as
+ * converged and the mark is spent.  SL_EINVAL for a null handle or a negative count.
+ * Synchronises with the device; call it between steps. */
+sl_status sl_hjb_inject_breakdown(sl_hjb *h, int iterations);
+
 /* Number of CUDA kernel launches the library has issued since it was loaded, over all
  * handles (host-side counter; used to report how many of the library's kernels ran in a
  * timed region). */

@@ -31,7 +31,7 @@ EXPORTED = ["sl_opts_default", "sl_hjb_create", "sl_hjb_step", "sl_hjb_solve",
             "sl_batch_last_error", "sl_batch_destroy", "sl_amg_create", "sl_amg_num_levels",
             "sl_amg_level", "sl_amg_apply", "sl_amg_last_error", "sl_amg_destroy",
             "sl_hjb_recorded_policy", "sl_hjb_set_launch", "sl_batch_autotune",
-            "sl_hjb_level_stats"]
+            "sl_hjb_level_stats", "sl_hjb_inject_breakdown"]
 
 
 class SlGrid(ctypes.Structure):
@@ -135,6 +135,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "sl_hjb_solve_record": (i, [vp, vp, d, d, i, i, ctypes.POINTER(SlStats), vp]),
         "sl_hjb_adjoint": (i, [vp, vp, vp, vp, i, vp, vp, ctypes.POINTER(SlStats), vp]),
         "sl_hjb_reset": (i, [vp]),
+        "sl_hjb_inject_breakdown": (i, [vp, i]),
         "sl_hjb_recorded_policy": (i, [vp, i, vp, vp]),
         "sl_hjb_set_launch": (i, [vp, i, i]),
         "sl_batch_autotune": (i, [vp, i, i, vp, i, ctypes.POINTER(i)]),
@@ -318,6 +319,11 @@ class Solver:
     def reset(self):
         """sl_hjb_reset: the next step starts like the first step of a new handle."""
         self._check(self._lib.sl_hjb_reset(self.h))
+
+    def inject_breakdown(self, iterations: int):
+        """sl_hjb_inject_breakdown: mark the BiCGSTAB iteration `iterations` from now as a
+        breakdown (a test hook for the restart path; 0 cancels)."""
+        self._check(self._lib.sl_hjb_inject_breakdown(self.h, iterations))
 
     def close(self):
         if getattr(self, "h", None):

@@ -111,6 +111,7 @@ struct sl_hjb {
   // step state (full-grid FP64 vectors)
   double *X = nullptr, *Xb = nullptr, *Uprev = nullptr, *F = nullptr, *R = nullptr, *Xpi = nullptr,
          *Fvec = nullptr, *Uprev2 = nullptr;
+  double *Ub = nullptr;  // U^{n-1} + dt f at the policy of the current solve (its ||F|| pass)
   bool have_prev2 = false;   // Uprev2 holds U^{n-2} of the step just taken (for extrapolation)
   double prev_t = 0.0, prev_dt = 0.0;
   float *F32 = nullptr;
@@ -840,8 +841,10 @@ sl_status true_residual(sl_hjb *h, double dt, double tolk, double *r, ResNorms *
   if (h->transposed)  // backward solve A^T mu = lambda
     launch_fineT_op<double>(OP_RESID, csrT_view<double>(h), h->o.omega, h->mu, h->lam, r, s);
   else
-    launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r, h->halo, h->SW, s);
-  // ||F|| (or ||lambda||) was taken once by linear_solve before its first round
+    launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r, h->halo, h->SW, s,
+                     0, nullptr, h->Ub);
+  // ||F|| (or ||lambda||) was taken once by linear_solve before its first round, which also
+  // left U^{n-1} + dt f of this policy in h->Ub
   launch_init_scalars_keep_b(h->S, tolk * tolk, s);
   launch_norms(r, N, 1, h->S, h->partials, h->counter, s);
   CK(cudaGetLastError());
@@ -870,7 +873,7 @@ sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
   // ||F||: the residual at X = (0 inside, psi on the boundary) is F itself
   if (!h->transposed)  // Xb vanishes inside: rows beyond the stencil reach need no taps
     launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, h->halo,
-                     h->SW, s, std::max(1, h->cl[0].R));
+                     h->SW, s, std::max(1, h->cl[0].R), h->Ub);
   CK(cudaGetLastError());
   // the right-hand side's norms, once per solve (every round keeps them in S)
   launch_init_scalars(h->S, 0.0, s);
@@ -1168,7 +1171,7 @@ sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long
   const bool fp64 = h->o.precision == 0;
   KBuf &k = h->kb;
   launch_hjb_resid(h->tab, h->policy, h->Xb, h->Uprev, h->F, h->d_phi, h->nf, dt, h->Fvec, h->halo,
-                   h->SW, s, std::max(1, h->cl[0].R));
+                   h->SW, s, std::max(1, h->cl[0].R), h->Ub);
   // the right-hand side's norms, once per solve (every round keeps them in S)
   launch_init_scalars(h->S, 0.0, s);
   launch_norms(h->Fvec, N, 0, h->S, h->partials, h->counter, s);
@@ -1181,7 +1184,8 @@ sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long
       h, s, depth, hir, cudaGraphCondTypeWhile, &G.k_ir, &tot,
       [&](cudaStream_t sb, int d, long long *nest) -> sl_status {
         double *r64 = fp64 ? k.r64 : h->R;
-        launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r64, h->halo, h->SW, sb);
+        launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r64, h->halo, h->SW, sb,
+                         0, nullptr, h->Ub);
         launch_init_scalars_ctl(h->S, h->ctl, sb);
         launch_norms(r64, N, 1, h->S, h->partials, h->counter, sb);
         cudaGraphConditionalHandle hen;
@@ -1991,6 +1995,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   AL(h->R, N);
   AL(h->Xpi, N);
   AL(h->Fvec, N);
+  AL(h->Ub, N);
   AL(h->F, N * h->nf);
   AL(h->F32, N * h->nf);
   if (h->f_cb) {
@@ -2402,6 +2407,15 @@ sl_status sl_hjb_level_info(const sl_hjb *h, int level, int *n, long long *expli
 }
 
 int sl_hjb_num_levels(const sl_hjb *h) { return h ? h->L : 0; }
+
+sl_status sl_hjb_inject_breakdown(sl_hjb *h, int iterations) {
+  if (!h || iterations < 0) return SL_EINVAL;
+  CK(cudaDeviceSynchronize());
+  BicgScalars *both[2] = {h->S, h->S32};
+  for (BicgScalars *S : both)
+    CK(cudaMemcpy(&S->inject_bd, &iterations, sizeof(int), cudaMemcpyHostToDevice));
+  return SL_OK;
+}
 
 long long sl_launch_count(void) { return launch_count(); }
 

@@ -275,6 +275,8 @@ struct BicgScalars {
   int first;                   // 1 until the first search direction has been formed
   int breakdown;               // 1: rho or (r^, v) or (t, t) vanished
   int nonfinite;               // 1: a NaN / Inf was seen
+  int inject_bd;               // > 0: iterations left until one is marked as a breakdown
+                               // (sl_hjb_inject_breakdown); kept across solves
 };
 
 }  // namespace sl

@@ -171,6 +171,7 @@ __global__ void k_init_scalars_ctl(BicgScalars *S, const DevCtl *c) {
   z.bnorm2 = S->bnorm2;
   z.bmax = S->bmax;
   z.tol2 = z.tolrel2 * z.bnorm2;
+  z.inject_bd = S->inject_bd;
   *S = z;
 }
 void launch_init_scalars_ctl(BicgScalars *S, const DevCtl *c, cudaStream_t s) {

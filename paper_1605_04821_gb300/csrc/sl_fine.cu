@@ -1321,7 +1321,8 @@ __global__ void __launch_bounds__(256) k_hjb_resid(FineTab tab, const uint8_t *_
                                                    const double *__restrict__ F,
                                                    const double *__restrict__ phi, int nf, double dt,
                                                    double *__restrict__ r, int zero_inside, int halo,
-                                                   int SW) {
+                                                   int SW, double *__restrict__ ub_out,
+                                                   const double *__restrict__ ub_in) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *xs = reinterpret_cast<double *>(smem_raw);
   constexpr int RPT = kFineRPT;
@@ -1356,12 +1357,18 @@ __global__ void __launch_bounds__(256) k_hjb_resid(FineTab tab, const uint8_t *_
     if (i2 > m) continue;
     const int j = i2 * n + i1;
     const int k = policy[(i2 - 1) * m + (i1 - 1)];
-    double f = 0.0;
+    double f = 0.0, ub = 0.0;
+    if (ub_in) {
+      ub = ub_in[j];
+    } else {
 #pragma unroll
-    for (int mm = 0; mm < 4; ++mm)
-      if (mm < nf) f = fma(__ldg(phi + k * nf + mm), F[mm * N + j], f);
+      for (int mm = 0; mm < 4; ++mm)
+        if (mm < nf) f = fma(__ldg(phi + k * nf + mm), F[mm * N + j], f);
+      if (ub_out || R > 0) ub = U[j] + dt * f;
+      if (ub_out) ub_out[j] = ub;
+    }
     if (R > 0 && i1 > R && i1 < n - 1 - R && i2 > R && i2 < n - 1 - R) {
-      r[j] = U[j] + dt * f;
+      r[j] = ub;
       continue;
     }
     const int sidx = (ty + 8 * rr + halo) * SW + tx + halo;
@@ -1380,24 +1387,32 @@ __global__ void __launch_bounds__(256) k_hjb_resid(FineTab tab, const uint8_t *_
       }
     }
     const double Xj = X[j];
-    const double v = fma(-tab.W64[e], xs[sidx], acc) + (f + tab.c64[k] * Xj);
-    r[j] = (U[j] - Xj) + dt * v;
+    if (ub_in) {
+      const double v = fma(-tab.W64[e], xs[sidx], acc) + tab.c64[k] * Xj;
+      r[j] = (ub - Xj) + dt * v;
+    } else {
+      const double v = fma(-tab.W64[e], xs[sidx], acc) + (f + tab.c64[k] * Xj);
+      r[j] = (U[j] - Xj) + dt * v;
+    }
   }
 }
 
 void launch_hjb_resid(const FineTab &tab, const uint8_t *policy, const double *X,
                       const double *Uprev, const double *F, const double *phi, int nf, double dt,
-                      double *r, int halo, int SW, cudaStream_t s, int zero_inside) {
+                      double *r, int halo, int SW, cudaStream_t s, int zero_inside, double *ub_out,
+                      const double *ub_in) {
   dim3 blk(32, 8), grd((tab.m + 31) / 32, (tab.m + 8 * kFineRPT - 1) / (8 * kFineRPT));
   const size_t bytes = size_t(SW) * (8 * kFineRPT + 2 * halo) * sizeof(double);
   note_launch();
+#define SL_RESID_ARGS tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW, ub_out, ub_in
   switch (tab.tmax) {
-    case 8: k_hjb_resid<8><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
-    case 12: k_hjb_resid<12><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
-    case 16: k_hjb_resid<16><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
-    case 20: k_hjb_resid<20><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
-    default: k_hjb_resid<0><<<grd, blk, bytes, s>>>(tab, policy, X, Uprev, F, phi, nf, dt, r, zero_inside, halo, SW); break;
+    case 8: k_hjb_resid<8><<<grd, blk, bytes, s>>>(SL_RESID_ARGS); break;
+    case 12: k_hjb_resid<12><<<grd, blk, bytes, s>>>(SL_RESID_ARGS); break;
+    case 16: k_hjb_resid<16><<<grd, blk, bytes, s>>>(SL_RESID_ARGS); break;
+    case 20: k_hjb_resid<20><<<grd, blk, bytes, s>>>(SL_RESID_ARGS); break;
+    default: k_hjb_resid<0><<<grd, blk, bytes, s>>>(SL_RESID_ARGS); break;
   }
+#undef SL_RESID_ARGS
 }
 
 // ----------------------------------------------------------------------------- transfers

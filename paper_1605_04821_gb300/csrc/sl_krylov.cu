@@ -121,6 +121,7 @@ __device__ void apply_post(int post, const double *tot, BicgScalars *S) {
       S->rr = tot[1];
       bad = !isfinite(tot[0]) || !isfinite(tot[1]);
       if (S->omega == 0.0 && S->ss > S->tol2) S->breakdown = 1;
+      if (S->inject_bd > 0 && --S->inject_bd == 0) S->breakdown = 1;
       break;
     case POST_BNORM:
       S->bnorm2 = tot[0];
@@ -333,6 +334,7 @@ __global__ void k_init_scalars(BicgScalars *S, double tolrel2) {
   z.alpha = 1.0;
   z.omega = 1.0;
   z.tolrel2 = tolrel2;
+  z.inject_bd = S->inject_bd;
   *S = z;
 }
 void launch_init_scalars(BicgScalars *S, double tolrel2, cudaStream_t s) {
@@ -351,6 +353,7 @@ __global__ void k_init_scalars_keep_b(BicgScalars *S, double tolrel2) {
   z.bnorm2 = S->bnorm2;
   z.bmax = S->bmax;
   z.tol2 = tolrel2 * z.bnorm2;
+  z.inject_bd = S->inject_bd;
   *S = z;
 }
 void launch_init_scalars_keep_b(BicgScalars *S, double tolrel2, cudaStream_t s) {

@@ -91,9 +91,13 @@ void launch_fine_od(const FineTab &tab, double dt, double omega, double *od64, f
 // r = U_prev - X + dt (L X + c X + f) for the current policy (interior), FP64.  With
 // zero_inside = R > 0 the caller promises X = 0 on the interior and R >= the longest tap:
 // rows farther than R from the boundary then skip their taps (r = U_prev + dt f).
+// ub_out (if not null) receives U_prev + dt f on every interior row; a later residual at the
+// same policy, U_prev, dt and source passes it back as ub_in and reads it in place of
+// U_prev, F and phi: r = ub - X + dt (L X + c X).
 void launch_hjb_resid(const FineTab &tab, const uint8_t *policy, const double *X,
                       const double *Uprev, const double *F, const double *phi, int nf, double dt,
-                      double *r, int halo, int SW, cudaStream_t s, int zero_inside = 0);
+                      double *r, int halo, int SW, cudaStream_t s, int zero_inside = 0,
+                      double *ub_out = nullptr, const double *ub_in = nullptr);
 
 template <typename T>
 void launch_restrict(const T *rf, int nf, T *bc, int nc, cudaStream_t s);

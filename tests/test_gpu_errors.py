@@ -7,7 +7,7 @@ import pytest
 
 import workloads as W
 from oracle import lisl
-from tests._gpu_util import TOL_FP64, rel_maxnorm, to_dev
+from tests._gpu_util import TOL_FP64, TOL_MIXED, rel_maxnorm, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -95,3 +95,44 @@ def test_nan_input_is_reported():
     assert e.value.status == S.SL_ENAN
     sol.close()
     _check_context_still_works(S)
+
+
+_BREAKDOWN_REF = {}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("use_graphs", [0, 1, 2])
+def test_bicgstab_breakdown_restarts(precision, use_graphs):
+    """SL_EBREAKDOWN is handled inside the solves: a breakdown marked on the first BiCGSTAB
+    iteration of the march (sl_hjb_inject_breakdown, as if rho had vanished) sends the solve
+    back to its true residual.  The march still ends with SL_OK and meets the oracle; it is not
+    bit-identical to the unmarked march (the restart changes the iterates), while a mark that
+    is cancelled before the march leaves it bit-identical.  The inner tolerance is tightened so
+    that no first FP32 iteration can meet its stop test (a mark on a converging iteration has
+    no effect)."""
+    import torch
+    S = _lib()
+    p = W.oracle_scale(True)
+    if "U" not in _BREAKDOWN_REF:
+        _BREAKDOWN_REF["U"] = lisl.solve(p).U
+    kw = dict(precision=precision, use_graphs=use_graphs)
+    if precision == 1:
+        kw["inner_tol"] = 1e-6
+    tol = TOL_FP64 if precision == 0 else TOL_MIXED
+    runs = {}
+    for mark in ("none", "first", "cancelled"):
+        sol = S.solver_from_problem(p, **kw)
+        if mark == "first":
+            sol.inject_breakdown(1)
+        elif mark == "cancelled":
+            sol.inject_breakdown(3)
+            sol.inject_breakdown(0)
+        u = to_dev(p.g)
+        st = sol.solve(u, 0.0, p.T, p.n_steps)
+        sol.close()
+        assert rel_maxnorm(u.cpu().numpy(), _BREAKDOWN_REF["U"]) <= tol, (mark, st)
+        runs[mark] = (u, st)
+    assert not torch.equal(runs["first"][0], runs["none"][0])
+    assert torch.equal(runs["cancelled"][0], runs["none"][0])
+    assert runs["cancelled"][1]["krylov_iters"] == runs["none"][1]["krylov_iters"]
+    assert runs["first"][1]["steps"] == runs["none"][1]["steps"] == p.n_steps
