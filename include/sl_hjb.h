@@ -221,6 +221,12 @@ typedef struct {
                            change since the last improvement keeps its control, and a tile
                            whose nodes all keep theirs is not evaluated.  The policies are the
                            same as with 0 (every node re-decided). */
+  int ir_recursive;     /* mixed precision: the most refinement rounds in a row that start from
+                           the previous inner solve's own residual (its recursively updated FP32
+                           r, which is F - A X up to FP32 drift) instead of a true FP64 residual,
+                           taken while that residual's 2-norm exceeds twice the stop threshold.
+                           The stop test is only ever applied to a true FP64 residual.  Default
+                           3; 0: every round starts from a true residual. */
 } sl_opts;
 
 typedef struct {
@@ -241,7 +247,7 @@ typedef struct {
  * krylov_tol 1e-12, kry_max 200, inner_tol 1e-2, ir_max 30, pi_tol 1e-10, pi_max 100,
  * tie_rel 1e-12, argmin_screen 1, rebuild_frac 0.01, use_graphs 2, coarse_tail_rows -1,
  * extrapolate 1, precond 0, amg_k_levels 2, smoother 0, fine_tma 1, coarse_fusion 3, howard_init 0,
- * howard_loose_tol 1e-7, argmin_skip 1. */
+ * howard_loose_tol 1e-7, argmin_skip 1, ir_recursive 3. */
 void sl_opts_default(sl_opts *o);
 
 /* Creates a solver.  Builds the Scheme-2 stencil tables of every control on every

@@ -67,7 +67,8 @@ class SlOpts(ctypes.Structure):
                 ("extrapolate", ctypes.c_int), ("precond", ctypes.c_int), ("amg_k_levels", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("fine_tma", ctypes.c_int),
                 ("coarse_fusion", ctypes.c_int), ("howard_init", ctypes.c_int),
-                ("howard_loose_tol", ctypes.c_double), ("argmin_skip", ctypes.c_int)]
+                ("howard_loose_tol", ctypes.c_double), ("argmin_skip", ctypes.c_int),
+                ("ir_recursive", ctypes.c_int)]
 
 
 class SlInstance(ctypes.Structure):

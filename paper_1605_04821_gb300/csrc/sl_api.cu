@@ -58,7 +58,7 @@ struct DevStepGraph {
   cudaGraphExec_t exec = nullptr;
   double dt = -1.0;
   long long k_step = 0, k_imp0 = 0, k_pre = 0, k_pi = 0, k_rebuild = 0, k_ir = 0, k_enter = 0, k_kry = 0,
-            k_ok = 0;
+            k_ok = 0, k_true = 0;
 };
 
 struct KBuf {  // BiCGSTAB vectors on the finest level
@@ -885,27 +885,35 @@ sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
   int total = 0;
   const bool fp64 = h->o.precision == 0;
   const int rounds = fp64 ? 12 : h->o.ir_max + 1;
+  bool need_true = true;  // mixed: this round starts from a true residual (ir_next_recursive)
+  int rec_rounds = 0;
+  double bn2 = 0.0;       // ||F||_2^2 of the solve
   for (int round = 0; round < rounds; ++round) {
-    ResNorms nr{};
-    double *r64 = fp64 ? k.r64 : h->R;
-    sl_status r = true_residual(h, dt, tolk, r64, &nr, s);
-    if (r != SL_OK) return r;
-    const double rel2 = nr.bn2 > 0 ? std::sqrt(nr.rr / nr.bn2) : std::sqrt(nr.rr);
-    if (st) st->res_final = rel2;
-    const bool ok2 = nr.rr <= tol * tol * nr.bn2;
-    const bool okinf = nr.rmax <= tol * nr.bmax;
-    if (ok2 && okinf) return SL_OK;
-    if (ok2 && !okinf) tolk *= 0.1;
-    if (fp64 && total >= h->o.kry_max) break;
+    sl_status r = SL_OK;
+    if (need_true) {
+      ResNorms nr{};
+      double *r64 = fp64 ? k.r64 : h->R;
+      r = true_residual(h, dt, tolk, r64, &nr, s);
+      if (r != SL_OK) return r;
+      bn2 = nr.bn2;
+      const double rel2 = nr.bn2 > 0 ? std::sqrt(nr.rr / nr.bn2) : std::sqrt(nr.rr);
+      if (st) st->res_final = rel2;
+      const bool ok2 = nr.rr <= tol * tol * nr.bn2;
+      const bool okinf = nr.rmax <= tol * nr.bmax;
+      if (ok2 && okinf) return SL_OK;
+      if (ok2 && !okinf) tolk *= 0.1;
+      if (fp64 && total >= h->o.kry_max) break;
+    }
     int it = 0;
     if (fp64) {
       // BiCGSTAB on the true residual; S holds ||F||_2 and the threshold (tolk ||F||_2)^2
       r = bicgstab<double, double>(h, dt, X, k.r64, k.rh64, k.p64, k.v64, k.s64, k.t64, k.ph64,
                                    k.sh64, h->S, h->o.kry_max - total, &it, s);
     } else {
-      // refinement: FP32 inner solve of A e = fp32(r) from e = 0, then X += e in FP64
+      // refinement: FP32 inner solve of A e = fp32(r) from e = 0, then X += e in FP64; r is the
+      // true residual, or the previous inner solve's own residual r - A e (left in k.r32)
       if (st) st->ir_iters += 1;
-      launch_convert<double, float>(h->R, k.r32, N, s);
+      if (need_true) launch_convert<double, float>(h->R, k.r32, N, s);
       launch_fill<float>(k.e32, N, 0.0f, s);
       launch_init_scalars(h->S32, h->o.inner_tol * h->o.inner_tol, s);
       launch_dot2<float>(k.r32, k.r32, nullptr, nullptr, N, POST_BNORM, h->S32, h->partials, h->counter, s);
@@ -913,6 +921,11 @@ sl_status linear_solve(sl_hjb *h, double dt, sl_stats *st, cudaStream_t s) {
                                  k.sh32, h->S32, h->o.kry_max, &it, s);
       launch_add_f32_to_f64(X, k.e32, N, s);
       CK(cudaGetLastError());
+      // bicgstab() left the inner solve's last scalars (S32) in h->hS
+      const bool rec = (r == SL_OK || r == SL_ENOCONV_KRYLOV) &&
+                       ir_next_recursive(h->hS->rr, tol, bn2, rec_rounds, h->o.ir_recursive);
+      need_true = !rec;
+      rec_rounds = rec ? rec_rounds + 1 : 0;
     }
     total += it;
     if (st) st->krylov_iters += it;
@@ -1184,13 +1197,25 @@ sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long
       h, s, depth, hir, cudaGraphCondTypeWhile, &G.k_ir, &tot,
       [&](cudaStream_t sb, int d, long long *nest) -> sl_status {
         double *r64 = fp64 ? k.r64 : h->R;
-        launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r64, h->halo, h->SW, sb,
-                         0, nullptr, h->Ub);
-        launch_init_scalars_ctl(h->S, h->ctl, sb);
-        launch_norms(r64, N, 1, h->S, h->partials, h->counter, sb);
-        cudaGraphConditionalHandle hen;
+        cudaGraphConditionalHandle htr, hen;
+        CK(new_cond_handle(sb, &htr));
         CK(new_cond_handle(sb, &hen));
-        launch_ctl_ir_decide(h->ctl, h->S, h->o.krylov_tol, fp64 ? 1 : 0, h->o.kry_max, hen, sb);
+        // a true residual and the stop test (if node), or the previous inner solve's residual
+        launch_ctl_ir_pre(h->ctl, htr, hen, sb);
+        long long t1 = 0;
+        const sl_status s1 = add_cond(
+            h, sb, d, htr, cudaGraphCondTypeIf, &G.k_true, &t1,
+            [&](cudaStream_t sc, int, long long *) -> sl_status {
+              launch_hjb_resid(h->tab, h->policy, h->X, h->Uprev, h->F, h->d_phi, h->nf, dt, r64, h->halo,
+                               h->SW, sc, 0, nullptr, h->Ub);
+              launch_init_scalars_ctl(h->S, h->ctl, sc);
+              launch_norms(r64, N, 1, h->S, h->partials, h->counter, sc);
+              launch_ctl_ir_decide(h->ctl, h->S, h->o.krylov_tol, fp64 ? 1 : 0, h->o.kry_max, hen, sc);
+              CK(cudaGetLastError());
+              return SL_OK;
+            });
+        *nest += t1;
+        if (s1 != SL_OK) return s1;
         long long t2 = 0;
         const sl_status s2 = add_cond(
             h, sb, d, hen, cudaGraphCondTypeIf, &G.k_enter, &t2,
@@ -1200,7 +1225,7 @@ sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long
                 s3 = cap_bicgstab<double, double>(h, dt, h->X, k.r64, k.rh64, k.p64, k.v64, k.s64, k.t64,
                                                   k.ph64, k.sh64, h->S, sc, d2, nest2, G);
               } else {
-                launch_convert<double, float>(h->R, k.r32, N, sc);
+                launch_convert<double, float>(h->R, k.r32, N, sc, &h->ctl->need_true);
                 launch_fill<float>(k.e32, N, 0.0f, sc);
                 launch_init_scalars(h->S32, h->o.inner_tol * h->o.inner_tol, sc);
                 launch_dot2<float>(k.r32, k.r32, nullptr, nullptr, N, POST_BNORM, h->S32, h->partials,
@@ -1211,6 +1236,7 @@ sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long
               }
               if (s3 != SL_OK) return s3;
               launch_ctl_kry_end(h->ctl, fp64 ? 1 : 0, sc);
+              if (!fp64) launch_ctl_ir_next(h->ctl, h->S, h->S32, h->o.ir_recursive, sc);
               CK(cudaGetLastError());
               return SL_OK;
             });
@@ -1331,7 +1357,8 @@ bool dev_step_ok(const sl_hjb *h) {
 long long dev_kernels(const DevStepGraph &G, const DevCtl &c) {
   return G.k_step * c.c_steps + G.k_imp0 * c.c_improve0 + G.k_pre * c.c_pre + G.k_pi * c.c_pibody +
          G.k_rebuild * c.c_rebuild +
-         G.k_ir * c.c_ir + G.k_enter * c.c_enter + G.k_kry * c.c_kry + G.k_ok * c.c_ok;
+         G.k_ir * c.c_ir + G.k_true * c.c_true + G.k_enter * c.c_enter + G.k_kry * c.c_kry +
+         G.k_ok * c.c_ok;
 }
 
 // Captures the step graph for step size dt (after the host-side tables for dt).
@@ -1710,6 +1737,7 @@ void sl_opts_default(sl_opts *o) {
   o->howard_init = 0;
   o->howard_loose_tol = 1e-7;
   o->argmin_skip = 1;
+  o->ir_recursive = 3;
 }
 
 const char *sl_hjb_last_error(const sl_hjb *h) { return h ? h->err.c_str() : "null handle"; }
@@ -1762,6 +1790,7 @@ static sl_status create_impl(sl_hjb *h, const sl_grid *g, const sl_controls *c, 
   if (h->o.coarse_fusion < 0) return fail(h, SL_EINVAL, "coarse_fusion must be >= 0");
   if (h->o.howard_init != 0 && h->o.howard_init != 1) return fail(h, SL_EINVAL, "howard_init must be 0 or 1");
   if (h->o.argmin_skip != 0 && h->o.argmin_skip != 1) return fail(h, SL_EINVAL, "argmin_skip must be 0 or 1");
+  if (h->o.ir_recursive < 0) return fail(h, SL_EINVAL, "ir_recursive must be >= 0");
   if (!(h->o.howard_loose_tol >= 0.0) || (h->o.howard_loose_tol > 0.0 && h->o.howard_loose_tol < h->o.krylov_tol))
     return fail(h, SL_EINVAL, "howard_loose_tol must be 0 or at least krylov_tol");
   if (h->o.precond == 1 && (h->o.nu1 < 1 || h->o.amg_k_levels < 0))

@@ -152,6 +152,8 @@ __global__ void k_ctl_ls_begin(DevCtl *c, double tol, double loose_tol, cudaGrap
   c->ls_tol = c->ls_loose ? loose_tol : tol;
   c->tolk = c->ls_tol;
   c->ls_done = 0;
+  c->need_true = 1;
+  c->rec_rounds = 0;
   cudaGraphSetConditional(ir, 1u);
 }
 void launch_ctl_ls_begin(DevCtl *c, double tol, double loose_tol, cudaGraphConditionalHandle ir, cudaStream_t s) {
@@ -184,7 +186,7 @@ void launch_init_scalars_ctl(BicgScalars *S, const DevCtl *c, cudaStream_t s) {
 // test holds; in FP64 give up once kry_max Krylov iterations are spent.
 __global__ void k_ctl_ir_decide(DevCtl *c, const BicgScalars *S, double tol, int fp64, int kry_max,
                                 cudaGraphConditionalHandle enter) {
-  c->c_ir += 1;
+  c->c_true += 1;
   tol = c->ls_tol;  // this solve's tolerance (k_ctl_ls_begin)
   const double bn2 = S->bnorm2, bmax = S->bmax, rr = S->rr, rmax = S->rmax;
   unsigned go = 0;
@@ -267,6 +269,37 @@ __global__ void k_ctl_ir_end(DevCtl *c, int rounds, cudaGraphConditionalHandle i
 void launch_ctl_ir_end(DevCtl *c, int rounds, cudaGraphConditionalHandle ir, cudaStream_t s) {
   note_launch();
   k_ctl_ir_end<<<1, 1, 0, s>>>(c, rounds, ir);
+}
+
+// Start of a refinement round: take a true residual (then k_ctl_ir_decide sets `enter`), or go
+// straight to the inner solve on the previous inner solve's residual.
+__global__ void k_ctl_ir_pre(DevCtl *c, cudaGraphConditionalHandle tr, cudaGraphConditionalHandle enter) {
+  c->c_ir += 1;
+  const bool t = c->need_true != 0;
+  cudaGraphSetConditional(tr, t ? 1u : 0u);
+  if (!t) {
+    c->c_enter += 1;
+    cudaGraphSetConditional(enter, 1u);
+  }
+}
+void launch_ctl_ir_pre(DevCtl *c, cudaGraphConditionalHandle tr, cudaGraphConditionalHandle enter,
+                       cudaStream_t s) {
+  note_launch();
+  k_ctl_ir_pre<<<1, 1, 0, s>>>(c, tr, enter);
+}
+
+// End of an inner solve of mixed precision: where the next round starts (ir_next_recursive); a
+// breakdown or a failure always goes back to a true residual.
+__global__ void k_ctl_ir_next(DevCtl *c, const BicgScalars *S, const BicgScalars *S32, int max_rec) {
+  const bool ok = c->status == SL_OK && (c->kry_res == KRY_CONVERGED || c->kry_res == KRY_CAP);
+  const bool rec = ok && ir_next_recursive(S32->rr, c->ls_tol, S->bnorm2, c->rec_rounds, max_rec);
+  c->need_true = rec ? 0 : 1;
+  c->rec_rounds = rec ? c->rec_rounds + 1 : 0;
+}
+void launch_ctl_ir_next(DevCtl *c, const BicgScalars *S, const BicgScalars *S32, int max_rec,
+                        cudaStream_t s) {
+  note_launch();
+  k_ctl_ir_next<<<1, 1, 0, s>>>(c, S, S32, max_rec);
 }
 
 // After the linear solve: improve only if it succeeded; a failure ends the Howard loop.

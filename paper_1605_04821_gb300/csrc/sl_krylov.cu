@@ -373,7 +373,8 @@ void launch_fill(T *x, size_t N, T v, cudaStream_t s) {
 }
 
 template <typename Tin, typename Tout>
-__global__ void k_convert(const Tin *__restrict__ x, Tout *__restrict__ y, size_t N) {
+__global__ void k_convert(const Tin *__restrict__ x, Tout *__restrict__ y, size_t N, const int *flag) {
+  if (flag && *flag == 0) return;  // the caller's device-side condition is off
   const size_t st = size_t(gridDim.x) * blockDim.x;
   for (size_t i0 = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i0 < N; i0 += kU * st) {
     Tin v[kU];
@@ -385,9 +386,9 @@ __global__ void k_convert(const Tin *__restrict__ x, Tout *__restrict__ y, size_
   }
 }
 template <typename Tin, typename Tout>
-void launch_convert(const Tin *x, Tout *y, size_t N, cudaStream_t s) {
+void launch_convert(const Tin *x, Tout *y, size_t N, cudaStream_t s, const int *flag) {
   note_launch();
-  k_convert<Tin, Tout><<<kRedBlocks, kVecThreads, 0, s>>>(x, y, N);
+  k_convert<Tin, Tout><<<kRedBlocks, kVecThreads, 0, s>>>(x, y, N, flag);
 }
 
 // X = 2 U - V on interior nodes (boundary of X untouched).
@@ -629,8 +630,8 @@ template void launch_bicg_xr<double, double>(double *, const double *, const dou
 template void launch_bicg_xr<float, float>(float *, const float *, const float *, const float *,
                                            const float *, float *, const float *, size_t,
                                            BicgScalars *, double *, unsigned *, cudaStream_t);
-template void launch_convert<double, float>(const double *, float *, size_t, cudaStream_t);
-template void launch_convert<float, double>(const float *, double *, size_t, cudaStream_t);
+template void launch_convert<double, float>(const double *, float *, size_t, cudaStream_t, const int *);
+template void launch_convert<float, double>(const float *, double *, size_t, cudaStream_t, const int *);
 template void launch_fill<int32_t>(int32_t *, size_t, int32_t, cudaStream_t);
 
 }  // namespace sl

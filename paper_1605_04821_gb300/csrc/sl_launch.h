@@ -236,7 +236,7 @@ void launch_adj_dtheta(const FineTab &tab, const DTabView &d, const uint8_t *pol
 template <typename T>
 void launch_fill(T *x, size_t N, T v, cudaStream_t s);
 template <typename Tin, typename Tout>
-void launch_convert(const Tin *x, Tout *y, size_t N, cudaStream_t s);
+void launch_convert(const Tin *x, Tout *y, size_t N, cudaStream_t s, const int *flag = nullptr);
 void launch_extrapolate(double *X, const double *U, const double *V, int n, cudaStream_t s);
 void launch_add_f32_to_f64(double *x, const float *e, size_t N, cudaStream_t s);
 
@@ -290,7 +290,19 @@ struct DevCtl {
   double ls_tol;         // stop tolerance of the current linear solve
   int ls_loose;          // the current solve is a step's first, at howard_loose_tol
   int skip_ok;           // the argmin may skip settled nodes (ArgminArgs::skip_flag)
+  int need_true;         // the next refinement round starts from a true FP64 residual
+  int rec_rounds;        // consecutive rounds on the inner solve's own residual
+  long long c_true;      // true residuals taken by refinement rounds
 };
+
+// Mixed-precision refinement: the next round starts from the inner solve's own residual (the
+// recursively updated FP32 r of BiCGSTAB, F - A X up to FP32 drift) when that residual's 2-norm
+// is still above twice the stop threshold tol ||F||_2 and fewer than max_rec rounds in a row
+// have done so; otherwise it starts from a true FP64 residual, the only one the stop test reads.
+// The host loop and the device-side control both decide with this function.
+SL_HD bool ir_next_recursive(double inner_rr, double tol, double bn2, int rec_rounds, int max_rec) {
+  return rec_rounds < max_rec && inner_rr > 4.0 * (tol * tol * bn2);
+}
 
 // Explicit-row counts of the coarse levels, gathered into DevCtl::nexpl (levels 1 .. L-1).
 struct NexplPtrs {
@@ -330,6 +342,10 @@ void launch_ctl_kry_begin(DevCtl *c, int fp64, int kry_max, cudaGraphConditional
 void launch_ctl_kry_check(DevCtl *c, const BicgScalars *S, cudaGraphConditionalHandle kry, cudaStream_t s);
 void launch_ctl_kry_end(DevCtl *c, int fp64, cudaStream_t s);
 void launch_ctl_ir_end(DevCtl *c, int rounds, cudaGraphConditionalHandle ir, cudaStream_t s);
+void launch_ctl_ir_pre(DevCtl *c, cudaGraphConditionalHandle tr, cudaGraphConditionalHandle enter,
+                       cudaStream_t s);
+void launch_ctl_ir_next(DevCtl *c, const BicgScalars *S, const BicgScalars *S32, int max_rec,
+                        cudaStream_t s);
 void launch_ctl_after_ls(DevCtl *c, cudaGraphConditionalHandle ok, cudaGraphConditionalHandle pi,
                          cudaStream_t s);
 void launch_ctl_pi_post(DevCtl *c, const unsigned long long *changes, const int *flags,

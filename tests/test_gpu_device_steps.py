@@ -72,11 +72,13 @@ def test_graph_steps_equal_host_steps(name, precision):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("opts", [dict(howard_init=1), dict(howard_loose_tol=1e-6),
-                                  dict(howard_init=1, howard_loose_tol=1e-6)])
+                                  dict(howard_init=1, howard_loose_tol=1e-6),
+                                  dict(ir_recursive=0), dict(ir_recursive=1)])
 def test_howard_variants_graph_equal_host_and_match_the_oracle(opts, precision):
-    """The Howard start (sl_opts.howard_init) and the loose first solve (howard_loose_tol) run
-    the same way in both modes and reach the oracle's solution: the last solve of every step
-    stays at krylov_tol and its policy is the improvement of its result."""
+    """The Howard start (sl_opts.howard_init), the loose first solve (howard_loose_tol) and the
+    refinement rounds on the inner solve's own residual (ir_recursive; the default is 3) run the
+    same way in both modes and reach the oracle's solution: the last solve of every step stays
+    at krylov_tol and its policy is the improvement of its result."""
     p = _case("s129")
     u1, pol1, st1 = _march(p, 1, precision, **opts)
     u2, pol2, st2 = _march(p, 2, precision, **opts)

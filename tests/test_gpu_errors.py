@@ -37,6 +37,8 @@ def test_invalid_arguments_are_refused():
         S.solver_from_problem(p, precision=2)
     with pytest.raises(S.SLError):
         S.solver_from_problem(p, precond=3)
+    with pytest.raises(S.SLError):
+        S.solver_from_problem(p, ir_recursive=-1)
     sol = S.solver_from_problem(p)
     with pytest.raises(S.SLError) as e:
         sol.step(to_dev(p.g), 0.1, -0.1)
