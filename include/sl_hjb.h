@@ -224,9 +224,11 @@ typedef struct {
   int ir_recursive;     /* mixed precision: the most refinement rounds in a row that start from
                            the previous inner solve's own residual (its recursively updated FP32
                            r, which is F - A X up to FP32 drift) instead of a true FP64 residual,
-                           taken while that residual's 2-norm exceeds twice the stop threshold.
+                           taken while that residual's 2-norm exceeds twice the stop threshold
+                           and lies within four orders of magnitude of the last true residual.
                            The stop test is only ever applied to a true FP64 residual.  Default
-                           3; 0: every round starts from a true residual. */
+                           3; 0: every round starts from a true residual.  The backward solves
+                           of sl_hjb_adjoint always start their rounds from a true residual. */
 } sl_opts;
 
 typedef struct {

@@ -288,11 +288,12 @@ void launch_ctl_ir_pre(DevCtl *c, cudaGraphConditionalHandle tr, cudaGraphCondit
   k_ctl_ir_pre<<<1, 1, 0, s>>>(c, tr, enter);
 }
 
-// End of an inner solve of mixed precision: where the next round starts (ir_next_recursive); a
-// breakdown or a failure always goes back to a true residual.
+// End of an inner solve of mixed precision: where the next round starts (ir_next_recursive; S
+// still holds the norms of the last true residual); a breakdown or a failure always goes back
+// to a true residual.
 __global__ void k_ctl_ir_next(DevCtl *c, const BicgScalars *S, const BicgScalars *S32, int max_rec) {
   const bool ok = c->status == SL_OK && (c->kry_res == KRY_CONVERGED || c->kry_res == KRY_CAP);
-  const bool rec = ok && ir_next_recursive(S32->rr, c->ls_tol, S->bnorm2, c->rec_rounds, max_rec);
+  const bool rec = ok && ir_next_recursive(S32->rr, c->ls_tol, S->bnorm2, S->rr, c->rec_rounds, max_rec);
   c->need_true = rec ? 0 : 1;
   c->rec_rounds = rec ? c->rec_rounds + 1 : 0;
 }

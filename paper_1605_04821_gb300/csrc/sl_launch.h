@@ -297,11 +297,14 @@ struct DevCtl {
 
 // Mixed-precision refinement: the next round starts from the inner solve's own residual (the
 // recursively updated FP32 r of BiCGSTAB, F - A X up to FP32 drift) when that residual's 2-norm
-// is still above twice the stop threshold tol ||F||_2 and fewer than max_rec rounds in a row
+// is still above twice the stop threshold tol ||F||_2, no more than four orders of magnitude
+// below the last true residual (rr_true = its squared 2-norm; the drift, about 1e-7 of that
+// residual, then stays below 1e-3 of the one handed on), and fewer than max_rec rounds in a row
 // have done so; otherwise it starts from a true FP64 residual, the only one the stop test reads.
 // The host loop and the device-side control both decide with this function.
-SL_HD bool ir_next_recursive(double inner_rr, double tol, double bn2, int rec_rounds, int max_rec) {
-  return rec_rounds < max_rec && inner_rr > 4.0 * (tol * tol * bn2);
+SL_HD bool ir_next_recursive(double inner_rr, double tol, double bn2, double rr_true, int rec_rounds,
+                             int max_rec) {
+  return rec_rounds < max_rec && inner_rr > 4.0 * (tol * tol * bn2) && inner_rr > 1e-8 * rr_true;
 }
 
 // Explicit-row counts of the coarse levels, gathered into DevCtl::nexpl (levels 1 .. L-1).
