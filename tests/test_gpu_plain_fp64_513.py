@@ -6,7 +6,7 @@ The oracle's march (sparse direct solve per Howard iteration, about 60 s per fac
 here) is stored in tests/golden/plain_fp64_513.npz by tests/golden/make_plain_fp64_513.py,
 which calls only the oracle.  Checks, element by element: U after step 1 and at t = T to 1e-10
 relative max-norm; the policies after step 1 and at T equal up to near-ties within 1e-12
-(judged with the oracle's control values at the nodes where they differ); the Howard
+(decided with the oracle's control values at the nodes where they differ); the Howard
 iteration count of every step (with the oracle's Howard iteration: sl_opts.howard_init = 0
 and howard_loose_tol = 0).
 At 513^2 the stencil offsets reach 3.4-3.8 cells, so the truncation band of Section 2.1 is
