@@ -864,7 +864,10 @@ sl_status true_residual(sl_hjb *h, double dt, double tolk, double *r, ResNorms *
 // A^alpha is an M-matrix with row sums >= 1 - dt c (Section 3.4), so for c = 0 the max-norm
 // test bounds the error of the step: ||X - X*||_inf <= ||r||_inf.  When the Krylov recurrence
 // meets the 2-norm test but the true max-norm test fails, the inner threshold is tightened
-// tenfold and BiCGSTAB restarts from the true residual.
+// tenfold and BiCGSTAB restarts from the true residual.  In mixed precision each round is an
+// FP32 inner solve of A e = r followed by X += e in FP64; r is the true residual, or, while
+// ir_next_recursive() allows it, the previous inner solve's own residual r - A e, so that the
+// true residual (and the stop test on it) is formed only once the solve may have converged.
 //
 // With h->transposed set, the same loop solves the backward system A^T mu = lambda of the
 // adjoint (h->mu from its initial value, right-hand side h->lam).
@@ -1182,8 +1185,9 @@ sl_status cap_bicgstab(sl_hjb *h, double dt, TX *x, T *r, T *rh, T *p, T *v, T *
   return st;
 }
 
-// linear_solve() with its refinement / restart rounds a while node and the Krylov part of a
-// round an if node.
+// linear_solve() with its refinement / restart rounds a while node; in a round, the true
+// residual with the stop test is an if node (skipped when the round starts from the previous
+// inner solve's residual) and the Krylov part another.
 sl_status cap_linear_solve(sl_hjb *h, double dt, cudaStream_t s, int depth, long long *nested,
                            DevStepGraph &G) {
   const size_t N = NN(h, 0);
